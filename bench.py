@@ -1,0 +1,392 @@
+"""Benchmark of the G-QAOA statevector hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload large|small]
+
+Workload "large" (default): one random 3-SAT instance with n = 28 variables
+and m = 118 clauses (d ~ 4.2, seed 0), p = 100 G-QAOA rounds with angles
+uniform in [0, pi), 10^6 fair-sampled shots. A step is the whole hot path on
+that input: cost table + histogram, p fused rounds + final readout, shots.
+Metric: amplitude-rounds per second, p * 2^n per step, whole job.
+
+Under torchrun (N > 1) each rank runs its own instance (seed = rank): the
+problems are independent, so there is no collective on the data path;
+value = all ranks' amplitude-rounds / max-over-ranks time ("weak" scaling).
+
+--impl reference times the FP64 CPU oracle (the plain reference written from
+the paper) on the host cores on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: (n, d, p, shots, seed)
+    "large": dict(n=28, m=118, p=100, shots=1_000_000, seed=0,
+                  desc="random 3-SAT n=28 m=118 (d~4.2) seed 0, p=100 random angles, 1e6 shots"),
+    "small": dict(n=10, m=42, p=8, shots=10_000, seed=0,
+                  desc="random 3-SAT n=10 m=42 (d=4.2) seed 0, p=8 random angles, 1e4 shots"),
+}
+METRIC = "G-QAOA amp-rounds/s"
+UNIT = "amp-rounds/s"
+PEAK_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (200 ms period)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- peaks / profiles
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return PEAK_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    path = os.path.join(ROOT, "paper_2402_02585_gb300", "csrc", "stream.cu")
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def profiled_traffic(n: int):
+    """dram bytes per round-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "round_kernel_n28.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    mh = re.search(r"stream\.cu sha256\[:16\]:\s*`?([0-9a-f]{16})", text)
+    mt = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not mh or not mt or mh.group(1) != kernel_source_hash():
+        return None
+    return float(mt.group(1))
+
+
+# ----------------------------------------------------------------- oracle (CPU) timing
+class OracleSample:
+    """The FP64 oracle on a bounded sample of the workload.
+
+    The cost table is built once at the workload's full n (timed); a step
+    sample then times `rounds` statevector rounds on the full 2^n state and
+    `shots` of the workload's shots. One step is extrapolated as
+    cost table + p x (time per round) + (time per shot) x all shots."""
+
+    def __init__(self, wl: dict, rounds: int = 1, shots: int = 50_000):
+        from oracle import statevector as sv
+        from paper_2402_02585_gb300 import instances
+        self.sv = sv
+        self.wl = wl
+        self.rounds = min(rounds, wl["p"])
+        self.shots = min(shots, wl["shots"])
+        n, m, p = wl["n"], wl["m"], wl["p"]
+        lits = instances.random_3sat(n, m, wl["seed"])
+        self.g, self.b = instances.random_angles(p, wl["seed"])
+        t0 = time.perf_counter()
+        self.cost, _ = sv.cost_table(lits, n)
+        self.t_cost = time.perf_counter() - t0
+        self.cores = sv.num_threads()
+
+    def step(self):
+        sv, wl = self.sv, self.wl
+        n, p = wl["n"], wl["p"]
+        t1 = time.perf_counter()
+        psi = sv.evolve(self.cost, n, self.g[:self.rounds], self.b[:self.rounds])
+        t2 = time.perf_counter()
+        sv.sample(psi, n, seed=1, shots=self.shots)
+        t3 = time.perf_counter()
+        t_round = (t2 - t1) / self.rounds
+        t_shots = (t3 - t2) * wl["shots"] / self.shots
+        step = self.t_cost + p * t_round + t_shots
+        self.desc = (f"n={n} m={wl['m']}: full FP64 cost table once ({self.t_cost:.2f} s), "
+                     f"{self.rounds} of {p} rounds on the full state ({t_round:.3f} s/round), "
+                     f"{self.shots} of {wl['shots']} shots ({t3 - t2:.2f} s); step = cost table "
+                     f"+ {p} rounds + all shots, extrapolated linearly")
+        return p * (1 << n) / step, step
+
+
+def run_reference(args, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    total_t0 = time.perf_counter()
+    sample = OracleSample(wl)
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        _, step = sample.step()
+        if i >= args.warmup:
+            per_step.append(step)
+    step = float(np.mean(per_step))
+    value = wl["p"] * (1 << wl["n"]) / step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl["desc"], "n": wl["n"], "m": wl["m"],
+                                        "p": wl["p"], "shots": wl["shots"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": sample.cores, "kind": "oracle",
+                         "sample": sample.desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - total_t0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_ours(args, wl):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2402_02585_gb300 import _capi as C
+    from paper_2402_02585_gb300 import core, instances
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    C.load()
+
+    n, m, p, shots = wl["n"], wl["m"], wl["p"], wl["shots"]
+    seed = wl["seed"] + rank
+    N = 1 << n
+    lits = instances.random_3sat(n, m, seed)
+    g_np, b_np = instances.random_angles(p, seed)
+    gam = torch.as_tensor(g_np, device=dev)
+    bet = torch.as_tensor(b_np, device=dev)
+
+    # caller-owned device buffers, allocated once
+    cost = torch.empty(N, dtype=torch.uint8, device=dev)
+    hist = torch.empty(m + 1, dtype=torch.int64, device=dev)
+    state = torch.empty(N, dtype=torch.complex64, device=dev)
+    out = torch.empty(3, dtype=torch.float64, device=dev)
+    shots_out = torch.empty(shots, dtype=torch.int64, device=dev)
+    ws_ev = core.workspace(C.gqaoa_evolve_workspace_size(n, p), dev)
+    ws_sa = core.workspace(C.gqaoa_sample_workspace_size(n, shots), dev)
+    lits_c = np.ascontiguousarray(lits, dtype=np.int32)
+    sh = stream.cuda_stream
+
+    ev_pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+
+    def step(pair=None):
+        C.gqaoa_build_cost(lits_c.ctypes.data, n, m, cost.data_ptr(), hist.data_ptr(), sh)
+        if pair:
+            pair[0].record(stream)
+        C.gqaoa_evolve(cost.data_ptr(), n, m, gam.data_ptr(), bet.data_ptr(), p, state.data_ptr(),
+                       out.data_ptr(), None, ws_ev.data_ptr(), ws_ev.numel(), 0, sh)
+        if pair:
+            pair[1].record(stream)
+        C.gqaoa_sample(state.data_ptr(), n, 12345, shots, shots_out.data_ptr(), ws_sa.data_ptr(),
+                       ws_sa.numel(), sh)
+
+    launches_per_step = 1 + (p + 3) + (6 if N >= 4096 else 1)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for i in range(args.steps):
+        step(ev_pairs[i])
+    stop.record(stream)
+    torch.cuda.synchronize(dev)
+    evolve_ms = [a.elapsed_time(b) for a, b in ev_pairs]
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed = start.elapsed_time(stop) / 1e3
+    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed = float(t.item())
+    units = p * N * args.steps * world
+    value = units / elapsed
+
+    # ---- end-to-end through the public API with host buffers -------------
+    h_g = torch.as_tensor(g_np).pin_memory()
+    h_b = torch.as_tensor(b_np).pin_memory()
+    h_shots = torch.empty(shots, dtype=torch.int64).pin_memory()
+    h_out = torch.empty(3, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        gam.copy_(h_g, non_blocking=True)
+        bet.copy_(h_b, non_blocking=True)
+        step()
+        h_out.copy_(out, non_blocking=True)
+        h_shots.copy_(shots_out, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_elapsed = time.perf_counter() - t0
+    te = torch.tensor([e2e_elapsed], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = units / float(te.item())
+    h2d = lits_c.nbytes + h_g.numel() * 8 + h_b.numel() * 8
+    d2h = h_shots.numel() * 8 + h_out.numel() * 8
+
+    # ---- roofline of the fused round (evolve call: p rounds + materialise) --
+    # algorithmic bytes: round 1 reads 1 B cost + writes 8 B; rounds 2..p read
+    # 8 B + 1 B and write 8 B; the materialise/readout pass reads 8 B + 1 B and
+    # writes 8 B.
+    alg_bytes = N * (9 + 17 * (p - 1) + 17)
+    ev_s = statistics.median(evolve_ms) / 1e3
+    achieved = alg_bytes / ev_s / 1e9
+    peak, peak_kind = hbm_peak()
+    traffic = profiled_traffic(n) if n == 28 else None
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and os.environ.get("GQAOA_BENCH_NO_CPU") != "1":
+            try:
+                osamp = OracleSample(wl)
+                v, _ = osamp.step()
+                cpu = {"value": v, "unit": UNIT, "cores": osamp.cores, "kind": "oracle",
+                       "sample": osamp.desc}
+            except Exception as exc:  # keep the GPU line even if the host run fails
+                cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                       "sample": f"failed: {exc!r}"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": n, "m": m, "p": p, "shots": shots,
+                       "parallelism": f"replicas x{world} (independent instances)",
+                       "l2": "inputs larger than L2 (2 GiB state, 256 MiB cost table)"
+                       if n >= 26 else "small case: L2-resident"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "round_kernel (K2) + materialise pass, per evolve call",
+                         "peak_kind": peak_kind,
+                         "evolve_ms": statistics.median(evolve_ms)},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "P0": float(out[0].item()),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,221 @@
+/*
+ * gqaoa.h - C ABI of the GB300 (sm_103a) Grover-QAOA statevector library.
+ *
+ * Method: Grover-mixer QAOA on random 3-SAT, arXiv:2402.02585
+ * ("Grover-QAOA for 3-SAT: Quadratic Speedup, Fair-Sampling, and Parameter
+ * Clustering", Zhang et al.). Section and equation numbers below refer to it.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Status: every function returns an int, GQAOA_OK (0) on success or a
+ *    negative GQAOA_E* code. No C++ exception and no abort crosses the ABI.
+ *    gqaoa_strerror() names a code.
+ *  - Ownership: the caller allocates and owns every buffer. The library never
+ *    allocates device memory; entry points that need scratch take a workspace
+ *    pointer and its size, and a *_workspace_size() function reports the
+ *    minimum. A workspace smaller than that is rejected with GQAOA_ENOMEM.
+ *  - Memory spaces: each pointer argument says "host" or "device". Device
+ *    pointers must be addresses in the current CUDA device's memory.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream). All
+ *    work is enqueued asynchronously on it; results written to device memory
+ *    are valid once the stream reaches that point. No entry point
+ *    synchronises, allocates or copies from the host after argument checks
+ *    (except gqaoa_build_cost, which passes the clause masks by value in the
+ *    kernel launch), so every call can be captured into a CUDA graph.
+ *  - Errors found by argument checks are returned before anything is
+ *    enqueued. A CUDA launch error is returned as GQAOA_ECUDA; the CUDA error
+ *    itself can be read with cudaGetLastError().
+ *  - Assignment index: z in [0, 2^n); bit j of z is Boolean variable x_j, and
+ *    bit value 1 means "true" (Appendix B: tau(x) = 1 satisfies literal x).
+ *  - Literals: DIMACS integers, +(v+1) for x_v and -(v+1) for NOT x_v.
+ *  - Complex state: complex64, interleaved (float re, float im), 8 bytes per
+ *    amplitude, index z. Alignment: 16 bytes.
+ *  - Sizes: 1 <= n <= GQAOA_MAX_N, 0 <= m <= GQAOA_MAX_M, 1 <= p.
+ */
+#ifndef GQAOA_H
+#define GQAOA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GQAOA_OK 0
+#define GQAOA_EINVAL (-1)   /* null pointer, bad literal, misaligned buffer */
+#define GQAOA_ERANGE (-2)   /* n, m, p or a count outside the supported range */
+#define GQAOA_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define GQAOA_ETIMEOUT (-4) /* a bounded device-side wait gave up */
+#define GQAOA_ENOMEM (-5)   /* the caller's workspace is smaller than required */
+
+#define GQAOA_MAX_N 34   /* 2^34 complex64 amplitudes = 128 GiB */
+#define GQAOA_MAX_M 255  /* the cost C(z) is stored in one byte */
+
+/* gqaoa_evolve flags */
+#define GQAOA_STATE_IN 1u /* `state` holds the initial state psi_0 on entry */
+
+/* gqaoa_grad objectives */
+#define GQAOA_OBJ_P0 0     /* P(C=0) = sum_{z: C(z)=0} |psi_p(z)|^2 */
+#define GQAOA_OBJ_ENERGY 1 /* <H_P> = sum_z C(z) |psi_p(z)|^2 (Eq. 4) */
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char *gqaoa_strerror(int status);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int gqaoa_version(void);
+
+/*
+ * Cost table and energy-manifold histogram (Section II.A, Eq. 1; Appendix B;
+ * Appendix C's "counting the states in each distinct energy manifold").
+ *
+ *   C(z) = number of clauses that assignment z leaves unsatisfied
+ *        = <z| H_P |z>,  H_P = sum_i H_C^(i)               (Eq. 1)
+ *   h[c] = #{ z : C(z) = c },  c = 0..m
+ *
+ * lits  host   int32 [m][3]  DIMACS literals; each |lit| in 1..n.
+ * n, m         1 <= n <= 34, 0 <= m <= 255.
+ * cost  device uint8 [2^n]   written: C(z).
+ * hist  device uint64 [m+1]  written: h[c]; may be NULL.
+ * Errors: GQAOA_EINVAL (NULL lits/cost, literal 0 or |lit| > n),
+ *         GQAOA_ERANGE (n, m out of range), GQAOA_ECUDA.
+ * The result is exact (integer arithmetic).
+ */
+int gqaoa_build_cost(const int32_t *lits, int n, int m, uint8_t *cost, uint64_t *hist,
+                     void *stream);
+
+/*
+ * Workspace bytes for gqaoa_evolve(n, p, ...). Writes *bytes.
+ * Errors: GQAOA_EINVAL (bytes NULL), GQAOA_ERANGE.
+ */
+int gqaoa_evolve_workspace_size(int n, int p, size_t *bytes);
+
+/*
+ * G-QAOA evolution (Section II.B, Eqs. 2-3):
+ *
+ *   psi_p = e^{-i beta_p H_M} e^{-i gamma_p H_P} ... e^{-i beta_1 H_M} e^{-i gamma_1 H_P} psi_0
+ *
+ * with H_M = |+><+| (Eq. 2), so each round is the diagonal phase
+ * chi(z) = e^{-i gamma_k C(z)} psi(z) followed by the rank-1 Grover mixer
+ * psi = chi + (e^{-i beta_k} - 1) <+|chi> |+>, whose coefficient needs a
+ * reduction over all 2^n amplitudes. psi_0 = |+> (uniform) unless
+ * flags & GQAOA_STATE_IN. The single-angle-pair protocol (Eq. 5) is the case
+ * gamma_k = gamma, beta_k = beta for all k.
+ *
+ * cost    device uint8 [2^n]     C(z) from gqaoa_build_cost; values <= m.
+ * n, m                           sizes as for gqaoa_build_cost.
+ * gammas  device double [p]      gamma_1..gamma_p (radians).
+ * betas   device double [p]      beta_1..beta_p (radians).
+ * p                              number of rounds, 1 <= p <= 2^20.
+ * state   device complex64 [2^n] written: psi_p. Read first as psi_0 when
+ *                                flags & GQAOA_STATE_IN. 16-byte aligned.
+ * out     device double [3]      written: P(C=0), <H_P>, sum |psi_p|^2 of the
+ *                                final state; may be NULL.
+ * trace   device double [p]      written: P(C=0) after each round; may be NULL.
+ * ws, ws_bytes  device workspace, at least gqaoa_evolve_workspace_size(n, p).
+ * flags                          0 or GQAOA_STATE_IN.
+ * Precision: complex64 state, phase factors e^{-i gamma c} evaluated in FP64
+ * and rounded to FP32; the mixer sum <+|chi> and every readout are FP64.
+ * Errors: GQAOA_EINVAL, GQAOA_ERANGE, GQAOA_ENOMEM, GQAOA_ECUDA.
+ */
+int gqaoa_evolve(const uint8_t *cost, int n, int m, const double *gammas, const double *betas,
+                 int p, void *state, double *out, double *trace, void *ws, size_t ws_bytes,
+                 unsigned flags, void *stream);
+
+/* Workspace bytes for gqaoa_prob(n, ...). */
+int gqaoa_prob_workspace_size(int n, size_t *bytes);
+
+/*
+ * Readout of a state (Eq. 4; Appendix B's solution probability):
+ *   out[0] = P(C=0) = sum_{z: C(z)=0} |psi(z)|^2
+ *   out[1] = <H_P>  = sum_z C(z) |psi(z)|^2
+ *   out[2] = sum_z |psi(z)|^2
+ * state device complex64 [2^n], cost device uint8 [2^n], out device double [3].
+ * Sums are FP64.
+ */
+int gqaoa_prob(const void *state, const uint8_t *cost, int n, double *out, void *ws,
+               size_t ws_bytes, void *stream);
+
+/* Workspace bytes for gqaoa_sample(n, shots, ...). */
+int gqaoa_sample_workspace_size(int n, int64_t shots, size_t *bytes);
+
+/*
+ * Fair sampling of measurement shots (Section IV, "sample all solutions";
+ * Section II.B: the Grover mixer weights every solution equally):
+ *   shot s = smallest z with CDF(z) > u_s * CDF(2^n - 1),
+ *   CDF(z) = sum_{y <= z} |psi(y)|^2 (FP64),
+ *   u_s    = uniform double in [0,1) from Philox4x32-10 (Salmon et al.,
+ *            SC 2011) with counter (s mod 2^32, s >> 32, 0, 0) and key
+ *            (seed mod 2^32, seed >> 32); the top 53 bits of the 64-bit word
+ *            (out1 << 32 | out0) scaled by 2^-53.
+ * state   device complex64 [2^n]; must have nonzero norm.
+ * seed    the Philox key.
+ * shots   0 <= shots <= 2^32.
+ * out_idx device uint64 [shots] written: z of each shot, in shot order.
+ * ws      device workspace of gqaoa_sample_workspace_size(n, shots) bytes.
+ */
+int gqaoa_sample(const void *state, int n, uint64_t seed, int64_t shots, uint64_t *out_idx,
+                 void *ws, size_t ws_bytes, void *stream);
+
+/* Workspace bytes for gqaoa_grad(n, p, ...): the per-round checkpoints of the
+ * state (p * 2^n * 8 bytes) plus reduction scratch. */
+int gqaoa_grad_workspace_size(int n, int p, size_t *bytes);
+
+/*
+ * Objective and adjoint gradient with respect to every angle of Eq. 3
+ * (Appendix C optimises the angles with a gradient method, L-BFGS-B):
+ *   objective GQAOA_OBJ_P0:     L = P(C=0)
+ *   objective GQAOA_OBJ_ENERGY: L = <H_P>  (Eq. 4)
+ * Forward: the rounds of gqaoa_evolve from |+>, storing each round's phased
+ * state chi_k = e^{-i gamma_k C} psi_{k-1} in the workspace (checkpoints).
+ * Backward, lambda_p = O psi_p and for k = p..1:
+ *   dL/dbeta_k   = 2 Re[-i e^{-i beta_k} (S_k / 2^n) conj(sum_z lambda_k)], S_k = sum_z chi_k
+ *   mu_k         = lambda_k + (e^{i beta_k} - 1) mean(lambda_k)
+ *   dL/dgamma_k  = 2 Re[ sum_z conj(mu_k) (-i C) chi_k ]
+ *   lambda_{k-1} = e^{+i gamma_k C} mu_k
+ * cost device uint8 [2^n]; gammas, betas device double [p];
+ * value  device double [1] written: L;
+ * dgamma, dbeta device double [p] written.
+ */
+int gqaoa_grad(const uint8_t *cost, int n, int m, const double *gammas, const double *betas,
+               int p, int objective, double *value, double *dgamma, double *dbeta, void *ws,
+               size_t ws_bytes, void *stream);
+
+/*
+ * Batched evolution of `batch` instances of equal n (Eq. 3 per instance).
+ * cost        device uint8: instance b's table at cost + b * cost_stride;
+ *             cost_stride = 2^n for one table per instance, 0 for one table
+ *             shared by every instance (e.g. many angle sets of one formula);
+ *             a multiple of 16 when n >= 12.
+ * gammas, betas device double [batch][p].
+ * state       device complex64 [batch][2^n] (in: psi_0 if GQAOA_STATE_IN; out: psi_p).
+ * out         device double [batch][3] or NULL; trace device double [batch][p] or NULL.
+ * ws          device workspace of gqaoa_evolve_batched_workspace_size(n, batch, p).
+ * Other arguments and errors as for gqaoa_evolve, plus GQAOA_ERANGE when
+ * batch < 1 or batch * p > 2^32.
+ */
+int gqaoa_evolve_batched_workspace_size(int n, int batch, int p, size_t *bytes);
+int gqaoa_evolve_batched(const uint8_t *cost, int64_t cost_stride, int n, int m, int batch,
+                         const double *gammas, const double *betas, int p, void *state,
+                         double *out, double *trace, void *ws, size_t ws_bytes, unsigned flags,
+                         void *stream);
+
+/*
+ * Batched objective and adjoint gradient of `batch` instances of equal n
+ * (same definitions as gqaoa_grad, per instance). cost and cost_stride as for
+ * gqaoa_evolve_batched; gammas, betas, dgamma, dbeta device double [batch][p];
+ * value device double [batch]. The workspace
+ * (gqaoa_grad_batched_workspace_size) holds p * batch * 2^n * 8 bytes of
+ * checkpoints.
+ */
+int gqaoa_grad_batched_workspace_size(int n, int batch, int p, size_t *bytes);
+int gqaoa_grad_batched(const uint8_t *cost, int64_t cost_stride, int n, int m, int batch,
+                       const double *gammas, const double *betas, int p, int objective,
+                       double *value, double *dgamma, double *dbeta, void *ws, size_t ws_bytes,
+                       void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GQAOA_H */

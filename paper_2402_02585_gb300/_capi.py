@@ -1,0 +1,166 @@
+"""ctypes binding of libgqaoa.so: the C ABI of include/gqaoa.h, same names.
+
+Arguments are plain integers (device or host addresses, sizes); every call
+returns the C status and a nonzero status raises GQAOAError. No computation
+happens here. If the library is missing the import of a function fails
+loudly: there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+GQAOA_OK = 0
+GQAOA_EINVAL = -1
+GQAOA_ERANGE = -2
+GQAOA_ECUDA = -3
+GQAOA_ETIMEOUT = -4
+GQAOA_ENOMEM = -5
+GQAOA_STATE_IN = 1
+GQAOA_OBJ_P0 = 0
+GQAOA_OBJ_ENERGY = 1
+GQAOA_MAX_N = 34
+GQAOA_MAX_M = 255
+
+
+class GQAOAError(RuntimeError):
+    def __init__(self, fn: str, status: int, msg: str):
+        super().__init__(f"{fn} failed with status {status}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_U64 = ctypes.c_uint64
+_SZ = ctypes.c_size_t
+_SZP = ctypes.POINTER(ctypes.c_size_t)
+_U = ctypes.c_uint
+
+# name -> argtypes (all return int status unless noted)
+SIGNATURES = {
+    "gqaoa_build_cost": [_P, _I, _I, _P, _P, _P],
+    "gqaoa_evolve_workspace_size": [_I, _I, _SZP],
+    "gqaoa_evolve": [_P, _I, _I, _P, _P, _I, _P, _P, _P, _P, _SZ, _U, _P],
+    "gqaoa_evolve_batched_workspace_size": [_I, _I, _I, _SZP],
+    "gqaoa_evolve_batched": [_P, _I64, _I, _I, _I, _P, _P, _I, _P, _P, _P, _P, _SZ, _U, _P],
+    "gqaoa_prob_workspace_size": [_I, _SZP],
+    "gqaoa_prob": [_P, _P, _I, _P, _P, _SZ, _P],
+    "gqaoa_sample_workspace_size": [_I, _I64, _SZP],
+    "gqaoa_sample": [_P, _I, _U64, _I64, _P, _P, _SZ, _P],
+    "gqaoa_grad_workspace_size": [_I, _I, _SZP],
+    "gqaoa_grad": [_P, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P],
+    "gqaoa_grad_batched_workspace_size": [_I, _I, _I, _SZP],
+    "gqaoa_grad_batched": [_P, _I64, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P],
+    "gqaoa_version": [],
+    "gqaoa_strerror": [_I],
+}
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libgqaoa.so (building it with nvcc first if it is absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path) or not _build.up_to_date():
+            if not build_if_missing:
+                raise RuntimeError(f"{path} is missing; run paper_2402_02585_gb300.build")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        for name, argtypes in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = argtypes
+            fn.restype = ctypes.c_char_p if name == "gqaoa_strerror" else ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def strerror(status: int) -> str:
+    return load().gqaoa_strerror(int(status)).decode()
+
+
+def _call(name: str, *args) -> None:
+    rc = getattr(load(), name)(*args)
+    if rc != GQAOA_OK:
+        raise GQAOAError(name, rc, strerror(rc))
+
+
+def _size(name: str, *args) -> int:
+    out = ctypes.c_size_t(0)
+    _call(name, *args, ctypes.byref(out))
+    return int(out.value)
+
+
+def gqaoa_version() -> int:
+    return int(load().gqaoa_version())
+
+
+def gqaoa_build_cost(lits, n, m, cost, hist, stream):
+    _call("gqaoa_build_cost", lits, n, m, cost, hist, stream)
+
+
+def gqaoa_evolve_workspace_size(n, p) -> int:
+    return _size("gqaoa_evolve_workspace_size", n, p)
+
+
+def gqaoa_evolve(cost, n, m, gammas, betas, p, state, out, trace, ws, ws_bytes, flags, stream):
+    _call("gqaoa_evolve", cost, n, m, gammas, betas, p, state, out, trace, ws, ws_bytes, flags,
+          stream)
+
+
+def gqaoa_evolve_batched_workspace_size(n, batch, p) -> int:
+    return _size("gqaoa_evolve_batched_workspace_size", n, batch, p)
+
+
+def gqaoa_evolve_batched(cost, cost_stride, n, m, batch, gammas, betas, p, state, out, trace, ws,
+                         ws_bytes, flags, stream):
+    _call("gqaoa_evolve_batched", cost, cost_stride, n, m, batch, gammas, betas, p, state, out,
+          trace, ws, ws_bytes, flags, stream)
+
+
+def gqaoa_prob_workspace_size(n) -> int:
+    return _size("gqaoa_prob_workspace_size", n)
+
+
+def gqaoa_prob(state, cost, n, out, ws, ws_bytes, stream):
+    _call("gqaoa_prob", state, cost, n, out, ws, ws_bytes, stream)
+
+
+def gqaoa_sample_workspace_size(n, shots) -> int:
+    return _size("gqaoa_sample_workspace_size", n, shots)
+
+
+def gqaoa_sample(state, n, seed, shots, out_idx, ws, ws_bytes, stream):
+    _call("gqaoa_sample", state, n, seed, shots, out_idx, ws, ws_bytes, stream)
+
+
+def gqaoa_grad_workspace_size(n, p) -> int:
+    return _size("gqaoa_grad_workspace_size", n, p)
+
+
+def gqaoa_grad(cost, n, m, gammas, betas, p, objective, value, dgamma, dbeta, ws, ws_bytes, stream):
+    _call("gqaoa_grad", cost, n, m, gammas, betas, p, objective, value, dgamma, dbeta, ws, ws_bytes,
+          stream)
+
+
+def gqaoa_grad_batched_workspace_size(n, batch, p) -> int:
+    return _size("gqaoa_grad_batched_workspace_size", n, batch, p)
+
+
+def gqaoa_grad_batched(cost, cost_stride, n, m, batch, gammas, betas, p, objective, value, dgamma,
+                       dbeta, ws, ws_bytes, stream):
+    _call("gqaoa_grad_batched", cost, cost_stride, n, m, batch, gammas, betas, p, objective, value,
+          dgamma, dbeta, ws, ws_bytes, stream)

@@ -1,0 +1,198 @@
+"""PyTorch-facing wrappers of the C ABI (argument marshalling only).
+
+Every function here allocates its outputs and workspace with torch on the
+current CUDA device, passes raw pointers and the current stream to
+libgqaoa.so, and returns torch tensors. All arithmetic happens in the CUDA
+kernels behind the C ABI; there is no CPU fallback.
+
+Conventions follow include/gqaoa.h: cost tables are uint8 [2^n], states are
+complex64 [2^n] (torch.complex64 has the interleaved (re, im) float layout
+the kernels use), angles are float64 on the device.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _capi as C
+
+OBJECTIVES = {"p0": C.GQAOA_OBJ_P0, "energy": C.GQAOA_OBJ_ENERGY}
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("tensor must live on a CUDA device")
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """Device scratch of at least nbytes (256-byte aligned by the allocator)."""
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def _angles(x, device) -> torch.Tensor:
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=torch.float64).contiguous()
+    return torch.as_tensor(np.asarray(x, dtype=np.float64), device=device).contiguous()
+
+
+def build_cost(lits, n: int, device=None, with_hist: bool = True):
+    """C(z) (uint8 [2^n]) and h[c] (int64 [m+1]) of a 3-SAT instance.
+
+    lits: int32 [m, 3] DIMACS literals on the host (numpy or CPU tensor).
+    """
+    lits = np.ascontiguousarray(np.asarray(lits, dtype=np.int32).reshape(-1, 3))
+    m = lits.shape[0]
+    device = torch.device(device or "cuda")
+    cost = torch.empty(1 << n, dtype=torch.uint8, device=device)
+    hist = torch.empty(m + 1, dtype=torch.int64, device=device) if with_hist else None
+    C.gqaoa_build_cost(lits.ctypes.data if m else None, n, m, _ptr(cost), _ptr(hist), _stream())
+    return cost, hist
+
+
+def evolve(cost: torch.Tensor, n: int, m: int, gammas, betas, state: torch.Tensor | None = None,
+           state_in: bool = False, trace: bool = False, ws: torch.Tensor | None = None):
+    """psi_p of Eq. 3. Returns (state complex64 [2^n], out float64 [3], trace or None)."""
+    _require_cuda(cost)
+    device = cost.device
+    g = _angles(gammas, device)
+    b = _angles(betas, device)
+    p = g.numel()
+    if state is None:
+        if state_in:
+            raise ValueError("state_in needs a state")
+        state = torch.empty(1 << n, dtype=torch.complex64, device=device)
+    out = torch.empty(3, dtype=torch.float64, device=device)
+    tr = torch.empty(p, dtype=torch.float64, device=device) if trace else None
+    need = C.gqaoa_evolve_workspace_size(n, p)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, device)
+    C.gqaoa_evolve(_ptr(cost), n, m, _ptr(g), _ptr(b), p, _ptr(state), _ptr(out), _ptr(tr),
+                   _ptr(ws), ws.numel(), C.GQAOA_STATE_IN if state_in else 0, _stream())
+    return state, out, tr
+
+
+def evolve_batched(cost: torch.Tensor, n: int, m: int, gammas, betas, shared_cost: bool = False,
+                   state: torch.Tensor | None = None, state_in: bool = False, trace: bool = False,
+                   ws: torch.Tensor | None = None):
+    """Batched Eq. 3. gammas, betas [B, p]; cost [B, 2^n] or [2^n] if shared_cost.
+    Returns (state [B, 2^n], out [B, 3], trace [B, p] or None)."""
+    _require_cuda(cost)
+    device = cost.device
+    g = _angles(gammas, device)
+    b = _angles(betas, device)
+    B, p = g.shape
+    if state is None:
+        state = torch.empty((B, 1 << n), dtype=torch.complex64, device=device)
+    out = torch.empty((B, 3), dtype=torch.float64, device=device)
+    tr = torch.empty((B, p), dtype=torch.float64, device=device) if trace else None
+    need = C.gqaoa_evolve_batched_workspace_size(n, B, p)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, device)
+    stride = 0 if shared_cost else (1 << n)
+    C.gqaoa_evolve_batched(_ptr(cost), stride, n, m, B, _ptr(g), _ptr(b), p, _ptr(state), _ptr(out),
+                           _ptr(tr), _ptr(ws), ws.numel(), C.GQAOA_STATE_IN if state_in else 0,
+                           _stream())
+    return state, out, tr
+
+
+def prob(state: torch.Tensor, cost: torch.Tensor, n: int, ws: torch.Tensor | None = None):
+    """[P(C=0), <H_P>, norm] of a state (float64 [3] on the device)."""
+    _require_cuda(state, cost)
+    out = torch.empty(3, dtype=torch.float64, device=state.device)
+    need = C.gqaoa_prob_workspace_size(n)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, state.device)
+    C.gqaoa_prob(_ptr(state), _ptr(cost), n, _ptr(out), _ptr(ws), ws.numel(), _stream())
+    return out
+
+
+def sample(state: torch.Tensor, n: int, seed: int, shots: int, ws: torch.Tensor | None = None,
+           out: torch.Tensor | None = None):
+    """Shots z ~ |psi(z)|^2 (int64 [shots] on the device)."""
+    _require_cuda(state)
+    if out is None:
+        out = torch.empty(int(shots), dtype=torch.int64, device=state.device)
+    need = C.gqaoa_sample_workspace_size(n, int(shots))
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, state.device)
+    C.gqaoa_sample(_ptr(state), n, int(seed) & 0xFFFFFFFFFFFFFFFF, int(shots), _ptr(out), _ptr(ws),
+                   ws.numel(), _stream())
+    return out
+
+
+def grad(cost: torch.Tensor, n: int, m: int, gammas, betas, objective: str = "p0",
+         ws: torch.Tensor | None = None):
+    """(L, dL/dgamma [p], dL/dbeta [p]) on the device, by the adjoint kernels."""
+    _require_cuda(cost)
+    device = cost.device
+    g = _angles(gammas, device)
+    b = _angles(betas, device)
+    p = g.numel()
+    value = torch.empty(1, dtype=torch.float64, device=device)
+    dg = torch.empty(p, dtype=torch.float64, device=device)
+    db = torch.empty(p, dtype=torch.float64, device=device)
+    need = C.gqaoa_grad_workspace_size(n, p)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, device)
+    C.gqaoa_grad(_ptr(cost), n, m, _ptr(g), _ptr(b), p, OBJECTIVES[objective], _ptr(value), _ptr(dg),
+                 _ptr(db), _ptr(ws), ws.numel(), _stream())
+    return value[0], dg, db
+
+
+def grad_batched(cost: torch.Tensor, n: int, m: int, gammas, betas, objective: str = "p0",
+                 shared_cost: bool = False, ws: torch.Tensor | None = None):
+    """Batched adjoint: value [B], dgamma [B, p], dbeta [B, p]."""
+    _require_cuda(cost)
+    device = cost.device
+    g = _angles(gammas, device)
+    b = _angles(betas, device)
+    B, p = g.shape
+    value = torch.empty(B, dtype=torch.float64, device=device)
+    dg = torch.empty((B, p), dtype=torch.float64, device=device)
+    db = torch.empty((B, p), dtype=torch.float64, device=device)
+    need = C.gqaoa_grad_batched_workspace_size(n, B, p)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, device)
+    stride = 0 if shared_cost else (1 << n)
+    C.gqaoa_grad_batched(_ptr(cost), stride, n, m, B, _ptr(g), _ptr(b), p, OBJECTIVES[objective],
+                         _ptr(value), _ptr(dg), _ptr(db), _ptr(ws), ws.numel(), _stream())
+    return value, dg, db
+
+
+class GQAOAObjective(torch.autograd.Function):
+    """L(gamma, beta) = P(C=0) or <H_P> of Eq. 3, differentiable in the angles.
+
+    forward runs the adjoint kernels once (forward passes with checkpoints,
+    then the backward passes) and keeps the gradient; backward scales it by
+    the incoming gradient. Works for one instance (angles [p]) or a batch of
+    equal-n instances (angles [B, p], cost [B, 2^n])."""
+
+    @staticmethod
+    def forward(ctx, gammas, betas, cost, n, m, objective="p0"):
+        if gammas.dim() == 1:
+            v, dg, db = grad(cost, n, m, gammas.detach(), betas.detach(), objective)
+        else:
+            v, dg, db = grad_batched(cost, n, m, gammas.detach(), betas.detach(), objective)
+        ctx.save_for_backward(dg, db)
+        return v.to(gammas.dtype)
+
+    @staticmethod
+    def backward(ctx, gout):
+        dg, db = ctx.saved_tensors
+        if dg.dim() == 2:
+            gout = gout.reshape(-1, 1)
+        return (gout * dg).to(dg.dtype), (gout * db).to(db.dtype), None, None, None, None
+
+
+def objective(gammas, betas, cost, n, m, objective="p0"):
+    return GQAOAObjective.apply(gammas, betas, cost, n, m, objective)

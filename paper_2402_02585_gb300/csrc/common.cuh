@@ -1,0 +1,153 @@
+// Shared device helpers of the G-QAOA CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gqaoa.h"
+
+namespace gq {
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+#define GQ_CHECK_LAUNCH()                                                      \
+  do {                                                                         \
+    if (cudaPeekAtLastError() != cudaSuccess) return GQAOA_ECUDA;              \
+  } while (0)
+
+#define GQ_CUDA(call)                                                          \
+  do {                                                                         \
+    if ((call) != cudaSuccess) return GQAOA_ECUDA;                             \
+  } while (0)
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+inline bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------
+// launch geometry of the streaming kernels
+// ---------------------------------------------------------------------------
+constexpr int kThreads = 256;          // threads per CTA
+constexpr int kWarps = kThreads / 32;  // warps per CTA
+constexpr int kVecPerThread = 8;       // float4 (2 amplitudes) per thread per tile
+constexpr int kWarpTileAmps = 32 * kVecPerThread * 2;  // 512 amplitudes
+constexpr int kTileAmps = kWarps * kWarpTileAmps;      // 4096 amplitudes per CTA tile
+constexpr int kTileLog2 = 12;
+constexpr int kClusterMax = 8;
+constexpr int kMaxParts = 4096;        // max partial records per reduction
+constexpr int kPartStride = 8;         // doubles per partial record
+
+// ---------------------------------------------------------------------------
+// small complex helpers (float2 = complex64, double2 = complex128)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Double-float accumulator: hi + lo carries ~48 significant bits, so the
+// running sum of many FP32 terms loses nothing measurable before it is
+// converted to FP64. It runs on the FP32 pipe, which matters on a part whose
+// FP64 rate is a small fraction of its FP32 rate.
+struct DF {
+  float hi, lo;
+  __device__ __forceinline__ void zero() { hi = 0.f; lo = 0.f; }
+  __device__ __forceinline__ void add(float x) {
+    float s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// ---------------------------------------------------------------------------
+// deterministic reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of one double per thread over the CTA in a fixed order; every thread
+// gets the result. `scratch` holds kWarps doubles; it is reused on return.
+__device__ __forceinline__ double block_sum(double v, double *scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) t += scratch[w];
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// thread-block cluster primitives (inline PTX; plain DSMEM loads, no multicast)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned cluster_ctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_nctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Load a double from the shared memory of CTA `rank` of this cluster at the
+// same offset as the local shared address `p`.
+__device__ __forceinline__ double ld_dsmem_f64(const double *p, unsigned rank) {
+  uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote) : "memory");
+  return v;
+}
+
+// Reduce `nvals` (<= kPartStride) per-CTA doubles held in shared `vals`
+// over the cluster and write one record to `out_rec` (global). Rank 0 sums
+// the CTAs in rank order. Must be called by all threads of every CTA.
+__device__ __forceinline__ void cluster_reduce_store(const double *vals, int nvals,
+                                                     double *out_rec) {
+  const unsigned cs = cluster_nctarank();
+  if (cs == 1) {
+    if (threadIdx.x < nvals) out_rec[threadIdx.x] = vals[threadIdx.x];
+    return;
+  }
+  cluster_sync();  // every CTA's vals visible cluster-wide
+  if (cluster_ctarank() == 0 && threadIdx.x < nvals) {
+    double acc = 0.0;
+    for (unsigned r = 0; r < cs; ++r) acc += ld_dsmem_f64(vals + threadIdx.x, r);
+    out_rec[threadIdx.x] = acc;
+  }
+  cluster_sync();  // keep every CTA's shared memory alive until rank 0 is done
+}
+
+// Sum slot `j` of `nparts` records of stride kPartStride, in index order
+// split over the CTA; every thread returns the same value in every CTA.
+__device__ __forceinline__ double sum_parts(const double *parts, int nparts, int j,
+                                            double *scratch) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += parts[(size_t)i * kPartStride + j];
+  return block_sum(v, scratch);
+}
+
+}  // namespace gq

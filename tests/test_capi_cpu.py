@@ -1,0 +1,117 @@
+"""C-ABI library checks that need no GPU: it loads, exports every declared
+symbol, sizes workspaces and rejects bad arguments before launching."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2402_02585_gb300 import _capi as C
+from paper_2402_02585_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fname in os.listdir(os.path.join(ROOT, "include")):
+        if fname.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fname)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(gqaoa_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(lib, s), s
+    # and the binding covers each of them
+    for s in syms:
+        assert s in C.SIGNATURES, s
+
+
+def test_version_and_strerror():
+    assert C.gqaoa_version() >= 100
+    for code in (0, -1, -2, -3, -4, -5):
+        assert C.strerror(code)
+    assert C.strerror(-99) == "unknown status"
+
+
+def test_workspace_sizes_monotone():
+    a = C.gqaoa_evolve_workspace_size(20, 10)
+    b = C.gqaoa_evolve_workspace_size(20, 100)
+    assert b > a > 0
+    g1 = C.gqaoa_grad_workspace_size(16, 4)
+    assert g1 >= 4 * (1 << 16) * 8
+    gb = C.gqaoa_grad_batched_workspace_size(16, 8, 4)
+    assert gb >= 8 * 4 * (1 << 16) * 8
+    s = C.gqaoa_sample_workspace_size(20, 1000)
+    assert s > 1000 * 4
+    assert C.gqaoa_prob_workspace_size(28) > 0
+
+
+@pytest.mark.parametrize("args,code", [
+    ((0, 10), C.GQAOA_ERANGE),
+    ((35, 10), C.GQAOA_ERANGE),
+    ((10, 0), C.GQAOA_ERANGE),
+])
+def test_workspace_size_ranges(args, code):
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_evolve_workspace_size(*args)
+    assert e.value.status == code
+
+
+def test_build_cost_rejects_bad_literals_before_launch():
+    lits = np.array([[1, 2, 9]], dtype=np.int32)  # |9| > n
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_build_cost(lits.ctypes.data, 4, 1, 16, None, None)
+    assert e.value.status == C.GQAOA_EINVAL
+    lits = np.array([[1, 0, 2]], dtype=np.int32)
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_build_cost(lits.ctypes.data, 4, 1, 16, None, None)
+    assert e.value.status == C.GQAOA_EINVAL
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_build_cost(lits.ctypes.data, 40, 1, 16, None, None)
+    assert e.value.status == C.GQAOA_ERANGE
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_build_cost(lits.ctypes.data, 4, 300, 16, None, None)
+    assert e.value.status == C.GQAOA_ERANGE
+
+
+def test_evolve_rejects_bad_arguments_before_launch():
+    fake = 1 << 20  # aligned non-null addresses; nothing is dereferenced
+    ws = C.gqaoa_evolve_workspace_size(12, 4)
+    cases = [
+        ((0, 12, 10, fake, fake, 4, fake, None, None, fake, ws, 0, None), C.GQAOA_EINVAL),  # null cost
+        ((fake, 12, 10, fake, fake, 0, fake, None, None, fake, ws, 0, None), C.GQAOA_ERANGE),  # p = 0
+        ((fake, 12, 10, fake, fake, 4, fake + 8, None, None, fake, ws, 0, None), C.GQAOA_EINVAL),
+        ((fake, 12, 10, fake, fake, 4, fake, None, None, fake, ws - 1, 0, None), C.GQAOA_ENOMEM),
+        ((fake, 12, 10, fake, fake, 4, fake, None, None, fake, ws, 4, None), C.GQAOA_EINVAL),  # flag
+        ((fake, 12, 256, fake, fake, 4, fake, None, None, fake, ws, 0, None), C.GQAOA_ERANGE),
+    ]
+    for args, code in cases:
+        with pytest.raises(C.GQAOAError) as e:
+            C.gqaoa_evolve(*args)
+        assert e.value.status == code, args
+
+
+def test_sample_and_grad_reject_bad_arguments_before_launch():
+    fake = 1 << 20
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_sample(fake, 20, 1, -1, fake, fake, 1 << 30, None)
+    assert e.value.status == C.GQAOA_ERANGE
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_sample(fake, 20, 1, 100, fake, fake, 16, None)
+    assert e.value.status == C.GQAOA_ENOMEM
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_grad(fake, 16, 60, fake, fake, 4, 7, fake, fake, fake, fake, 1 << 40, None)
+    assert e.value.status == C.GQAOA_EINVAL
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_grad(fake, 16, 60, fake, fake, 4, 0, fake, fake, fake, fake, 1024, None)
+    assert e.value.status == C.GQAOA_ENOMEM

@@ -1,0 +1,333 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: cost tables and histograms bit-exact; complex64 amplitudes within
+1e-5 max-abs and P(C=0) within 1e-6 absolute of the FP64 oracle; gradients
+within 2e-5 absolute (complex64 state, FP64 sums). Sizes span several
+4096-amplitude tiles and the single-CTA small-state path (n < 12).
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import reduced, statevector as sv
+from paper_2402_02585_gb300 import core, instances
+from tests.golden_io import paper_instances
+
+pytestmark = pytest.mark.gpu
+
+AMP_TOL = 1e-5
+P_TOL = 1e-6
+
+
+def gpu_cost(lits, n):
+    cost, hist = core.build_cost(lits, n)
+    torch.cuda.synchronize()
+    return cost, hist
+
+
+# ---------------------------------------------------------------- cost table
+
+@pytest.mark.parametrize("n,m,seed", [
+    (3, 1, 0), (4, 8, 1), (5, 21, 2), (8, 34, 3), (11, 46, 4),       # per-assignment kernel
+    (12, 50, 5), (13, 55, 6), (16, 67, 7), (18, 76, 8), (20, 84, 9),  # bit-sliced kernel
+    (12, 0, 10), (12, 255, 11), (14, 1, 12), (15, 9, 13),
+])
+def test_cost_table_bit_exact(n, m, seed):
+    lits = instances.random_3sat(n, m, seed)
+    cost, hist = gpu_cost(lits, n)
+    ref_cost, ref_hist = sv.cost_table(lits, n)
+    assert np.array_equal(cost.cpu().numpy(), ref_cost)
+    assert np.array_equal(hist.cpu().numpy().astype(np.uint64), ref_hist)
+
+
+def test_cost_table_paper_instances():
+    for inst in paper_instances():
+        cost, hist = gpu_cost(inst["lits"], inst["n"])
+        ref_cost, ref_hist = sv.cost_table(inst["lits"], inst["n"])
+        assert np.array_equal(cost.cpu().numpy(), ref_cost)
+        assert np.array_equal(hist.cpu().numpy().astype(np.uint64), ref_hist)
+
+
+def test_cost_table_high_variables_only():
+    # clauses touching only variables >= 5 exercise the word-constant branch
+    n = 14
+    lits = np.array([[6, -7, 8], [-9, 10, -14], [12, 13, -6]], dtype=np.int32)
+    cost, hist = gpu_cost(lits, n)
+    ref_cost, ref_hist = sv.cost_table(lits, n)
+    assert np.array_equal(cost.cpu().numpy(), ref_cost)
+    assert np.array_equal(hist.cpu().numpy().astype(np.uint64), ref_hist)
+
+
+def test_cost_table_without_histogram():
+    lits = instances.random_3sat(13, 50, 3)
+    cost, hist = core.build_cost(lits, 13, with_hist=False)
+    assert hist is None
+    assert np.array_equal(cost.cpu().numpy(), sv.cost_table(lits, 13)[0])
+
+
+# ---------------------------------------------------------------- evolution
+
+def check_state(psi_gpu, psi_ref):
+    err = np.max(np.abs(psi_gpu.cpu().numpy().astype(np.complex128) - psi_ref))
+    assert err < AMP_TOL, err
+
+
+@pytest.mark.parametrize("n,m,p,seed", [
+    (4, 8, 3, 0), (10, 42, 8, 0), (11, 46, 16, 1),   # single-CTA path
+    (12, 50, 8, 2), (13, 55, 12, 3), (16, 67, 20, 4), (18, 76, 10, 5),  # streaming path
+])
+def test_evolve_matches_oracle(n, m, p, seed):
+    lits = instances.random_3sat(n, m, seed)
+    g, b = instances.random_angles(p, seed)
+    cost, _ = gpu_cost(lits, n)
+    state, out, tr = core.evolve(cost, n, m, g, b, trace=True)
+    torch.cuda.synchronize()
+    ref_cost, _ = sv.cost_table(lits, n)
+    psi, ref_tr = sv.evolve(ref_cost, n, g, b, trace=True)
+    check_state(state, psi)
+    r = sv.readout(psi, ref_cost, n)
+    o = out.cpu().numpy()
+    assert abs(o[0] - r[0]) < P_TOL
+    assert abs(o[1] - r[1]) < 1e-5 * max(1.0, m / 8)
+    assert abs(o[2] - 1.0) < 1e-5
+    assert np.max(np.abs(tr.cpu().numpy() - ref_tr)) < P_TOL
+
+
+def test_config1_small_instance():
+    # n = 10, m = 42 (d = 4.2), seed 0, p = 8, angles uniform in [0, pi)
+    n, m, p = 10, 42, 8
+    lits = instances.random_3sat(n, m, 0)
+    g, b = instances.random_angles(p, 0)
+    cost, hist = gpu_cost(lits, n)
+    ref_cost, ref_hist = sv.cost_table(lits, n)
+    assert np.array_equal(cost.cpu().numpy(), ref_cost)
+    assert np.array_equal(hist.cpu().numpy().astype(np.uint64), ref_hist)
+    state, out, _ = core.evolve(cost, n, m, g, b)
+    psi = sv.evolve(ref_cost, n, g, b)
+    check_state(state, psi)
+    assert abs(out[0].item() - sv.readout(psi, ref_cost, n)[0]) < P_TOL
+
+
+@pytest.mark.parametrize("n", [9, 13])
+def test_evolve_from_given_state(n):
+    m, p = 4 * n, 6
+    lits = instances.random_3sat(n, m, 21)
+    g, b = instances.random_angles(p, 21)
+    psi0 = instances.random_state(n, 21)
+    cost, _ = gpu_cost(lits, n)
+    st = torch.as_tensor(psi0.astype(np.complex64)).cuda()
+    state, out, _ = core.evolve(cost, n, m, g, b, state=st, state_in=True)
+    ref_cost, _ = sv.cost_table(lits, n)
+    psi = sv.evolve(ref_cost, n, g, b, psi0=psi0.astype(np.complex64).astype(np.complex128))
+    check_state(state, psi)
+
+
+def test_special_cases_on_gpu():
+    n, m, p = 13, 52, 5
+    lits = instances.random_3sat(n, m, 31)
+    cost, hist = gpu_cost(lits, n)
+    h0 = hist[0].item() / (1 << n)
+    g, b = instances.random_angles(p, 31)
+    _, out, _ = core.evolve(cost, n, m, np.zeros(p), b)
+    assert abs(out[0].item() - h0) < P_TOL
+    _, out, _ = core.evolve(cost, n, m, g, np.zeros(p))
+    assert abs(out[0].item() - h0) < P_TOL
+    # Grover (Appendix A): one clause, gamma = beta = pi, C=1 weight sin^2((2k+1) theta)
+    one = np.array([[1, -2, 3]], dtype=np.int32)
+    cost1, hist1 = gpu_cost(one, n)
+    theta = math.asin(math.sqrt(hist1[1].item() / (1 << n)))
+    for k in (1, 3, 7):
+        _, out, _ = core.evolve(cost1, n, 1, [math.pi] * k, [math.pi] * k)
+        assert abs(out[1].item() - math.sin((2 * k + 1) * theta) ** 2) < 1e-5
+
+
+def test_reduced_model_at_every_amplitude():
+    n, m, p = 16, 67, 24
+    lits = instances.random_3sat(n, m, 41)
+    g, b = instances.random_angles(p, 41)
+    cost, hist = gpu_cost(lits, n)
+    state, out, _ = core.evolve(cost, n, m, g, b)
+    f = reduced.evolve(hist.cpu().numpy(), g, b)
+    ref_cost, _ = sv.cost_table(lits, n)
+    check_state(state, reduced.amplitudes(f, ref_cost))
+    assert abs(out[0].item() - reduced.readout(hist.cpu().numpy(), f)[0]) < P_TOL
+
+
+def test_prob_readout():
+    for n in (10, 14):
+        m = 4 * n
+        lits = instances.random_3sat(n, m, 51)
+        psi0 = instances.random_state(n, 51).astype(np.complex64)
+        cost, _ = gpu_cost(lits, n)
+        out = core.prob(torch.as_tensor(psi0).cuda(), cost, n).cpu().numpy()
+        ref = sv.readout(psi0.astype(np.complex128), sv.cost_table(lits, n)[0], n)
+        assert np.allclose(out, ref, atol=1e-6, rtol=1e-6)
+
+
+def test_evolve_batched_matches_per_instance():
+    n, p, B = 13, 7, 5
+    ms = [40, 52, 55, 60, 65]
+    m = max(ms)
+    costs, refs = [], []
+    for i in range(B):
+        lits = instances.random_3sat(n, ms[i], 100 + i)
+        c, _ = gpu_cost(lits, n)
+        costs.append(c)
+        refs.append(sv.cost_table(lits, n)[0])
+    cost = torch.stack(costs)
+    G = np.stack([instances.random_angles(p, 200 + i)[0] for i in range(B)])
+    Bt = np.stack([instances.random_angles(p, 200 + i)[1] for i in range(B)])
+    state, out, tr = core.evolve_batched(cost, n, m, G, Bt, trace=True)
+    torch.cuda.synchronize()
+    for i in range(B):
+        psi, rtr = sv.evolve(refs[i], n, G[i], Bt[i], trace=True)
+        check_state(state[i], psi)
+        assert abs(out[i, 0].item() - sv.readout(psi, refs[i], n)[0]) < P_TOL
+        assert np.max(np.abs(tr[i].cpu().numpy() - rtr)) < P_TOL
+
+
+@pytest.mark.parametrize("n", [8, 12])
+def test_evolve_batched_shared_cost(n):
+    # one formula, many angle sets: the single-angle-pair grid of Eq. 5
+    m, p = 4 * n, 6
+    lits = instances.random_3sat(n, m, 61)
+    cost, hist = gpu_cost(lits, n)
+    grid = [(gi * math.pi / 4, bj * math.pi / 4) for gi in range(4) for bj in range(4)]
+    G = np.array([[gg] * p for gg, _ in grid])
+    Bt = np.array([[bb] * p for _, bb in grid])
+    _, out, _ = core.evolve_batched(cost, n, m, G, Bt, shared_cost=True)
+    h = hist.cpu().numpy()
+    for i in range(len(grid)):
+        ref = reduced.readout(h, reduced.evolve(h, G[i], Bt[i]))
+        assert abs(out[i, 0].item() - ref[0]) < P_TOL
+
+
+# ---------------------------------------------------------------- sampling
+
+def check_shots_valid(shots, psi_ref, seed, tol):
+    """Every shot z must satisfy CDF(z-1) - tol <= u * total <= CDF(z) + tol."""
+    cdf = np.cumsum(np.abs(psi_ref) ** 2)
+    total = cdf[-1]
+    u = np.array([sv.shot_uniform(seed, s) for s in range(len(shots))])
+    t = u * total
+    lo = np.where(shots > 0, cdf[np.maximum(shots - 1, 0)], 0.0)
+    hi = cdf[shots]
+    assert np.all(lo - tol <= t) and np.all(t <= hi + tol)
+
+
+@pytest.mark.parametrize("n,shots", [(6, 3000), (10, 20000), (12, 20000), (15, 50000)])
+def test_sample_matches_oracle(n, shots):
+    m, p, seed = 4 * n, 5, 71
+    lits = instances.random_3sat(n, m, seed)
+    g, b = instances.random_angles(p, seed)
+    cost, _ = gpu_cost(lits, n)
+    state, _, _ = core.evolve(cost, n, m, g, b)
+    got = core.sample(state, n, seed=1234, shots=shots).cpu().numpy()
+    psi = sv.evolve(sv.cost_table(lits, n)[0], n, g, b)
+    ref = sv.sample(psi, n, seed=1234, shots=shots).astype(np.int64)
+    # same uniforms (Philox on both sides); complex64 vs complex128 state may
+    # move a shot that lies within rounding of a CDF boundary
+    assert np.mean(got == ref) > 0.999
+    check_shots_valid(got, psi, 1234, tol=1e-5)
+
+
+def test_sample_fair_over_solutions():
+    import scipy.stats
+    n, m, p = 16, 56, 12
+    for seed in range(200, 260):
+        lits = instances.random_3sat(n, m, seed)
+        if sv.histogram(lits, n)[0] >= 8:
+            break
+    g, b = instances.random_angles(p, seed)
+    cost, hist = gpu_cost(lits, n)
+    state, out, _ = core.evolve(cost, n, m, g, b)
+    shots = core.sample(state, n, seed=5, shots=200000)
+    c = cost[shots].cpu().numpy()
+    z = shots.cpu().numpy()
+    sol = z[c == 0]
+    counts = np.bincount(sol, minlength=1 << n)[np.flatnonzero(sv.cost_table(lits, n)[0] == 0)]
+    # uniform over the solutions (fair sampling, Section IV)
+    stat = np.sum((counts - counts.mean()) ** 2 / counts.mean())
+    assert scipy.stats.chi2.sf(stat, len(counts) - 1) > 1e-4
+    # weight per cost class matches h[c] |f_p(c)|^2
+    h = hist.cpu().numpy()
+    f = reduced.evolve(h, g, b)
+    w = h * np.abs(f) ** 2
+    obs = np.bincount(c, minlength=len(h))
+    exp = w * len(c)
+    keep = exp > 5
+    stat = np.sum((obs[keep] - exp[keep]) ** 2 / exp[keep])
+    assert scipy.stats.chi2.sf(stat, keep.sum() - 1) > 1e-4
+
+
+def test_sample_zero_shots_and_point_mass():
+    n = 13
+    st = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+    st[777] = 1.0
+    got = core.sample(st, n, seed=3, shots=1000).cpu().numpy()
+    assert np.all(got == 777)
+    st[777] = 0.0
+    st[(1 << n) - 1] = 1.0  # last amplitude only
+    got = core.sample(st, n, seed=4, shots=1000).cpu().numpy()
+    assert np.all(got == (1 << n) - 1)
+    assert core.sample(st, n, seed=4, shots=0).numel() == 0
+
+
+# ---------------------------------------------------------------- gradients
+
+@pytest.mark.parametrize("n,m,p,obj", [(9, 38, 4, "p0"), (10, 42, 6, "energy"),
+                                       (13, 55, 5, "p0"), (14, 60, 4, "energy")])
+def test_grad_matches_reduced_adjoint_and_fd(n, m, p, obj):
+    lits = instances.random_3sat(n, m, 81)
+    g, b = instances.random_angles(p, 81)
+    cost, hist = gpu_cost(lits, n)
+    v, dg, db = core.grad(cost, n, m, g, b, obj)
+    h = hist.cpu().numpy()
+    code = reduced.OBJ_P0 if obj == "p0" else reduced.OBJ_ENERGY
+    L, rdg, rdb = reduced.grad(h, g, b, code)
+    scale = 1.0 if obj == "p0" else m / 8
+    assert abs(v.item() - L) < 1e-6 * scale
+    assert np.max(np.abs(dg.cpu().numpy() - rdg)) < 2e-5 * scale
+    assert np.max(np.abs(db.cpu().numpy() - rdb)) < 2e-5 * scale
+    fg, fb = reduced.fd_grad(h, g, b, code, step=1e-4)
+    assert np.max(np.abs(dg.cpu().numpy() - fg)) < 5e-5 * scale
+    assert np.max(np.abs(db.cpu().numpy() - fb)) < 5e-5 * scale
+
+
+def test_grad_batched_and_autograd():
+    n, m, p, B = 12, 50, 5, 4
+    costs, hists = [], []
+    for i in range(B):
+        c, h = gpu_cost(instances.random_3sat(n, m, 300 + i), n)
+        costs.append(c)
+        hists.append(h.cpu().numpy())
+    cost = torch.stack(costs)
+    G = torch.tensor(np.stack([instances.random_angles(p, 400 + i)[0] for i in range(B)]),
+                     device="cuda", requires_grad=True)
+    Bt = torch.tensor(np.stack([instances.random_angles(p, 400 + i)[1] for i in range(B)]),
+                      device="cuda", requires_grad=True)
+    val = core.objective(G, Bt, cost, n, m, "p0")
+    val.sum().backward()
+    for i in range(B):
+        L, rdg, rdb = reduced.grad(hists[i], G[i].detach().cpu().numpy(), Bt[i].detach().cpu().numpy())
+        assert abs(val[i].item() - L) < 1e-6
+        assert np.max(np.abs(G.grad[i].cpu().numpy() - rdg)) < 2e-5
+        assert np.max(np.abs(Bt.grad[i].cpu().numpy() - rdb)) < 2e-5
+
+
+def test_single_angle_gradient_is_round_sum():
+    n, m, p = 12, 50, 8
+    lits = instances.random_3sat(n, m, 91)
+    cost, hist = gpu_cost(lits, n)
+    gam, bet = 0.37, 2.1
+    _, dg, db = core.grad(cost, n, m, [gam] * p, [bet] * p)
+    h = hist.cpu().numpy()
+    eps = 1e-5
+    fg = (reduced.objective_value(h, [gam + eps] * p, [bet] * p)
+          - reduced.objective_value(h, [gam - eps] * p, [bet] * p)) / (2 * eps)
+    fb = (reduced.objective_value(h, [gam] * p, [bet + eps] * p)
+          - reduced.objective_value(h, [gam] * p, [bet - eps] * p)) / (2 * eps)
+    assert abs(dg.sum().item() - fg) < 1e-4 and abs(db.sum().item() - fb) < 1e-4
