@@ -42,6 +42,9 @@ WORKLOADS = {
                   desc="random 3-SAT n=28 m=118 (d~4.2) seed 0, p=100 random angles, 1e6 shots"),
     "small": dict(n=10, m=42, p=8, shots=10_000, seed=0,
                   desc="random 3-SAT n=10 m=42 (d=4.2) seed 0, p=8 random angles, 1e4 shots"),
+    # the profiling case: same recipe, state (512 MiB) still far larger than L2
+    "profile": dict(n=26, m=109, p=8, shots=100_000, seed=0,
+                    desc="random 3-SAT n=26 m=109 (d~4.2) seed 0, p=8 random angles, 1e5 shots"),
 }
 METRIC = "G-QAOA amp-rounds/s"
 UNIT = "amp-rounds/s"
@@ -51,7 +54,7 @@ PEAK_FALLBACK_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
@@ -67,7 +70,7 @@ def dist_env():
 
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples during the timed region (200 ms period)."""
+    """nvidia-smi samples during the timed region (100 ms period)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -82,7 +85,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
