@@ -214,6 +214,30 @@ int gqaoa_grad_batched(const uint8_t *cost, int64_t cost_stride, int n, int m, i
                        double *value, double *dgamma, double *dbeta, void *ws, size_t ws_bytes,
                        void *stream);
 
+/*
+ * gqaoa_evolve without a workspace, for callers that cannot allocate device
+ * memory or pass scratch: a plugin behind a fixed interface that hands over
+ * only inputs and outputs, code inside a framework that owns all device
+ * memory, or code issuing work while a stream is captured in the global
+ * capture mode (where cudaMalloc is refused). The paper has no counterpart;
+ * this is a calling convention of this library only.
+ *
+ * Same arguments, results and errors as gqaoa_evolve, minus ws/ws_bytes.
+ * Scratch: one file-scope device array of GQAOA_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits. p is limited
+ * to 1..GQAOA_NOALLOC_MAX_P (GQAOA_ERANGE beyond). The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make it before any stream capture. All calls on a
+ * device share the array: calls whose GPU work overlaps race and must be
+ * serialised by the caller. No scratch word needs to start at zero; the
+ * contents left by a previous call are overwritten before use.
+ */
+#define GQAOA_NOALLOC_MAX_P 256
+#define GQAOA_NOALLOC_SCRATCH_BYTES (1u << 20) /* 1 MiB */
+int gqaoa_evolve_noalloc(const uint8_t *cost, int n, int m, const double *gammas,
+                         const double *betas, int p, void *state, double *out, double *trace,
+                         unsigned flags, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -59,6 +59,7 @@ SIGNATURES = {
     "gqaoa_grad": [_P, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P],
     "gqaoa_grad_batched_workspace_size": [_I, _I, _I, _SZP],
     "gqaoa_grad_batched": [_P, _I64, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P],
+    "gqaoa_evolve_noalloc": [_P, _I, _I, _P, _P, _I, _P, _P, _P, _U, _P],
     "gqaoa_version": [],
     "gqaoa_strerror": [_I],
 }
@@ -164,3 +165,9 @@ def gqaoa_grad_batched(cost, cost_stride, n, m, batch, gammas, betas, p, objecti
                        dbeta, ws, ws_bytes, stream):
     _call("gqaoa_grad_batched", cost, cost_stride, n, m, batch, gammas, betas, p, objective, value,
           dgamma, dbeta, ws, ws_bytes, stream)
+
+
+def gqaoa_evolve_noalloc(cost, n, m, gammas, betas, p, state, out, trace, flags, stream):
+    """gqaoa_evolve with the library's fixed static scratch instead of a
+    caller workspace (for callers that cannot allocate device memory)."""
+    _call("gqaoa_evolve_noalloc", cost, n, m, gammas, betas, p, state, out, trace, flags, stream)
