@@ -144,7 +144,7 @@ def kernel_source_hash() -> str:
 def profiled_traffic(n: int):
     """dram bytes per round-kernel launch from the committed ncu summary, if it
     was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "round_kernel_n28.md")
+    path = os.path.join(ROOT, "profiles", "round_kernel.md")
     try:
         text = open(path).read()
     except OSError:
@@ -367,7 +367,8 @@ def run_ours(args, wl):
                        if n >= 26 else "small case: L2-resident"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "round_kernel (K2) + materialise pass, per evolve call",
+                         "alg_bytes_per_launch": 17 * N,
+                         "kernel": "round_kernel (K2): mean over the p+1 streaming passes of the evolve call",
                          "peak_kind": peak_kind,
                          "evolve_ms": statistics.median(evolve_ms)},
             "cpu_baseline": cpu,
