@@ -214,6 +214,51 @@ int gqaoa_grad_batched(const uint8_t *cost, int64_t cost_stride, int n, int m, i
                        double *value, double *dgamma, double *dbeta, void *ws, size_t ws_bytes,
                        void *stream);
 
+/* ------------------------------------------------------------------------
+ * Learned angle proposer (K9). The paper observes that optimal angles
+ * cluster with the instance size and clause count (Section III.B, Fig. 2;
+ * Appendix D) and proposes deriving angles from statistics of the density of
+ * states (Section V). The proposer is an MLP on the normalised cost
+ * histogram:
+ *   x = [h[c]/2^n for c = 0..d_in-3 (zero-padded), n/32, m/128]
+ *   z1 = W1 x + b1, h1 = GELU(z1); z2 = W2 h1 + b2, h2 = GELU(z2);
+ *   o = W3 h2 + b3; angles = 2 pi sigmoid(o) (d_out = 2p: p gammas, p betas)
+ *   loss = mean over batch and outputs of (angles - labels)^2
+ * GELU(x) = x Phi(x), exact normal CDF. FP32 throughout (loss in FP64).
+ * params: device float, one flat vector [W1 (d_h x d_in), b1, W2 (d_h x d_h),
+ * b2, W3 (d_out x d_h), b3], row-major. x: device float [batch][d_in].
+ * ------------------------------------------------------------------------ */
+int gqaoa_mlp_param_count(int d_in, int d_h, int d_out, size_t *count);
+/* Activation workspace for a batch (both forward and backward). */
+int gqaoa_mlp_workspace_size(int batch, int d_in, int d_h, int d_out, size_t *bytes);
+/* angles: device float [batch][d_out] written. */
+int gqaoa_mlp_forward(const float *params, int d_in, int d_h, int d_out, const float *x,
+                      int batch, float *angles, void *ws, size_t ws_bytes, void *stream);
+/* Forward + backward of the MSE loss against labels (device float
+ * [batch][d_out]); grads: device float [param_count] written; loss: device
+ * double [1] written. */
+int gqaoa_mlp_backward(const float *params, int d_in, int d_h, int d_out, const float *x,
+                       const float *labels, int batch, float *grads, double *loss, void *ws,
+                       size_t ws_bytes, void *stream);
+/* Features from histograms: hist device int64 [batch][hist_stride] (h[c] for
+ * c <= m_b), ns, ms device int32 [batch]; x device float [batch][d_in]. */
+int gqaoa_mlp_features(const int64_t *hist, int hist_stride, const int32_t *ns, const int32_t *ms,
+                       int batch, int d_in, float *x, void *stream);
+
+/*
+ * Adam (Kingma and Ba, 2015) on `count` device values, in place:
+ *   g' = grad_scale * g; m = b1 m + (1-b1) g'; v = b2 v + (1-b2) g'^2;
+ *   p -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps)
+ * step >= 1 is the 1-based update count. grad_scale = -1 maximises.
+ * Used for the proposer's weights (f32) and for G-QAOA angles (f64).
+ */
+int gqaoa_adam_f32(float *params, const float *grads, float *m, float *v, int64_t count,
+                   double lr, double beta1, double beta2, double eps, int step, double grad_scale,
+                   void *stream);
+int gqaoa_adam_f64(double *params, const double *grads, double *m, double *v, int64_t count,
+                   double lr, double beta1, double beta2, double eps, int step, double grad_scale,
+                   void *stream);
+
 /*
  * gqaoa_evolve without a workspace, for callers that cannot allocate device
  * memory or pass scratch: a plugin behind a fixed interface that hands over

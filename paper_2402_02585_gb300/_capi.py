@@ -43,6 +43,7 @@ _U64 = ctypes.c_uint64
 _SZ = ctypes.c_size_t
 _SZP = ctypes.POINTER(ctypes.c_size_t)
 _U = ctypes.c_uint
+_D = ctypes.c_double
 
 # name -> argtypes (all return int status unless noted)
 SIGNATURES = {
@@ -60,6 +61,13 @@ SIGNATURES = {
     "gqaoa_grad_batched_workspace_size": [_I, _I, _I, _SZP],
     "gqaoa_grad_batched": [_P, _I64, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P],
     "gqaoa_evolve_noalloc": [_P, _I, _I, _P, _P, _I, _P, _P, _P, _U, _P],
+    "gqaoa_mlp_param_count": [_I, _I, _I, _SZP],
+    "gqaoa_mlp_workspace_size": [_I, _I, _I, _I, _SZP],
+    "gqaoa_mlp_forward": [_P, _I, _I, _I, _P, _I, _P, _P, _SZ, _P],
+    "gqaoa_mlp_backward": [_P, _I, _I, _I, _P, _P, _I, _P, _P, _P, _SZ, _P],
+    "gqaoa_mlp_features": [_P, _I, _P, _P, _I, _I, _P, _P],
+    "gqaoa_adam_f32": [_P, _P, _P, _P, _I64, _D, _D, _D, _D, _I, _D, _P],
+    "gqaoa_adam_f64": [_P, _P, _P, _P, _I64, _D, _D, _D, _D, _I, _D, _P],
     "gqaoa_version": [],
     "gqaoa_strerror": [_I],
 }
@@ -165,6 +173,38 @@ def gqaoa_grad_batched(cost, cost_stride, n, m, batch, gammas, betas, p, objecti
                        dbeta, ws, ws_bytes, stream):
     _call("gqaoa_grad_batched", cost, cost_stride, n, m, batch, gammas, betas, p, objective, value,
           dgamma, dbeta, ws, ws_bytes, stream)
+
+
+def gqaoa_mlp_param_count(d_in, d_h, d_out) -> int:
+    return _size("gqaoa_mlp_param_count", d_in, d_h, d_out)
+
+
+def gqaoa_mlp_workspace_size(batch, d_in, d_h, d_out) -> int:
+    return _size("gqaoa_mlp_workspace_size", batch, d_in, d_h, d_out)
+
+
+def gqaoa_mlp_forward(params, d_in, d_h, d_out, x, batch, angles, ws, ws_bytes, stream):
+    _call("gqaoa_mlp_forward", params, d_in, d_h, d_out, x, batch, angles, ws, ws_bytes, stream)
+
+
+def gqaoa_mlp_backward(params, d_in, d_h, d_out, x, labels, batch, grads, loss, ws, ws_bytes,
+                       stream):
+    _call("gqaoa_mlp_backward", params, d_in, d_h, d_out, x, labels, batch, grads, loss, ws,
+          ws_bytes, stream)
+
+
+def gqaoa_mlp_features(hist, hist_stride, ns, ms, batch, d_in, x, stream):
+    _call("gqaoa_mlp_features", hist, hist_stride, ns, ms, batch, d_in, x, stream)
+
+
+def gqaoa_adam_f32(params, grads, m, v, count, lr, beta1, beta2, eps, step, grad_scale, stream):
+    _call("gqaoa_adam_f32", params, grads, m, v, count, lr, beta1, beta2, eps, step, grad_scale,
+          stream)
+
+
+def gqaoa_adam_f64(params, grads, m, v, count, lr, beta1, beta2, eps, step, grad_scale, stream):
+    _call("gqaoa_adam_f64", params, grads, m, v, count, lr, beta1, beta2, eps, step, grad_scale,
+          stream)
 
 
 def gqaoa_evolve_noalloc(cost, n, m, gammas, betas, p, state, out, trace, flags, stream):

@@ -140,3 +140,25 @@ def random_state(n: int, seed: int) -> np.ndarray:
     r = np.sqrt(-2.0 * np.log(u1))
     z = r * np.cos(2 * np.pi * u2) + 1j * r * np.sin(2 * np.pi * u2)
     return z / np.linalg.norm(z)
+
+
+def mlp_dims(p: int = 16, d_in: int = 130, d_hidden: int = 256) -> tuple[int, int, int]:
+    """(d_in, d_hidden, d_out) of the angle proposer: d_out = 2p (p gammas, p betas)."""
+    return d_in, d_hidden, 2 * p
+
+
+def mlp_param_count(d_in: int, d_h: int, d_out: int) -> int:
+    return d_h * d_in + d_h + d_h * d_h + d_h + d_out * d_h + d_out
+
+
+def random_mlp_params(d_in: int, d_h: int, d_out: int, seed: int) -> np.ndarray:
+    """Flat float32 parameters [W1 (d_h x d_in), b1, W2 (d_h x d_h), b2, W3 (d_out x d_h), b3],
+    weights uniform in +-sqrt(1/fan_in) (the usual fully-connected initialisation), biases 0."""
+    bg = _raw(seed, 4)
+    out = []
+    for fan_out, fan_in in ((d_h, d_in), (d_h, d_h), (d_out, d_h)):
+        lim = np.sqrt(1.0 / fan_in)
+        w = (2.0 * _unit(bg, fan_out * fan_in) - 1.0) * lim
+        out.append(w.astype(np.float32))
+        out.append(np.zeros(fan_out, dtype=np.float32))
+    return np.concatenate(out)

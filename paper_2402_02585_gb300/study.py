@@ -1,0 +1,147 @@
+"""The learned-initialisation study: labels from the batched optimizer, the
+proposer trained on them, and the comparison with the plain optimizer.
+
+Pipeline (every numerical step runs in the library's kernels):
+  1. instances: random 3-SAT (n, d drawn per instance), cost tables and
+     histograms by gqaoa_build_cost; only satisfiable ones (h[0] > 0) kept,
+     as the paper does for its solution-probability study (Section III).
+  2. labels: per instance the best single angle pair on a grid (Eq. 5;
+     batched evolution with a shared cost table), then Adam over all 2p angles
+     with the adjoint gradient of P(C=0) (Appendix C's grid-then-local-search
+     protocol with Adam in place of L-BFGS-B), canonicalised.
+  3. the proposer is fit to (features, labels).
+  4. evaluation on held-out instances: the plain optimizer from random angles
+     sets the target (95 % of its final P); the same optimizer started from
+     the proposal is timed to that target; an instance whose proposed start
+     never reaches it falls back to the plain run.
+"""
+
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import torch
+
+from . import _capi as C
+from . import core, instances
+from .optim import AngleOptimizer, canonicalize, single_angle_grid_start
+
+CKPT_BUDGET_BYTES = 8 << 30
+
+
+def make_instances(count: int, seed: int, n_values, d_lo: float, d_hi: float,
+                   sat_only: bool = True, device="cuda"):
+    """List of dicts (n, m, lits, cost [2^n] on the device, hist numpy)."""
+    out = []
+    shapes = instances.uniform_density_shapes(count * 4 + 16, seed, n_values, d_lo, d_hi)
+    for i, (n, m, _) in enumerate(shapes):
+        lits = instances.random_3sat(n, m, seed * 1_000_003 + i)
+        cost, hist = core.build_cost(lits, n, device=device)
+        h = hist.cpu().numpy()
+        if sat_only and h[0] == 0:
+            continue
+        out.append({"n": n, "m": m, "lits": lits, "cost": cost, "hist": h})
+        if len(out) >= count:
+            break
+    return out
+
+
+def features(insts, d_in: int = 130, device="cuda") -> torch.Tensor:
+    B = len(insts)
+    stride = max(len(it["hist"]) for it in insts)
+    H = np.zeros((B, stride), dtype=np.int64)
+    for i, it in enumerate(insts):
+        H[i, :len(it["hist"])] = it["hist"]
+    Hd = torch.as_tensor(H, device=device)
+    nd = torch.as_tensor(np.array([it["n"] for it in insts], dtype=np.int32), device=device)
+    md = torch.as_tensor(np.array([it["m"] for it in insts], dtype=np.int32), device=device)
+    x = torch.empty((B, d_in), dtype=torch.float32, device=device)
+    C.gqaoa_mlp_features(Hd.data_ptr(), stride, nd.data_ptr(), md.data_ptr(), B, d_in, x.data_ptr(),
+                         torch.cuda.current_stream().cuda_stream)
+    return x
+
+
+def _groups(insts, p):
+    """Indices grouped by n, chunked so the checkpoints fit the budget."""
+    by_n: dict[int, list[int]] = {}
+    for i, it in enumerate(insts):
+        by_n.setdefault(it["n"], []).append(i)
+    for n in sorted(by_n):
+        idx = by_n[n]
+        per = max(1, CKPT_BUDGET_BYTES // (p * (1 << n) * 8))
+        for s in range(0, len(idx), per):
+            yield n, idx[s:s + per]
+
+
+def generate_labels(insts, p: int, grid: int = 16, steps: int = 150, lr: float = 0.05,
+                    d_in: int = 130):
+    """(X [B, d_in] float32, Y [B, 2p] float32) on the device."""
+    labels = np.zeros((len(insts), 2 * p))
+    for n, idx in _groups(insts, p):
+        cost = torch.stack([insts[i]["cost"] for i in idx])
+        m = max(insts[i]["m"] for i in idx)
+        g0, b0 = single_angle_grid_start(cost, n, m, p, grid=grid)
+        opt = AngleOptimizer(cost, n, m, p)
+        opt.reset(np.repeat(g0[:, None], p, 1), np.repeat(b0[:, None], p, 1))
+        opt.run(steps, lr=lr)
+        g, b = opt.angles()
+        labels[idx] = canonicalize(g.cpu().numpy(), b.cpu().numpy())
+    X = features(insts, d_in)
+    Y = torch.as_tensor(labels, dtype=torch.float32, device=X.device)
+    return X, Y
+
+
+def evaluate(prop, test, p: int, plain_steps: int = 200, max_steps: int = 200, lr: float = 0.05,
+             seed: int = 0):
+    """Steps and wall-seconds to reach 95 % of the plain optimizer's final P."""
+    steps_plain, steps_prop, wall_plain, wall_prop = [], [], [], []
+    P_plain, P_prop = [], []
+    hits = 0
+    for n, idx in _groups(test, p):
+        cost = torch.stack([test[i]["cost"] for i in idx])
+        m = max(test[i]["m"] for i in idx)
+        opt = AngleOptimizer(cost, n, m, p)
+        G = np.stack([instances.random_angles(p, seed * 1_000_003 + i)[0] for i in idx])
+        Bt = np.stack([instances.random_angles(p, seed * 1_000_003 + i)[1] for i in idx])
+        opt.reset(G, Bt)
+        plain = opt.run(plain_steps, lr=lr)
+        final = plain["values"][-1]
+        target = 0.95 * final
+        ok = plain["values"] >= target[None, :]
+        first_plain = ok.argmax(0)
+        # proposer: features + inference + the same optimizer from the proposal
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x = features([test[i] for i in idx])
+        g, b = prop.propose(x)
+        torch.cuda.synchronize()
+        t_infer = time.perf_counter() - t0
+        opt.reset(g, b)
+        run = opt.run(max_steps, lr=lr, target=target)
+        first = run["first_hit"]
+        for j in range(len(idx)):
+            sp = int(first_plain[j])
+            steps_plain.append(sp)
+            wall_plain.append(plain["wall"][sp])
+            P_plain.append(final[j])
+            P_prop.append(run["values"][-1][j])
+            if first[j] >= 0:
+                hits += 1
+                steps_prop.append(int(first[j]))
+                wall_prop.append(t_infer + run["wall"][first[j]])
+            else:  # fallback: the proposal's budget is spent, then the plain run
+                steps_prop.append(max_steps + sp)
+                wall_prop.append(t_infer + run["wall"][-1] + plain["wall"][sp])
+    N = len(steps_plain)
+    return {
+        "instances": N,
+        "median_steps_plain": float(np.median(steps_plain)),
+        "median_steps_proposer": float(np.median(steps_prop)),
+        "median_wall_plain": float(np.median(wall_plain)),
+        "median_wall_proposer": float(np.median(wall_prop)),
+        "hit_rate": hits / N,
+        "fallback_rate": 1.0 - hits / N,
+        "mean_P_plain": float(np.mean(P_plain)),
+        "mean_P_proposer_final": float(np.mean(P_prop)),
+    }
