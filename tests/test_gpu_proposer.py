@@ -146,6 +146,7 @@ def test_trained_proposer_gains_over_plain_optimizer():
     assert losses[-1] < 0.2 * losses[0]
     test = study.make_instances(32, seed=2, n_values=[14], d_lo=3.0, d_hi=5.0)
     ev = study.evaluate(prop, test, p=p, plain_steps=200, max_steps=200, lr=0.05, seed=5)
+    print(ev)
     assert ev["hit_rate"] >= 0.9
     assert ev["median_steps_proposer"] < ev["median_steps_plain"]
     assert ev["median_wall_proposer"] < ev["median_wall_plain"]
