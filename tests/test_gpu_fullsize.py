@@ -1,0 +1,111 @@
+"""Parity at the benchmark's full size, in the launch configuration bench.py
+times: n = 28, m = 118 (seed 0), p = 100 random angles, 10^6 shots, through
+gqaoa_build_cost / gqaoa_evolve / gqaoa_sample with caller-owned buffers.
+
+The oracle checks every output it can compute one by one: the whole cost
+table and histogram (FP64 C oracle, all 2^28 assignments), every amplitude
+psi_p(z) = f_p(C(z)) from the exact cost-class model (pinned against the
+full statevector oracle at small n), P(C=0), and each shot against the exact
+cumulative distribution.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import reduced, statevector as sv
+from paper_2402_02585_gb300 import _capi as C
+from paper_2402_02585_gb300 import core, instances
+
+pytestmark = pytest.mark.gpu
+
+N_VARS, M_CLAUSES, P_ROUNDS, SHOTS, SEED = 28, 118, 100, 1_000_000, 0
+
+
+@pytest.fixture(scope="module")
+def run():
+    n, m, p = N_VARS, M_CLAUSES, P_ROUNDS
+    N = 1 << n
+    lits = instances.random_3sat(n, m, SEED)
+    g, b = instances.random_angles(p, SEED)
+    dev = torch.device("cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    cost = torch.empty(N, dtype=torch.uint8, device=dev)
+    hist = torch.empty(m + 1, dtype=torch.int64, device=dev)
+    state = torch.empty(N, dtype=torch.complex64, device=dev)
+    out = torch.empty(3, dtype=torch.float64, device=dev)
+    trace = torch.empty(p, dtype=torch.float64, device=dev)
+    shots = torch.empty(SHOTS, dtype=torch.int64, device=dev)
+    gd = torch.as_tensor(g, device=dev)
+    bd = torch.as_tensor(b, device=dev)
+    ws_ev = core.workspace(C.gqaoa_evolve_workspace_size(n, p))
+    ws_sa = core.workspace(C.gqaoa_sample_workspace_size(n, SHOTS))
+    lc = np.ascontiguousarray(lits, dtype=np.int32)
+    C.gqaoa_build_cost(lc.ctypes.data, n, m, cost.data_ptr(), hist.data_ptr(), s)
+    C.gqaoa_evolve(cost.data_ptr(), n, m, gd.data_ptr(), bd.data_ptr(), p, state.data_ptr(),
+                   out.data_ptr(), trace.data_ptr(), ws_ev.data_ptr(), ws_ev.numel(), 0, s)
+    C.gqaoa_sample(state.data_ptr(), n, 12345, SHOTS, shots.data_ptr(), ws_sa.data_ptr(),
+                   ws_sa.numel(), s)
+    torch.cuda.synchronize()
+    ref_cost, ref_hist = sv.cost_table(lits, n)
+    f = reduced.evolve(ref_hist, g, b)
+    return dict(lits=lits, g=g, b=b, cost=cost.cpu().numpy(), hist=hist.cpu().numpy(),
+                state=state, out=out.cpu().numpy(), trace=trace.cpu().numpy(),
+                shots=shots.cpu().numpy(), ref_cost=ref_cost, ref_hist=ref_hist, f=f)
+
+
+def test_cost_table_and_histogram_bit_exact(run):
+    assert np.array_equal(run["cost"], run["ref_cost"])
+    assert np.array_equal(run["hist"].astype(np.uint64), run["ref_hist"])
+
+
+def test_every_amplitude_matches_cost_class_model(run):
+    f = run["f"].astype(np.complex64)
+    cost = torch.as_tensor(run["ref_cost"].astype(np.int64), device="cuda")
+    ref = torch.as_tensor(f, device="cuda")[cost]
+    err = torch.max(torch.abs(run["state"] - ref)).item()
+    assert err < 1e-5, err
+    # also relative to the amplitude scale 2^-14 of this size
+    assert err < 0.01 * 2.0 ** -14
+
+
+def test_readout_and_trace(run):
+    h = run["ref_hist"]
+    _, tr = reduced.evolve(h, run["g"], run["b"], trace=True)
+    r = reduced.readout(h, run["f"])
+    assert abs(run["out"][0] - r[0]) < 1e-6
+    assert abs(run["out"][1] - r[1]) < 1e-4 * M_CLAUSES / 8
+    assert abs(run["out"][2] - 1.0) < 1e-5
+    assert np.max(np.abs(run["trace"] - tr)) < 1e-6
+
+
+def test_shots_valid_against_exact_cdf(run):
+    # exact distribution: |f_p(C(z))|^2, CDF in index order (FP64)
+    w = (np.abs(run["f"]) ** 2)[run["ref_cost"]]
+    cdf = np.cumsum(w)
+    total = cdf[-1]
+    shots = run["shots"]
+    assert shots.min() >= 0 and shots.max() < (1 << N_VARS)
+    sel = np.arange(0, SHOTS, 97)  # every 97th shot: the oracle's uniforms one by one
+    u = np.array([sv.shot_uniform(12345, int(s)) for s in sel])
+    t = u * total
+    z = shots[sel]
+    lo = np.where(z > 0, cdf[np.maximum(z - 1, 0)], 0.0)
+    hi = cdf[z]
+    tol = 1e-5 * total
+    assert np.all(lo - tol <= t) and np.all(t <= hi + tol)
+    exact = np.searchsorted(cdf, t, side="right")
+    assert np.mean(exact == z) > 0.99
+
+
+def test_shot_classes_follow_cost_class_weights(run):
+    import scipy.stats
+    c = run["ref_cost"][run["shots"]]
+    h = run["ref_hist"].astype(np.float64)
+    wts = h * np.abs(run["f"]) ** 2
+    obs = np.bincount(c, minlength=len(h)).astype(np.float64)
+    exp = wts / wts.sum() * SHOTS
+    keep = exp > 5
+    stat = np.sum((obs[keep] - exp[keep]) ** 2 / exp[keep])
+    assert scipy.stats.chi2.sf(stat, keep.sum() - 1) > 1e-4
+    assert obs[~keep].sum() <= exp[~keep].sum() * 3 + 30
