@@ -92,10 +92,13 @@ def test_shots_valid_against_exact_cdf(run):
     z = shots[sel]
     lo = np.where(z > 0, cdf[np.maximum(z - 1, 0)], 0.0)
     hi = cdf[z]
+    # Single probabilities are ~2^-28 here while the complex64 state moves the
+    # CDF by up to ~1e-6 of the total, so the exact index can shift by
+    # hundreds of amplitudes; what must hold is that every shot's target lies
+    # in its amplitude's CDF interval up to that state error.
     tol = 1e-5 * total
-    assert np.all(lo - tol <= t) and np.all(t <= hi + tol)
-    exact = np.searchsorted(cdf, t, side="right")
-    assert np.mean(exact == z) > 0.99
+    miss = np.maximum(np.maximum(lo - t, t - hi), 0.0)
+    assert np.max(miss) <= tol, np.max(miss) / total
 
 
 def test_shot_classes_follow_cost_class_weights(run):
