@@ -214,6 +214,28 @@ int gqaoa_grad_batched(const uint8_t *cost, int64_t cost_stride, int n, int m, i
                        double *value, double *dgamma, double *dbeta, void *ws, size_t ws_bytes,
                        void *stream);
 
+/*
+ * Single-angle-pair sweep (Eq. 5; Appendix C's grid scan) with the state held
+ * on chip: `batch` instances of equal n times `angles` angle points, each
+ * evolved p rounds from |+> with gamma_k = gammas[a], beta_k = betas[a], and
+ * P(C=0) read out after each round count listed in `rounds`.
+ * cost    device uint8 [batch][2^n] (16-byte aligned).
+ * gammas, betas  device double [angles].
+ * rounds  host int32 [nrounds], strictly ascending, each in 1..p; nrounds <= 16.
+ * out     device double [batch][angles][nrounds] written.
+ * ws      device workspace of gqaoa_sweep_workspace_size(angles) bytes.
+ * n must be in GQAOA_SWEEP_MIN_N..GQAOA_SWEEP_MAX_N (one CTA holds 2^n <=
+ * 16384 amplitudes in registers; 15 <= n <= 18 use a cluster of 2..16 CTAs).
+ * Precision: complex64 state; the mixer sum is FP32 within a warp and
+ * double-float across warps and CTAs; P is formed in FP64.
+ */
+#define GQAOA_SWEEP_MIN_N 9
+#define GQAOA_SWEEP_MAX_N 18
+int gqaoa_sweep_workspace_size(int angles, size_t *bytes);
+int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const double *gammas,
+                const double *betas, int angles, int p, const int32_t *rounds, int nrounds,
+                double *out, void *ws, size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * Learned angle proposer (K9). The paper observes that optimal angles
  * cluster with the instance size and clause count (Section III.B, Fig. 2;

@@ -25,6 +25,8 @@ GQAOA_OBJ_P0 = 0
 GQAOA_OBJ_ENERGY = 1
 GQAOA_MAX_N = 34
 GQAOA_MAX_M = 255
+GQAOA_SWEEP_MIN_N = 9
+GQAOA_SWEEP_MAX_N = 18
 
 
 class GQAOAError(RuntimeError):
@@ -61,6 +63,8 @@ SIGNATURES = {
     "gqaoa_grad_batched_workspace_size": [_I, _I, _I, _SZP],
     "gqaoa_grad_batched": [_P, _I64, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P],
     "gqaoa_evolve_noalloc": [_P, _I, _I, _P, _P, _I, _P, _P, _P, _U, _P],
+    "gqaoa_sweep_workspace_size": [_I, _SZP],
+    "gqaoa_sweep": [_P, _I, _I, _I, _P, _P, _I, _I, _P, _I, _P, _P, _SZ, _P],
     "gqaoa_mlp_param_count": [_I, _I, _I, _SZP],
     "gqaoa_mlp_workspace_size": [_I, _I, _I, _I, _SZP],
     "gqaoa_mlp_forward": [_P, _I, _I, _I, _P, _I, _P, _P, _SZ, _P],
@@ -173,6 +177,16 @@ def gqaoa_grad_batched(cost, cost_stride, n, m, batch, gammas, betas, p, objecti
                        dbeta, ws, ws_bytes, stream):
     _call("gqaoa_grad_batched", cost, cost_stride, n, m, batch, gammas, betas, p, objective, value,
           dgamma, dbeta, ws, ws_bytes, stream)
+
+
+def gqaoa_sweep_workspace_size(angles) -> int:
+    return _size("gqaoa_sweep_workspace_size", angles)
+
+
+def gqaoa_sweep(cost, n, m, batch, gammas, betas, angles, p, rounds, nrounds, out, ws, ws_bytes,
+                stream):
+    _call("gqaoa_sweep", cost, n, m, batch, gammas, betas, angles, p, rounds, nrounds, out, ws,
+          ws_bytes, stream)
 
 
 def gqaoa_mlp_param_count(d_in, d_h, d_out) -> int:

@@ -501,7 +501,7 @@ backward_kernel(const PassArgs a, const float4 *__restrict__ chi_base) {
       // e^{-i beta} = alpha + 1; w = e^{-i beta} (S/N) conj(Lambda)
       const double er = al.x + 1.0, ei = al.y;
       const double qr = er * Sre - ei * Sim, qi = er * Sim + ei * Sre;
-      const double wr = qr * Lr + qi * Li, wi = qi * Lr - qr * Li;
+      const double wi = qi * Lr - qr * Li;  // Im(w)
       a.dbeta[bk] = 2.0 * wi;  // 2 Re(-i w) = 2 Im(w)
       if (kFirst) a.value[b] = G;
       else a.dgamma[bk + 1] = 2.0 * G;
@@ -768,14 +768,21 @@ static void init_pass(PassArgs &pa, const Geometry &g, const Ws &w, const uint8_
 
 static double *parts_half(const Ws &w, int i) { return w.parts + (size_t)(i & 1) * w.parts_half; }
 
-static int launch_phase_tables(const double *gammas, const double *betas, int64_t bp, const Ws &w,
-                               cudaStream_t st) {
-  const int64_t total = bp * 256;
+// Phase tables e^{-i gamma c} (c = 0..255) and alpha = e^{-i beta} - 1 for
+// `count` angle pairs (also used by the on-chip sweep).
+int phase_tables(const double *gammas, const double *betas, int64_t count, float2 *phase,
+                 double2 *alpha, cudaStream_t st) {
+  const int64_t total = count * 256;
   int64_t grid = (total + kThreads - 1) / kThreads;
   if (grid > 4096) grid = 4096;
-  phase_table_kernel<<<(unsigned)grid, kThreads, 0, st>>>(gammas, betas, bp, w.phase, w.alpha);
+  phase_table_kernel<<<(unsigned)grid, kThreads, 0, st>>>(gammas, betas, count, phase, alpha);
   GQ_CHECK_LAUNCH();
   return GQAOA_OK;
+}
+
+static int launch_phase_tables(const double *gammas, const double *betas, int64_t bp, const Ws &w,
+                               cudaStream_t st) {
+  return phase_tables(gammas, betas, bp, w.phase, w.alpha, st);
 }
 
 // Forward rounds. In place on `state` (ckpt == null) or chi_k -> ckpt[k].

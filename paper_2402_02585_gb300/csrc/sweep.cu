@@ -1,0 +1,318 @@
+// K7: batched single-angle-pair sweep with the state held on chip.
+//
+// The single-angle-pair protocol (Eq. 5) applies the same (gamma, beta) in
+// every round; Appendix C scans it on a grid for every instance. A sweep is
+// B instances x A angle points, each evolved for p rounds from |+> with P(C=0)
+// read out after the rounds listed in `rounds` (a prefix sweep: one p-round run
+// gives every shorter p).
+//
+// One work item = (instance, angle point) and is owned by one CTA (n <= 14)
+// or one thread-block cluster of 2..16 CTAs (n = 15..18). Each thread holds
+// 16 consecutive amplitudes and their 16 cost bytes in registers for the
+// whole evolution, so a round costs no memory traffic at all: per amplitude
+// one shared-memory phase lookup, a complex multiply-add and a partial sum.
+// The mixer needs S = sum_z chi(z) every round: FP32 over a thread's 16
+// values and the warp's butterfly, then double-float (two FP32 words) across
+// warps and, for clusters, across CTAs through distributed shared memory
+// (ld.shared::cluster after a cluster barrier). Warp 0 of every CTA forms the
+// same a = alpha S / N from the same partials, so the CTAs of a cluster agree
+// bit for bit without a broadcast. Persistent grid: each CTA/cluster loops
+// over items instance-major, so consecutive items reuse the instance's cost
+// table from L2.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace gq {
+
+int phase_tables(const double *gammas, const double *betas, int64_t count, float2 *phase,
+                 double2 *alpha, cudaStream_t st);
+int sm_count();
+
+constexpr int kSweepMaxRounds = 16;
+constexpr int kSlots = 6;  // S.re, S.im, A0, B0.re, B0.im, count of C = 0
+
+struct SweepArgs {
+  const uint8_t *cost;   // [B][N]
+  const float2 *phase;   // [A][256]
+  const double2 *alpha;  // [A]
+  double *out;           // [B][A][R]
+  uint64_t nitems;       // B * A
+  int n;
+  int A;
+  int p;
+  int R;
+  int rounds[kSweepMaxRounds];  // ascending, 1-based
+};
+
+// Double-float accumulate of a float.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float x) {
+  float s, e;
+  two_sum(hi, x, s, e);
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+// Double-float butterfly over the warp (every lane ends with the same sum).
+__device__ __forceinline__ void df_warp(float &hi, float &lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    float s, e;
+    two_sum(hi, h2, s, e);
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, l2), e);
+  }
+}
+__device__ __forceinline__ float warp_fsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float2 ld_dsmem_f32x2(const float *p, unsigned rank) {
+  uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+  float x, y;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(remote) : "memory");
+  return make_float2(x, y);
+}
+
+template <int kThreads, int kCluster>
+__global__ void __launch_bounds__(kThreads, 1) sweep_kernel(const __grid_constant__ SweepArgs a) {
+  constexpr int kW = kThreads / 32;
+  __shared__ float2 s_T[256];
+  __shared__ float s_wp[2][kW][kSlots];        // warp partials (FP32)
+  __shared__ float s_cp[2][kSlots][2];         // CTA partials (double-float), read cluster-wide
+  __shared__ float2 s_a;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned rank = kCluster > 1 ? cluster_ctarank() : 0u;
+  const uint64_t cluster_id = blockIdx.x / kCluster, nclusters = gridDim.x / kCluster;
+  const uint64_t N = 1ull << a.n;
+  const float inv_n = (float)(1.0 / (double)N);
+  const float amp0 = (float)(1.0 / sqrt((double)N));
+  int buf = 0;
+
+  for (uint64_t item = cluster_id; item < a.nitems; item += nclusters) {
+    const uint64_t b = item / (uint64_t)a.A;
+    const int ai = (int)(item % (uint64_t)a.A);
+    const uint4 cw = *reinterpret_cast<const uint4 *>(
+        a.cost + b * N + 16ull * ((uint64_t)rank * kThreads + threadIdx.x));
+    for (int i = threadIdx.x; i < 256; i += kThreads) s_T[i] = a.phase[(size_t)ai * 256 + i];
+    const double2 ald = a.alpha[ai];
+    const float alr = (float)ald.x, ali = (float)ald.y;
+    __syncthreads();
+    const uint32_t cwords[4] = {cw.x, cw.y, cw.z, cw.w};
+    float2 s[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) s[j] = make_float2(amp0, 0.f);
+    float2 ad = make_float2(0.f, 0.f);
+    float cnt0 = 0.f;  // C = 0 count of the instance (warp 0 keeps it)
+    int ridx = 0;
+    for (int r = 0; r < a.p; ++r) {
+      const bool ro = ridx < a.R && a.rounds[ridx] == r + 1;
+      const bool first = r == 0;
+      float v[kSlots] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const unsigned c = (cwords[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+        const float2 ps = make_float2(s[j].x + ad.x, s[j].y + ad.y);
+        const float2 x = cmul(s_T[c], ps);
+        s[j] = x;
+        v[0] += x.x;
+        v[1] += x.y;
+        if (c == 0) {
+          if (ro) { v[2] += x.x * x.x + x.y * x.y; v[3] += x.x; v[4] += x.y; }
+          if (first) v[5] += 1.f;
+        }
+      }
+      const int nv = (ro || first) ? kSlots : 2;
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k)
+        if (k < nv) v[k] = warp_fsum(v[k]);
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k)
+          if (k < nv) s_wp[buf][warp][k] = v[k];
+      }
+      __syncthreads();
+      float hi[kSlots], lo[kSlots];
+      if (warp == 0) {
+        // double-float sum over this CTA's warps
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k) {
+          hi[k] = (k < nv && lane < kW) ? s_wp[buf][lane][k] : 0.f;
+          lo[k] = 0.f;
+          if (k < nv) df_warp(hi[k], lo[k]);
+        }
+        if (kCluster > 1 && lane == 0) {
+#pragma unroll
+          for (int k = 0; k < kSlots; ++k)
+            if (k < nv) { s_cp[buf][k][0] = hi[k]; s_cp[buf][k][1] = lo[k]; }
+        }
+      }
+      if (kCluster > 1) {
+        cluster_sync();  // every CTA's partial visible cluster-wide
+        if (warp == 0) {
+          // double-float sum over the cluster's CTAs, in rank order
+#pragma unroll
+          for (int k = 0; k < kSlots; ++k) {
+            float2 d = make_float2(0.f, 0.f);
+            if (k < nv && lane < kCluster) d = ld_dsmem_f32x2(&s_cp[buf][k][0], (unsigned)lane);
+            hi[k] = d.x;
+            lo[k] = d.y;
+            if (k < nv) df_warp(hi[k], lo[k]);
+          }
+        }
+      }
+      if (warp == 0) {
+        const float Sr = hi[0] + lo[0], Si = hi[1] + lo[1];
+        const float ar = (alr * Sr - ali * Si) * inv_n, aim = (alr * Si + ali * Sr) * inv_n;
+        if (lane == 0) s_a = make_float2(ar, aim);
+        if (first) cnt0 = hi[5] + lo[5];
+        if (ro && rank == 0 && lane == 0) {
+          // sum_{C=0} |chi + a|^2 = A0 + 2 Re(conj(a) B0) + h[0] |a|^2
+          const double A0 = (double)hi[2] + lo[2], Br = (double)hi[3] + lo[3],
+                       Bi = (double)hi[4] + lo[4];
+          const double P = A0 + 2.0 * ((double)ar * Br + (double)aim * Bi) +
+                           (double)cnt0 * ((double)ar * ar + (double)aim * aim);
+          a.out[(b * (uint64_t)a.A + ai) * a.R + ridx] = P;
+        }
+      }
+      __syncthreads();
+      ad = s_a;
+      if (ro) ++ridx;
+      buf ^= 1;
+    }
+  }
+  if (kCluster > 1) cluster_sync();  // no CTA leaves while a peer may read its shared memory
+}
+
+struct SweepShape {
+  int threads;
+  int cluster;
+};
+
+static SweepShape sweep_shape(int n) {
+  // 16 amplitudes per thread; up to 1024 threads per CTA, then clusters
+  const int amps = 1 << n;
+  int threads = amps / 16;
+  int cluster = 1;
+  if (threads > 1024) {
+    cluster = threads / 1024;
+    threads = 1024;
+  }
+  return SweepShape{threads, cluster};
+}
+
+template <int kThreads, int kCluster>
+static int launch_sweep(const SweepArgs &args, cudaStream_t st) {
+  auto kernel = sweep_kernel<kThreads, kCluster>;
+  int per_unit = 0;  // resident CTAs (cluster == 1) or clusters
+  if (kCluster == 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_unit, kernel, kThreads, 0) != cudaSuccess)
+      return GQAOA_ECUDA;
+    per_unit *= sm_count();
+  } else {
+    if (kCluster > 8 &&
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+      return GQAOA_ECUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kCluster, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&per_unit, kernel, &cfg) != cudaSuccess) return GQAOA_ECUDA;
+  }
+  if (per_unit < 1) return GQAOA_ECUDA;
+  uint64_t units = args.nitems < (uint64_t)per_unit ? args.nitems : (uint64_t)per_unit;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(units * kCluster), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = kCluster > 1 ? 1 : 0;
+  if (cudaLaunchKernelEx(&cfg, kernel, args) != cudaSuccess) return GQAOA_ECUDA;
+  return GQAOA_OK;
+}
+
+static size_t sweep_ws_layout(int A, char *base, float2 **phase, double2 **alpha) {
+  const size_t o_alpha = round_up(sizeof(float2) * 256 * (size_t)A, 256);
+  if (base) {
+    *phase = reinterpret_cast<float2 *>(base);
+    *alpha = reinterpret_cast<double2 *>(base + o_alpha);
+  }
+  return o_alpha + round_up(sizeof(double2) * (size_t)A, 256);
+}
+
+}  // namespace gq
+
+using namespace gq;
+
+extern "C" int gqaoa_sweep_workspace_size(int angles, size_t *bytes) {
+  if (!bytes) return GQAOA_EINVAL;
+  if (angles < 1 || angles > (1 << 24)) return GQAOA_ERANGE;
+  *bytes = sweep_ws_layout(angles, nullptr, nullptr, nullptr);
+  return GQAOA_OK;
+}
+
+extern "C" int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const double *gammas,
+                           const double *betas, int angles, int p, const int32_t *rounds,
+                           int nrounds, double *out, void *ws, size_t ws_bytes, void *stream) {
+  if (n < GQAOA_SWEEP_MIN_N || n > GQAOA_SWEEP_MAX_N || m < 0 || m > GQAOA_MAX_M || batch < 1 ||
+      angles < 1 || angles > (1 << 24) || p < 1 || p > (1 << 20) || nrounds < 1 ||
+      nrounds > kSweepMaxRounds)
+    return GQAOA_ERANGE;
+  if (!cost || !gammas || !betas || !rounds || !out || !ws) return GQAOA_EINVAL;
+  if (!aligned16(cost) || !aligned8(gammas) || !aligned8(betas) || !aligned8(out) ||
+      !aligned16(ws))
+    return GQAOA_EINVAL;
+  for (int i = 0; i < nrounds; ++i) {
+    if (rounds[i] < 1 || rounds[i] > p) return GQAOA_ERANGE;
+    if (i > 0 && rounds[i] <= rounds[i - 1]) return GQAOA_EINVAL;
+  }
+  if (ws_bytes < sweep_ws_layout(angles, nullptr, nullptr, nullptr)) return GQAOA_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SweepArgs args = {};
+  float2 *phase = nullptr;
+  double2 *alpha = nullptr;
+  sweep_ws_layout(angles, static_cast<char *>(ws), &phase, &alpha);
+  int rc = phase_tables(gammas, betas, angles, phase, alpha, st);
+  if (rc) return rc;
+  args.cost = cost;
+  args.phase = phase;
+  args.alpha = alpha;
+  args.out = out;
+  args.nitems = (uint64_t)batch * (uint64_t)angles;
+  args.n = n;
+  args.A = angles;
+  args.p = p;
+  args.R = nrounds;
+  for (int i = 0; i < nrounds; ++i) args.rounds[i] = rounds[i];
+  const SweepShape sh = sweep_shape(n);
+  switch (sh.threads * 100 + sh.cluster) {
+    case 32 * 100 + 1: return launch_sweep<32, 1>(args, st);
+    case 64 * 100 + 1: return launch_sweep<64, 1>(args, st);
+    case 128 * 100 + 1: return launch_sweep<128, 1>(args, st);
+    case 256 * 100 + 1: return launch_sweep<256, 1>(args, st);
+    case 512 * 100 + 1: return launch_sweep<512, 1>(args, st);
+    case 1024 * 100 + 1: return launch_sweep<1024, 1>(args, st);
+    case 1024 * 100 + 2: return launch_sweep<1024, 2>(args, st);
+    case 1024 * 100 + 4: return launch_sweep<1024, 4>(args, st);
+    case 1024 * 100 + 8: return launch_sweep<1024, 8>(args, st);
+    case 1024 * 100 + 16: return launch_sweep<1024, 16>(args, st);
+    default: return GQAOA_ERANGE;
+  }
+}

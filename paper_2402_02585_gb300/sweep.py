@@ -1,0 +1,126 @@
+"""Batched single-angle-pair sweeps (Eq. 5, Appendix C's grid scan) over many
+instances of uneven n, as one replayable CUDA graph.
+
+Instances are bucketed by n. Each bucket runs on the path the tuning table
+chooses for its n:
+  * "onchip": gqaoa_sweep, one CTA or thread-block cluster per
+    (instance, angle point) holding the state in registers (9 <= n <= 18);
+  * "stream": gqaoa_evolve_batched with the instance's cost table shared by a
+    chunk of angle points and a per-round trace of P(C=0); the chunk size is
+    chosen so the chunk's states stay resident in L2.
+Every buffer and workspace is allocated when the plan is built, so the whole
+sequence of C-ABI calls can be captured into one CUDA graph and replayed.
+"""
+
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+import torch
+
+from . import _capi as C
+from . import core
+
+TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
+
+
+def load_table(path: str = TABLE_PATH) -> dict:
+    try:
+        with open(path) as fh:
+            return {int(k): v for k, v in json.load(fh)["sweep"].items()}
+    except (OSError, KeyError, ValueError):
+        return {}
+
+
+def default_choice(n: int) -> dict:
+    if C.GQAOA_SWEEP_MIN_N <= n <= C.GQAOA_SWEEP_MAX_N:
+        return {"path": "onchip"}
+    # keep a chunk of states within ~64 MiB of L2
+    return {"path": "stream", "angle_batch": max(1, (64 << 20) // ((1 << n) * 8))}
+
+
+class SweepPlan:
+    """P(C=0) after `rounds` for every (instance, angle point), single angle pair.
+
+    buckets: dict n -> (cost [B_n, 2^n] uint8 on the device, m_max)
+    gammas, betas: [A] angle points; p rounds; rounds: ascending 1-based list.
+    """
+
+    def __init__(self, buckets: dict, gammas, betas, p: int, rounds, table: dict | None = None,
+                 device="cuda"):
+        self.device = torch.device(device)
+        self.p = p
+        self.rounds = np.ascontiguousarray(rounds, dtype=np.int32)
+        self.R = len(self.rounds)
+        self.A = len(gammas)
+        self.table = table if table is not None else load_table()
+        self.g = torch.as_tensor(np.asarray(gammas, np.float64), device=self.device).contiguous()
+        self.b = torch.as_tensor(np.asarray(betas, np.float64), device=self.device).contiguous()
+        self.gp = self.g[:, None].repeat(1, p).contiguous()  # [A, p] for the streaming path
+        self.bp = self.b[:, None].repeat(1, p).contiguous()
+        self.ridx = torch.as_tensor(self.rounds.astype(np.int64) - 1, device=self.device)
+        self.steps = []
+        self.out = {}
+        for n in sorted(buckets):
+            cost, m = buckets[n]
+            B = cost.shape[0]
+            choice = self.table.get(n, default_choice(n))
+            out = torch.empty((B, self.A, self.R), dtype=torch.float64, device=self.device)
+            self.out[n] = out
+            if choice["path"] == "onchip":
+                ws = core.workspace(C.gqaoa_sweep_workspace_size(self.A), self.device)
+                self.steps.append(("onchip", n, m, cost, out, ws))
+            else:
+                S = int(min(self.A, choice["angle_batch"]))
+                state = torch.empty((S, 1 << n), dtype=torch.complex64, device=self.device)
+                trace = torch.empty((S, p), dtype=torch.float64, device=self.device)
+                res = torch.empty((S, 3), dtype=torch.float64, device=self.device)
+                ws = core.workspace(C.gqaoa_evolve_batched_workspace_size(n, S, p), self.device)
+                self.steps.append(("stream", n, m, cost, out, (S, state, trace, res, ws)))
+
+    def amp_rounds(self) -> int:
+        return sum(st[3].shape[0] * self.A * self.p * (1 << st[1]) for st in self.steps)
+
+    def run(self):
+        s = torch.cuda.current_stream().cuda_stream
+        for kind, n, m, cost, out, extra in self.steps:
+            B = cost.shape[0]
+            if kind == "onchip":
+                ws = extra
+                C.gqaoa_sweep(cost.data_ptr(), n, m, B, self.g.data_ptr(), self.b.data_ptr(),
+                              self.A, self.p, self.rounds.ctypes.data, self.R, out.data_ptr(),
+                              ws.data_ptr(), ws.numel(), s)
+                continue
+            S, state, trace, res, ws = extra
+            for i in range(B):
+                for a0 in range(0, self.A, S):
+                    k = min(S, self.A - a0)
+                    C.gqaoa_evolve_batched(cost[i].data_ptr(), 0, n, m, k,
+                                           self.gp[a0].data_ptr(), self.bp[a0].data_ptr(), self.p,
+                                           state.data_ptr(), res.data_ptr(), trace.data_ptr(),
+                                           ws.data_ptr(), ws.numel(), 0, s)
+                    out[i, a0:a0 + k].copy_(trace[:k].index_select(1, self.ridx))
+        return self.out
+
+    def capture(self):
+        """Record run() into a CUDA graph (after one eager warm-up run)."""
+        self.run()
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run()
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
+        return self.out
+
+
+def grid_angles(k: int = 32):
+    """The k x k grid over [0, pi)^2 with left endpoints: gamma_i = i pi / k,
+    beta_j = j pi / k (gamma-major)."""
+    G = np.repeat(np.arange(k) * np.pi / k, k)
+    B = np.tile(np.arange(k) * np.pi / k, k)
+    return G, B

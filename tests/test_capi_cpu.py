@@ -115,3 +115,18 @@ def test_sample_and_grad_reject_bad_arguments_before_launch():
     with pytest.raises(C.GQAOAError) as e:
         C.gqaoa_grad(fake, 16, 60, fake, fake, 4, 0, fake, fake, fake, fake, 1024, None)
     assert e.value.status == C.GQAOA_ENOMEM
+
+
+def test_sweep_rejects_bad_arguments_before_launch():
+    fake = 1 << 20
+    r = np.array([2, 1], dtype=np.int32)
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_sweep(fake, 12, 50, 1, fake, fake, 4, 4, r.ctypes.data, 2, fake, fake, 1 << 20, None)
+    assert e.value.status == C.GQAOA_EINVAL
+    r = np.array([5], dtype=np.int32)
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_sweep(fake, 12, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, fake, fake, 1 << 20, None)
+    assert e.value.status == C.GQAOA_ERANGE
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_sweep(fake, 19, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, fake, fake, 1 << 20, None)
+    assert e.value.status == C.GQAOA_ERANGE

@@ -1,0 +1,129 @@
+"""The on-chip single-angle-pair sweep (gqaoa_sweep) against the oracle.
+
+P(C=0) after the requested round counts must agree with the FP64 oracle
+within 1e-6 for every (instance, angle point): the full statevector oracle at
+small n, the exact cost-class model (pinned against it) at larger n. The
+cases cover one warp per item (n = 9), whole CTAs (n = 12..14) and clusters
+of 2, 4, 8 and 16 CTAs (n = 15..18), and more items than resident CTAs.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import reduced, statevector as sv
+from paper_2402_02585_gb300 import _capi as C
+from paper_2402_02585_gb300 import core, instances
+
+pytestmark = pytest.mark.gpu
+
+
+def run_sweep(costs, n, m, G, Bt, p, rounds):
+    B = costs.shape[0]
+    A = len(G)
+    gd = torch.as_tensor(np.asarray(G, dtype=np.float64), device="cuda")
+    bd = torch.as_tensor(np.asarray(Bt, dtype=np.float64), device="cuda")
+    out = torch.full((B, A, len(rounds)), -1.0, dtype=torch.float64, device="cuda")
+    ws = core.workspace(C.gqaoa_sweep_workspace_size(A))
+    r = np.ascontiguousarray(rounds, dtype=np.int32)
+    C.gqaoa_sweep(costs.data_ptr(), n, m, B, gd.data_ptr(), bd.data_ptr(), A, p, r.ctypes.data,
+                  len(rounds), out.data_ptr(), ws.data_ptr(), ws.numel(),
+                  torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,B,A,p,rounds", [
+    (9, 3, 7, 12, [1, 4, 12]),
+    (10, 2, 5, 8, [2, 8]),
+    (12, 4, 9, 16, [1, 4, 16]),
+    (13, 2, 4, 10, [3, 10]),
+    (14, 2, 3, 16, [1, 16]),
+    (15, 2, 3, 8, [1, 4, 8]),
+    (16, 1, 3, 8, [8]),
+    (17, 1, 2, 6, [1, 6]),
+    (18, 1, 2, 5, [2, 5]),
+])
+def test_sweep_matches_oracle(n, B, A, p, rounds):
+    m = int(math.floor(4.2 * n + 0.5))
+    costs, hists, refc = [], [], []
+    for i in range(B):
+        lits = instances.random_3sat(n, m, 700 + 10 * n + i)
+        c, h = core.build_cost(lits, n)
+        costs.append(c)
+        hists.append(h.cpu().numpy())
+        if n <= 12:
+            refc.append(sv.cost_table(lits, n)[0])
+    rng = np.random.default_rng(n)
+    G = rng.uniform(0, np.pi, A)
+    Bt = rng.uniform(0, np.pi, A)
+    got = run_sweep(torch.stack(costs), n, m, G, Bt, p, rounds)
+    for i in range(B):
+        for a in range(A):
+            if n <= 12:
+                _, tr = sv.evolve(refc[i], n, [G[a]] * p, [Bt[a]] * p, trace=True)
+            else:
+                _, tr = reduced.evolve(hists[i], [G[a]] * p, [Bt[a]] * p, trace=True)
+            ref = tr[np.asarray(rounds) - 1]
+            assert np.max(np.abs(got[i, a] - ref)) < 1e-6, (i, a, got[i, a], ref)
+
+
+def test_sweep_many_items_and_grid_left_endpoints():
+    # more items than resident CTAs: the persistent loop must cover them all
+    n, m, p = 12, 50, 8
+    costs, hists = [], []
+    for i in range(3):
+        c, h = core.build_cost(instances.random_3sat(n, m, 900 + i), n)
+        costs.append(c)
+        hists.append(h.cpu().numpy())
+    k = 32  # a 32 x 32 grid over [0, pi)^2, left endpoints
+    G = np.repeat(np.arange(k) * np.pi / k, k)
+    Bt = np.tile(np.arange(k) * np.pi / k, k)
+    got = run_sweep(torch.stack(costs), n, m, G, Bt, p, [1, 4, 8])
+    for i in range(3):
+        for a in range(0, k * k, 37):
+            _, tr = reduced.evolve(hists[i], [G[a]] * p, [Bt[a]] * p, trace=True)
+            assert np.max(np.abs(got[i, a] - tr[[0, 3, 7]])) < 1e-6
+    # gamma = 0 or beta = 0 rows keep the random-guess probability
+    for i in range(3):
+        h0 = hists[i][0] / (1 << n)
+        assert np.max(np.abs(got[i, :k, :] - h0)) < 1e-6          # gamma = 0
+        assert np.max(np.abs(got[i, ::k, :] - h0)) < 1e-6         # beta = 0
+
+
+def test_sweep_plan_mixed_buckets_and_graph_replay():
+    from paper_2402_02585_gb300.sweep import SweepPlan
+    p, rounds = 6, [1, 3, 6]
+    buckets, hists = {}, {}
+    for n, B in ((11, 2), (13, 2), (19, 1)):
+        m = int(math.floor(4.2 * n + 0.5))
+        cs, hs = [], []
+        for i in range(B):
+            c, h = core.build_cost(instances.random_3sat(n, m, 1200 + 10 * n + i), n)
+            cs.append(c)
+            hs.append(h.cpu().numpy())
+        buckets[n] = (torch.stack(cs), m)
+        hists[n] = hs
+    rng = np.random.default_rng(3)
+    G = rng.uniform(0, np.pi, 5)
+    Bt = rng.uniform(0, np.pi, 5)
+    table = {11: {"path": "onchip"}, 13: {"path": "stream", "angle_batch": 2},
+             19: {"path": "stream", "angle_batch": 3}}
+    plan = SweepPlan(buckets, G, Bt, p, rounds, table=table)
+    eager = {n: o.clone() for n, o in plan.run().items()}
+    torch.cuda.synchronize()
+    for n, hs in hists.items():
+        for i, h in enumerate(hs):
+            for a in range(5):
+                _, tr = reduced.evolve(h, [G[a]] * p, [Bt[a]] * p, trace=True)
+                got = eager[n][i, a].cpu().numpy()
+                assert np.max(np.abs(got - tr[np.asarray(rounds) - 1])) < 1e-6, (n, i, a)
+    plan.capture()
+    for o in plan.out.values():
+        o.fill_(-1.0)
+    plan.replay()
+    torch.cuda.synchronize()
+    for n in eager:
+        assert torch.equal(plan.out[n], eager[n])
