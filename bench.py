@@ -42,6 +42,11 @@ WORKLOADS = {
                   desc="random 3-SAT n=28 m=118 (d~4.2) seed 0, p=100 random angles, 1e6 shots"),
     "small": dict(n=10, m=42, p=8, shots=10_000, seed=0,
                   desc="random 3-SAT n=10 m=42 (d=4.2) seed 0, p=8 random angles, 1e4 shots"),
+    # the batched single-angle-pair sweep: one step = the whole sweep
+    "sweep": dict(kind="sweep", count=4096, grid=32, p=64, rounds=[1, 4, 16, 64], seed=0,
+                  desc="4096 random 3-SAT instances, n uniform in 12..20, d in {3.0, 4.2, 5.0}; "
+                       "single angle pair on a 32x32 grid over [0,pi)^2, p=64 with P read out "
+                       "at p=1,4,16,64 (prefix reuse); one CUDA graph per step"),
     # batched adjoint gradient + Adam over all 2p angles (one step = one Adam step)
     "grad": dict(kind="grad", n=16, m=67, p=32, batch=1024, seed=0, lr=0.05,
                  desc="1024 random 3-SAT instances n=16 m=67 (d~4.2), p=32 random angles; "
@@ -447,17 +452,73 @@ def run_grad(args, wl):
     return 0
 
 
+def run_sweep(args, wl):
+    """Workload "sweep": all instances x all grid points through SweepPlan (the
+    on-chip sweep for n <= 18, L2/HBM streaming chunks above), replayed as one
+    CUDA graph. Metric: amplitude-rounds per second, sum over items of p * 2^n."""
+    import torch
+
+    from paper_2402_02585_gb300 import core, instances
+    from paper_2402_02585_gb300.sweep import SweepPlan, grid_angles
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    count = int(os.environ.get("GQAOA_SWEEP_INSTANCES", wl["count"]))
+    shapes = instances.sweep_shapes(count, wl["seed"])
+    per_n: dict[int, list] = {}
+    mmax: dict[int, int] = {}
+    for i, (n, m, _) in enumerate(shapes):
+        if i % world != rank:
+            continue
+        lits = instances.random_3sat(n, m, wl["seed"] * 1_000_003 + i)
+        per_n.setdefault(n, []).append(core.build_cost(lits, n, with_hist=False)[0])
+        mmax[n] = max(mmax.get(n, 0), m)
+    buckets = {n: (torch.stack(v), mmax[n]) for n, v in per_n.items()}
+    G, B = grid_angles(wl["grid"])
+    plan = SweepPlan(buckets, G, B, wl["p"], wl["rounds"])
+    plan.capture()  # includes one eager run
+    for _ in range(max(0, args.warmup - 1)):
+        plan.replay()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    start.record()
+    for _ in range(args.steps):
+        plan.replay()
+    stop.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    el = start.elapsed_time(stop) / 1e3
+    units = plan.amp_rounds() * args.steps
+    best = {n: float(o[..., -1].max().item()) for n, o in plan.out.items()}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": units / el, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64+f32/f64 sums", "data": "synthetic",
+            "config": {"workload": wl["desc"], "instances": count,
+                       "amp_rounds_per_step": plan.amp_rounds(),
+                       "buckets": {n: int(c.shape[0]) for n, (c, _) in buckets.items()}},
+            "per_n_best_P_at_p64": best, "clocks": clk}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
-        if wl.get("kind") == "grad":
-            print(json.dumps({"impl": "reference", "unavailable": "the grad workload has no "
+        if wl.get("kind") in ("grad", "sweep"):
+            print(json.dumps({"impl": "reference", "unavailable": "this workload has no "
                               "bounded oracle arm; run the default workload"}))
             return 0
         return run_reference(args, wl)
     if wl.get("kind") == "grad":
         return run_grad(args, wl)
+    if wl.get("kind") == "sweep":
+        return run_sweep(args, wl)
     return run_ours(args, wl)
 
 

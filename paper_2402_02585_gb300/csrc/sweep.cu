@@ -80,8 +80,11 @@ __device__ __forceinline__ float2 ld_dsmem_f32x2(const float *p, unsigned rank) 
   return make_float2(x, y);
 }
 
+// 64 registers per thread, so small CTAs run several per SM (1024 threads in
+// all) and one CTA's reduction overlaps another's rounds.
 template <int kThreads, int kCluster>
-__global__ void __launch_bounds__(kThreads, 1) sweep_kernel(const __grid_constant__ SweepArgs a) {
+__global__ void __launch_bounds__(kThreads, (kThreads >= 1024 ? 1 : 1024 / kThreads))
+sweep_kernel(const __grid_constant__ SweepArgs a) {
   constexpr int kW = kThreads / 32;
   __shared__ float2 s_T[256];
   __shared__ float s_wp[2][kW][kSlots];        // warp partials (FP32)

@@ -8,8 +8,11 @@ chooses for its n:
   * "stream": gqaoa_evolve_batched with the instance's cost table shared by a
     chunk of angle points and a per-round trace of P(C=0); the chunk size is
     chosen so the chunk's states stay resident in L2.
-Every buffer and workspace is allocated when the plan is built, so the whole
-sequence of C-ABI calls can be captured into one CUDA graph and replayed.
+Every buffer and workspace is allocated when the plan is built. The on-chip
+buckets (one persistent launch each) are captured into one CUDA graph and
+replayed; the streaming buckets issue p + 3 launches per chunk of several GB
+each, so they run eagerly after the graph (launch overhead ~2 % there, and a
+graph of hundreds of thousands of nodes would cost more than it saves).
 """
 
 from __future__ import annotations
@@ -83,10 +86,12 @@ class SweepPlan:
     def amp_rounds(self) -> int:
         return sum(st[3].shape[0] * self.A * self.p * (1 << st[1]) for st in self.steps)
 
-    def run(self):
+    def run(self, onchip: bool = True, stream: bool = True):
         s = torch.cuda.current_stream().cuda_stream
         for kind, n, m, cost, out, extra in self.steps:
             B = cost.shape[0]
+            if (kind == "onchip" and not onchip) or (kind == "stream" and not stream):
+                continue
             if kind == "onchip":
                 ws = extra
                 C.gqaoa_sweep(cost.data_ptr(), n, m, B, self.g.data_ptr(), self.b.data_ptr(),
@@ -105,16 +110,18 @@ class SweepPlan:
         return self.out
 
     def capture(self):
-        """Record run() into a CUDA graph (after one eager warm-up run)."""
+        """Record the on-chip launches into a CUDA graph (after one eager
+        warm-up run of everything)."""
         self.run()
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
-            self.run()
+            self.run(onchip=True, stream=False)
         return self.graph
 
     def replay(self):
         self.graph.replay()
+        self.run(onchip=False, stream=True)
         return self.out
 
 

@@ -37,11 +37,11 @@ def _time_plan(plan: SweepPlan, reps: int = 3) -> float:
     return t0.elapsed_time(t1) / 1e3 / reps
 
 
-def tune(n_values, p: int = 16, angles: int = 64, verbose: bool = True) -> dict:
+def tune(n_values, p: int = 16, angles: int = 256, verbose: bool = True) -> dict:
     table = {}
     for n in n_values:
         m = int(math.floor(4.2 * n + 0.5))
-        B = max(1, min(8, (1 << 22) >> n))
+        B = max(1, min(8, (1 << 20) >> n))
         cost = torch.stack([core.build_cost(instances.random_3sat(n, m, 5000 + i), n)[0]
                             for i in range(B)])
         rng = np.random.default_rng(n)
@@ -50,8 +50,8 @@ def tune(n_values, p: int = 16, angles: int = 64, verbose: bool = True) -> dict:
         cands = []
         if C.GQAOA_SWEEP_MIN_N <= n <= C.GQAOA_SWEEP_MAX_N:
             cands.append({"path": "onchip"})
-        for S in (8, 16, 32, 64, 256, 1024):
-            if S <= angles or S == 8:
+        for S in (16, 64, 256):
+            if S <= angles and (S << n) * 8 <= (4 << 30):
                 cands.append({"path": "stream", "angle_batch": S})
         best = None
         for cand in cands:
