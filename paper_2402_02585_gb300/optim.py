@@ -111,25 +111,35 @@ def canonicalize(gammas: np.ndarray, betas: np.ndarray) -> np.ndarray:
 def single_angle_grid_start(cost: torch.Tensor, n: int, m: int, p: int, grid: int = 16,
                             objective: str = "p0"):
     """Best single angle pair (Eq. 5) on a grid x grid lattice of [0, 2pi) x [0, pi)
-    per instance, by batched evolution with a shared cost table per instance.
-    Returns gammas [B], betas [B] (numpy)."""
+    per instance (cost [B, 2^n]). P(C=0) of every lattice point comes from one
+    on-chip sweep (gqaoa_sweep) when n allows, else from batched evolution with
+    the instance's cost table shared by the lattice. Returns gammas [B], betas [B]."""
     B = cost.shape[0]
     gs = (np.arange(grid) + 0.5) * (2 * np.pi / grid)
     bs = (np.arange(grid) + 0.5) * (np.pi / grid)
     G = np.repeat(gs, grid)
     Bt = np.tile(bs, grid)
+    A = grid * grid
+    if objective == "p0" and C.GQAOA_SWEEP_MIN_N <= n <= C.GQAOA_SWEEP_MAX_N:
+        gd = torch.as_tensor(G, device=cost.device)
+        bd = torch.as_tensor(Bt, device=cost.device)
+        out = torch.empty((B, A, 1), dtype=torch.float64, device=cost.device)
+        ws = core.workspace(C.gqaoa_sweep_workspace_size(A), cost.device)
+        r = np.array([p], dtype=np.int32)
+        C.gqaoa_sweep(cost.data_ptr(), n, m, B, gd.data_ptr(), bd.data_ptr(), A, p, r.ctypes.data, 1,
+                      out.data_ptr(), ws.data_ptr(), ws.numel(),
+                      torch.cuda.current_stream().cuda_stream)
+        k = torch.argmax(out[:, :, 0], dim=1).cpu().numpy()
+        return G[k], Bt[k]
     Gm = np.repeat(G[:, None], p, 1)
     Bm = np.repeat(Bt[:, None], p, 1)
     best_g = np.zeros(B)
     best_b = np.zeros(B)
-    ws = None
     gd = torch.as_tensor(Gm, device=cost.device)
     bd = torch.as_tensor(Bm, device=cost.device)
-    state = torch.empty((grid * grid, 1 << n), dtype=torch.complex64, device=cost.device)
+    state = torch.empty((A, 1 << n), dtype=torch.complex64, device=cost.device)
+    ws = core.workspace(C.gqaoa_evolve_batched_workspace_size(n, A, p), cost.device)
     for i in range(B):
-        need = C.gqaoa_evolve_batched_workspace_size(n, grid * grid, p)
-        if ws is None or ws.numel() < need:
-            ws = core.workspace(need, cost.device)
         _, out, _ = core.evolve_batched(cost[i], n, m, gd, bd, shared_cost=True, state=state, ws=ws)
         col = out[:, 0] if objective == "p0" else -out[:, 1]
         k = int(torch.argmax(col).item())

@@ -150,3 +150,53 @@ def evaluate(prop, test, p: int, plain_steps: int = 200, max_steps: int = 200, l
         "mean_P_proposer_final": float(np.mean(P_prop)),
         "proposer_inference_s": float(np.sum(infer)),
     }
+
+
+def run(train_count=20000, train_n=range(10, 19), test_count=2000, test_n=(20,), d_lo=3.0,
+        d_hi=5.0, p=16, grid=16, label_steps=150, lr=0.05, epochs=200, batch=512, mlp_lr=1e-3,
+        plain_steps=200, max_steps=200, seed=0, log=print):
+    """The whole study; returns a dict of timings and the evaluation summary."""
+    from .proposer import Proposer
+    t = {}
+    t0 = time.perf_counter()
+    train = make_instances(train_count, seed=seed + 1, n_values=train_n, d_lo=d_lo, d_hi=d_hi)
+    test = make_instances(test_count, seed=seed + 2, n_values=test_n, d_lo=d_lo, d_hi=d_hi)
+    torch.cuda.synchronize()
+    t["instances_s"] = time.perf_counter() - t0
+    log(f"instances: {len(train)} train, {len(test)} test ({t['instances_s']:.1f} s)")
+    t0 = time.perf_counter()
+    X, Y = generate_labels(train, p=p, grid=grid, steps=label_steps, lr=lr)
+    torch.cuda.synchronize()
+    t["labels_s"] = time.perf_counter() - t0
+    log(f"labels: {t['labels_s']:.1f} s")
+    t0 = time.perf_counter()
+    prop = Proposer(p=p, seed=seed)
+    losses = prop.fit(X, Y, epochs=epochs, batch=batch, lr=mlp_lr, seed=seed)
+    torch.cuda.synchronize()
+    t["train_s"] = time.perf_counter() - t0
+    log(f"training: {t['train_s']:.1f} s, loss {losses[0]:.4f} -> {losses[-1]:.4f}")
+    t0 = time.perf_counter()
+    ev = evaluate(prop, test, p=p, plain_steps=plain_steps, max_steps=max_steps, lr=lr,
+                  seed=seed + 3)
+    t["evaluate_s"] = time.perf_counter() - t0
+    log(f"evaluation: {t['evaluate_s']:.1f} s")
+    return {"timings": t, "loss_first": losses[0], "loss_last": losses[-1],
+            "train_instances": len(train), "test_instances": len(test), "p": p, **ev}
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=20000)
+    ap.add_argument("--test", type=int, default=2000)
+    ap.add_argument("--p", type=int, default=16)
+    ap.add_argument("--epochs", type=int, default=200)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    res = run(train_count=a.train, test_count=a.test, p=a.p, epochs=a.epochs)
+    text = json.dumps(res, indent=1, default=float)
+    if a.out:
+        with open(a.out, "w") as fh:
+            fh.write(text + "\n")
+    print(text)
