@@ -204,6 +204,16 @@ struct PassArgs {
   float amp0;               // N^{-1/2}
 };
 
+// Programmatic dependent launch. A streaming pass is launched while the
+// previous one drains; it reads or writes no global memory before
+// griddepcontrol.wait, and it lets the next pass launch only after that wait
+// (so every kernel before the previous one has completed too). What overlaps
+// is the launch and CTA set-up of pass k+1 with the tail of pass k.
+__device__ __forceinline__ void pdl_wait_then_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Sum slot j of instance b's records in index order within warp 0.
 __device__ __forceinline__ double w0_parts(const PassArgs &a, int b, int j) {
   const int lane = threadIdx.x & 31;
@@ -257,6 +267,7 @@ __global__ void __launch_bounds__(kThreads, 4) round_kernel(const PassArgs a) {
   const int b = blockIdx.x / a.cpi, local = blockIdx.x % a.cpi;
   const size_t bk = (size_t)b * a.p + a.round;
 
+  pdl_wait_then_release();
   s_T[threadIdx.x] = a.phase[bk * 256 + threadIdx.x];
   if (warp == 0) {
     double2 av = make_double2(0.0, 0.0);
@@ -344,6 +355,7 @@ __global__ void __launch_bounds__(kThreads, 4) readout_kernel(const PassArgs a) 
   __shared__ double s_vals[kPartStride];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int b = blockIdx.x / a.cpi, local = blockIdx.x % a.cpi;
+  pdl_wait_then_release();
   if (warp == 0) {
     double2 av = make_double2(0.0, 0.0);
     if (kPending) {
@@ -431,6 +443,7 @@ __global__ void __launch_bounds__(kThreads, 4) lambda_init_kernel(const PassArgs
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int b = blockIdx.x / a.cpi, local = blockIdx.x % a.cpi;
   const size_t bk = (size_t)b * a.p + a.round;  // last forward round
+  pdl_wait_then_release();
   if (warp == 0) {
     const double Sre = w0_parts(a, b, 0), Sim = w0_parts(a, b, 1);
     const double2 al = a.alpha[bk];
@@ -488,6 +501,7 @@ backward_kernel(const PassArgs a, const float4 *__restrict__ chi_base) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int b = blockIdx.x / a.cpi, local = blockIdx.x % a.cpi;
   const size_t bk = (size_t)b * a.p + a.round;
+  pdl_wait_then_release();
   s_T[threadIdx.x] = a.phase[bk * 256 + threadIdx.x];
   if (warp == 0) {
     const double Lr = w0_parts(a, b, 0), Li = w0_parts(a, b, 1), G = w0_parts(a, b, 2);
@@ -731,13 +745,20 @@ static cudaError_t launch_pass(const Geometry &g, Kernel kernel, cudaStream_t st
   cfg.blockDim = dim3(kThreads, 1, 1);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)g.cluster;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[na].val.programmaticStreamSerializationAllowed = 1;
+  ++na;
+  if (g.cluster > 1) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = (unsigned)g.cluster;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = g.cluster > 1 ? 1 : 0;
+  cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
