@@ -80,18 +80,17 @@ __device__ __forceinline__ float2 ld_dsmem_f32x2(const float *p, unsigned rank) 
   return make_float2(x, y);
 }
 
-// One round over a thread's 16 amplitudes: chi = T[c] s + (T[c] a), then the
-// partial sums. kExtra adds the readout sums over C = 0 and the C = 0 count.
+// One round over a thread's 16 amplitudes: chi = T[c] (s + a), then the
+// partial sums. kExtra adds the readout sums over C = 0 and the C = 0 count
+// (only readout rounds and the first round pay for them).
 template <bool kExtra>
 __device__ __forceinline__ void round_body(float2 (&s)[16], const uint32_t (&cw)[4],
-                                           const float4 *s_T, float (&v)[kSlots], bool ro,
-                                           bool first) {
+                                           const float2 *s_T, float2 ad, float (&v)[kSlots],
+                                           bool ro, bool first) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     const unsigned c = (cw[j >> 2] >> (8 * (j & 3))) & 0xFFu;
-    const float4 t = s_T[c];
-    const float2 x = make_float2(fmaf(t.x, s[j].x, fmaf(-t.y, s[j].y, t.z)),
-                                 fmaf(t.x, s[j].y, fmaf(t.y, s[j].x, t.w)));
+    const float2 x = cmul(s_T[c], make_float2(s[j].x + ad.x, s[j].y + ad.y));
     s[j] = x;
     v[0] += x.x;
     v[1] += x.y;
@@ -108,11 +107,10 @@ template <int kThreads, int kCluster>
 __global__ void __launch_bounds__(kThreads, (kThreads >= 1024 ? 1 : 1024 / kThreads))
 sweep_kernel(const __grid_constant__ SweepArgs a) {
   constexpr int kW = kThreads / 32;
-  // per cost class c: (T[c], T[c] * a) with a the pending mixer add, so a
-  // round is chi = T s + T a = two FMAs per component
-  __shared__ float4 s_T[256];
+  __shared__ float2 s_T[256];
   __shared__ float s_wp[2][kW][kSlots];        // warp partials (FP32)
   __shared__ float s_cp[2][kSlots][2];         // CTA partials (double-float), read cluster-wide
+  __shared__ float2 s_a;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned rank = kCluster > 1 ? cluster_ctarank() : 0u;
   const uint64_t cluster_id = blockIdx.x / kCluster, nclusters = gridDim.x / kCluster;
@@ -126,10 +124,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
     const int ai = (int)(item % (uint64_t)a.A);
     const uint4 cw = *reinterpret_cast<const uint4 *>(
         a.cost + b * N + 16ull * ((uint64_t)rank * kThreads + threadIdx.x));
-    for (int i = threadIdx.x; i < 256; i += kThreads) {
-      const float2 t = a.phase[(size_t)ai * 256 + i];
-      s_T[i] = make_float4(t.x, t.y, 0.f, 0.f);  // no pending add before round 1
-    }
+    for (int i = threadIdx.x; i < 256; i += kThreads) s_T[i] = a.phase[(size_t)ai * 256 + i];
     const double2 ald = a.alpha[ai];
     const float alr = (float)ald.x, ali = (float)ald.y;
     __syncthreads();
@@ -137,6 +132,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
     float2 s[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) s[j] = make_float2(amp0, 0.f);
+    float2 ad = make_float2(0.f, 0.f);  // pending mixer add
     float cnt0 = 0.f;  // C = 0 count of the instance (warp 0 keeps it)
     int ridx = 0;
     for (int r = 0; r < a.p; ++r) {
@@ -144,9 +140,9 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
       const bool first = r == 0;
       float v[kSlots] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (ro || first) {
-        round_body<true>(s, cwords, s_T, v, ro, first);
+        round_body<true>(s, cwords, s_T, ad, v, ro, first);
       } else {
-        round_body<false>(s, cwords, s_T, v, false, false);
+        round_body<false>(s, cwords, s_T, ad, v, false, false);
       }
       const int nv = (ro || first) ? kSlots : 2;
 #pragma unroll
@@ -190,13 +186,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
       if (warp == 0) {
         const float Sr = hi[0] + lo[0], Si = hi[1] + lo[1];
         const float ar = (alr * Sr - ali * Si) * inv_n, aim = (alr * Si + ali * Sr) * inv_n;
-        // next round's pending-add table: T[c] * a for every class
-        for (int c = lane; c < 256; c += 32) {
-          float4 t = s_T[c];
-          t.z = fmaf(t.x, ar, -t.y * aim);
-          t.w = fmaf(t.x, aim, t.y * ar);
-          s_T[c] = t;
-        }
+        if (lane == 0) s_a = make_float2(ar, aim);
         if (first) cnt0 = hi[5] + lo[5];
         if (ro && rank == 0 && lane == 0) {
           // sum_{C=0} |chi + a|^2 = A0 + 2 Re(conj(a) B0) + h[0] |a|^2
@@ -208,6 +198,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
         }
       }
       __syncthreads();
+      ad = s_a;
       if (ro) ++ridx;
       buf ^= 1;
     }
