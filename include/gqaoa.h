@@ -245,7 +245,9 @@ int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const double *gamm
  *   x = [h[c]/2^n for c = 0..d_in-3 (zero-padded), n/32, m/128]
  *   z1 = W1 x + b1, h1 = GELU(z1); z2 = W2 h1 + b2, h2 = GELU(z2);
  *   o = W3 h2 + b3; angles = 2 pi sigmoid(o) (d_out = 2p: p gammas, p betas)
- *   loss = mean over batch and outputs of (angles - labels)^2
+ *   loss = mean over batch and outputs of 2 (1 - cos(angles - labels))
+ *          (angles are 2 pi periodic; equal to the squared error for small
+ *          differences)
  * GELU(x) = x Phi(x), exact normal CDF. FP32 throughout (loss in FP64).
  * params: device float, one flat vector [W1 (d_h x d_in), b1, W2 (d_h x d_h),
  * b2, W3 (d_out x d_h), b3], row-major. x: device float [batch][d_in].
@@ -256,7 +258,7 @@ int gqaoa_mlp_workspace_size(int batch, int d_in, int d_h, int d_out, size_t *by
 /* angles: device float [batch][d_out] written. */
 int gqaoa_mlp_forward(const float *params, int d_in, int d_h, int d_out, const float *x,
                       int batch, float *angles, void *ws, size_t ws_bytes, void *stream);
-/* Forward + backward of the MSE loss against labels (device float
+/* Forward + backward of the periodic loss against labels (device float
  * [batch][d_out]); grads: device float [param_count] written; loss: device
  * double [1] written. */
 int gqaoa_mlp_backward(const float *params, int d_in, int d_h, int d_out, const float *x,

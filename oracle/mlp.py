@@ -12,7 +12,11 @@ states (Section V). The proposer is a small MLP on that density of states:
   z2 = W2 h1 + b2, h2 = GELU(z2)
   o  = W3 h2 + b3
   angles = 2 pi sigmoid(o)     (first p entries gammas, last p betas)
-  loss = mean over the batch and the 2p outputs of (angles - labels)^2
+  loss = mean over the batch and the 2p outputs of 2 (1 - cos(angles - labels))
+
+The angles are 2 pi periodic (C is an integer, H_M a projector), so the loss is
+the squared chord between the angles on the unit circle; it equals the squared
+difference to fourth order and does not penalise a wrap through 0 = 2 pi.
 
 GELU(x) = x Phi(x) with the exact normal CDF Phi(x) = (1 + erf(x / sqrt 2)) / 2.
 Adam: m <- b1 m + (1-b1) g; v <- b2 v + (1-b2) g^2;
@@ -80,8 +84,8 @@ def loss_and_grad(params, x, labels, dims):
     ang, (x, z1, h1, z2, h2, o, s) = forward(params, x, dims)
     B = x.shape[0]
     diff = ang - labels
-    loss = float(np.mean(diff ** 2))
-    dang = 2.0 * diff / (B * d_out)
+    loss = float(np.mean(2.0 * (1.0 - np.cos(diff))))
+    dang = 2.0 * np.sin(diff) / (B * d_out)
     do = dang * 2 * np.pi * s * (1 - s)
     dW3 = do.T @ h2
     db3 = do.sum(0)

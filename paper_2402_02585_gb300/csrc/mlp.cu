@@ -8,7 +8,8 @@
 // cost histogram h[c] / 2^n (its density of states), n and m to p angle pairs:
 //
 //   z1 = W1 x + b1, h1 = GELU(z1); z2 = W2 h1 + b2, h2 = GELU(z2);
-//   o = W3 h2 + b3;  angles = 2 pi sigmoid(o);  loss = mean (angles - labels)^2
+//   o = W3 h2 + b3;  angles = 2 pi sigmoid(o);
+//   loss = mean 2 (1 - cos(angles - labels))   (angles are 2 pi periodic)
 //
 // GELU uses the exact normal CDF (erff). The layers are small dense
 // contractions (d_in = 130, d_h = 256, d_out = 32 at the bench shape): they run
@@ -128,7 +129,8 @@ static cudaError_t gemm(const GemmArgs &g, cudaStream_t st) {
   return cudaPeekAtLastError();
 }
 
-// angles = 2 pi sigmoid(o); with labels: dO and per-block loss partials.
+// angles = 2 pi sigmoid(o); with labels: the periodic loss 2 (1 - cos(d)),
+// d = angle - label, its gradient 2 sin(d) / count, and per-block loss partials.
 __global__ void head_kernel(const float *__restrict__ o, const float *__restrict__ labels,
                             int64_t total, float inv_count, float *__restrict__ angles,
                             float *__restrict__ dO, double *__restrict__ loss_parts) {
@@ -140,9 +142,12 @@ __global__ void head_kernel(const float *__restrict__ o, const float *__restrict
     const float a = kTwoPi * s;
     if (angles) angles[i] = a;
     if (labels) {
-      const float d = a - labels[i];
-      l += (double)d * d;
-      dO[i] = 2.0f * d * inv_count * kTwoPi * s * (1.0f - s);
+      // 2 (1 - cos d) = 4 sin^2(d/2) and 2 sin d = 4 sin(d/2) cos(d/2): no
+      // cancellation for small d
+      float sh, ch;
+      sincosf(0.5f * (a - labels[i]), &sh, &ch);
+      l += 4.0 * (double)sh * (double)sh;
+      dO[i] = 4.0f * sh * ch * inv_count * kTwoPi * s * (1.0f - s);
     }
   }
   if (labels) {

@@ -6,7 +6,8 @@ clause count (Section III.B, Fig. 2; Appendix D) and suggests determining
 angles from statistics of the density of states (Section V). The proposer
 reads x = [h[c]/2^n (padded to d_in - 2), n/32, m/128] and outputs
 angles = 2 pi sigmoid(MLP(x)), the first p gammas then p betas. It is trained
-by mean-squared error to canonicalised angles that the batched optimizer
+with the periodic loss 2 (1 - cos(angle - label)) to canonicalised angles that
+the batched optimizer
 (`optim.AngleOptimizer`) produces; gqaoa_mlp_backward and gqaoa_adam_f32 do
 every step. At inference the plain optimizer starts from the proposal and
 remains the judge: the proposer only chooses the starting point.
@@ -78,7 +79,7 @@ class Proposer:
 
     # ------------------------------------------------------------ training
     def train_step(self, x: torch.Tensor, labels: torch.Tensor, lr: float) -> torch.Tensor:
-        """One Adam step on the MSE loss of a batch; returns the loss (device)."""
+        """One Adam step on the periodic loss of a batch; returns the loss (device)."""
         B = x.shape[0]
         ws = self._workspace(B)
         s = torch.cuda.current_stream().cuda_stream

@@ -44,7 +44,7 @@ def test_forward_and_grad_match_torch_float64():
     h1 = torch.nn.functional.gelu(torch.nn.functional.linear(X, W1.view(d_h, d_in), b1))
     h2 = torch.nn.functional.gelu(torch.nn.functional.linear(h1, W2.view(d_h, d_h), b2))
     a = 2 * np.pi * torch.sigmoid(torch.nn.functional.linear(h2, W3.view(d_out, d_h), b3))
-    L = torch.mean((a - torch.tensor(y)) ** 2)
+    L = torch.mean(2 * (1 - torch.cos(a - torch.tensor(y))))
     L.backward()
     assert np.allclose(ang, a.detach().numpy(), atol=1e-12)
     assert abs(loss - L.item()) < 1e-12
@@ -75,3 +75,15 @@ def test_adam_first_step_is_signed_lr():
 def test_features_layout():
     x = mlp.features([2, 3, 1], n=2, m=2, d_in=8)
     assert np.allclose(x, [0.5, 0.75, 0.25, 0, 0, 0, 2 / 32, 2 / 128])
+
+
+def test_loss_is_periodic_and_quadratic_near_zero():
+    params, x, y = _data(B=3, seed=4)
+    ang, _ = mlp.forward(params, x, DIMS)
+    l0, _ = mlp.loss_and_grad(params, x, ang, DIMS)
+    assert abs(l0) < 1e-15
+    l1, _ = mlp.loss_and_grad(params, x, ang + 2 * np.pi, DIMS)
+    assert abs(l1) < 1e-12
+    d = 1e-3
+    l2, _ = mlp.loss_and_grad(params, x, ang + d, DIMS)
+    assert abs(l2 - d * d) < 1e-12
