@@ -92,28 +92,44 @@ def generate_labels(insts, p: int, grid: int = 16, steps: int = 150, lr: float =
     return X, Y
 
 
+def _first_hits(values: np.ndarray, target: np.ndarray) -> np.ndarray:
+    ok = values >= target[None, :]
+    return np.where(ok.any(0), ok.argmax(0), -1)
+
+
 def evaluate(prop, test, p: int, plain_steps: int = 200, max_steps: int = 200, lr: float = 0.05,
-             seed: int = 0):
-    """Steps and wall-seconds to reach 95 % of the plain optimizer's final P."""
-    steps_plain, steps_prop, wall_plain, wall_prop = [], [], [], []
-    P_plain, P_prop, infer = [], [], []
-    hits = 0
-    # the proposer is a loaded, warm model: one untimed call brings its kernels in
-    prop.propose(features(test[:1]))
+             seed: int = 0, grid: int = 16):
+    """Steps and wall-seconds to reach 95 % of two plain baselines' final P:
+      * "random": Adam from angles uniform in [0, pi) (the configs' initialisation);
+      * "grid": Appendix C's protocol, the best single angle pair on a grid x grid
+        lattice, then Adam over all 2p angles (its wall time includes the grid scan).
+    The proposed start runs once; its first evaluation reaching each target is
+    recorded. A proposal that never reaches a target falls back to that
+    baseline and is charged its own budget plus the baseline's time."""
+    res = {k: {"steps_plain": [], "steps_prop": [], "wall_plain": [], "wall_prop": [], "hits": 0,
+               "P_plain": []} for k in ("random", "grid")}
+    P_prop, infer = [], []
+    prop.propose(features(test[:1]))  # a loaded, warm model: bring its kernels in
     torch.cuda.synchronize()
     for n, idx in _groups(test, p):
         cost = torch.stack([test[i]["cost"] for i in idx])
         m = max(test[i]["m"] for i in idx)
         opt = AngleOptimizer(cost, n, m, p)
+        base = {}
+        # baseline 1: random start
         G = np.stack([instances.random_angles(p, seed * 1_000_003 + i)[0] for i in idx])
         Bt = np.stack([instances.random_angles(p, seed * 1_000_003 + i)[1] for i in idx])
         opt.reset(G, Bt)
-        plain = opt.run(plain_steps, lr=lr)
-        final = plain["values"][-1]
-        target = 0.95 * final
-        ok = plain["values"] >= target[None, :]
-        first_plain = ok.argmax(0)
-        # proposer: features + inference + the same optimizer from the proposal
+        base["random"] = (opt.run(plain_steps, lr=lr), 0.0)
+        # baseline 2: single-angle grid, then all angles
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g0, b0 = single_angle_grid_start(cost, n, m, p, grid=grid)
+        torch.cuda.synchronize()
+        t_grid = time.perf_counter() - t0
+        opt.reset(np.repeat(g0[:, None], p, 1), np.repeat(b0[:, None], p, 1))
+        base["grid"] = (opt.run(plain_steps, lr=lr), t_grid)
+        # the proposer: features + inference + the same optimizer from the proposal
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         x = features([test[i] for i in idx])
@@ -122,34 +138,42 @@ def evaluate(prop, test, p: int, plain_steps: int = 200, max_steps: int = 200, l
         t_infer = time.perf_counter() - t0
         infer.append(t_infer)
         opt.reset(g, b)
-        run = opt.run(max_steps, lr=lr, target=target)
-        first = run["first_hit"]
-        for j in range(len(idx)):
-            sp = int(first_plain[j])
-            steps_plain.append(sp)
-            wall_plain.append(plain["wall"][sp])
-            P_plain.append(final[j])
-            P_prop.append(run["values"][-1][j])
-            if first[j] >= 0:
-                hits += 1
-                steps_prop.append(int(first[j]))
-                wall_prop.append(t_infer + run["wall"][first[j]])
-            else:  # fallback: the proposal's budget is spent, then the plain run
-                steps_prop.append(max_steps + sp)
-                wall_prop.append(t_infer + run["wall"][-1] + plain["wall"][sp])
-    N = len(steps_plain)
-    return {
-        "instances": N,
-        "median_steps_plain": float(np.median(steps_plain)),
-        "median_steps_proposer": float(np.median(steps_prop)),
-        "median_wall_plain": float(np.median(wall_plain)),
-        "median_wall_proposer": float(np.median(wall_prop)),
-        "hit_rate": hits / N,
-        "fallback_rate": 1.0 - hits / N,
-        "mean_P_plain": float(np.mean(P_plain)),
-        "mean_P_proposer_final": float(np.mean(P_prop)),
-        "proposer_inference_s": float(np.sum(infer)),
-    }
+        run = opt.run(max_steps, lr=lr)
+        P_prop.extend(run["values"][-1].tolist())
+        for key, (pl, t_pre) in base.items():
+            final = pl["values"][-1]
+            target = 0.95 * final
+            first_plain = _first_hits(pl["values"], target)
+            first = _first_hits(run["values"], target)
+            r = res[key]
+            for j in range(len(idx)):
+                sp = int(first_plain[j])
+                r["steps_plain"].append(sp)
+                r["wall_plain"].append(t_pre + pl["wall"][sp])
+                r["P_plain"].append(final[j])
+                if first[j] >= 0:
+                    r["hits"] += 1
+                    r["steps_prop"].append(int(first[j]))
+                    r["wall_prop"].append(t_infer + run["wall"][first[j]])
+                else:
+                    r["steps_prop"].append(max_steps + sp)
+                    r["wall_prop"].append(t_infer + run["wall"][-1] + t_pre + pl["wall"][sp])
+    N = len(P_prop)
+    out = {"instances": N, "mean_P_proposer_final": float(np.mean(P_prop)),
+           "proposer_inference_s": float(np.sum(infer))}
+    for key, r in res.items():
+        out[key] = {
+            "median_steps_plain": float(np.median(r["steps_plain"])),
+            "median_steps_proposer": float(np.median(r["steps_prop"])),
+            "median_wall_plain": float(np.median(r["wall_plain"])),
+            "median_wall_proposer": float(np.median(r["wall_prop"])),
+            "hit_rate": r["hits"] / N,
+            "fallback_rate": 1.0 - r["hits"] / N,
+            "mean_P_plain": float(np.mean(r["P_plain"])),
+        }
+    # the headline comparison is against the random-start optimizer of the configs
+    out.update({k: out["random"][k] for k in out["random"]})
+    return out
 
 
 def run(train_count=20000, train_n=range(10, 19), test_count=2000, test_n=(20,), d_lo=3.0,
