@@ -594,9 +594,11 @@ struct SmallArgs {
   int B;
 };
 
-__device__ __forceinline__ double small_round(float2 (&s)[kSmallPer], const unsigned (&c)[kSmallPer],
-                                              const float2 *T, const double2 al, int N, double inv_n,
-                                              double *s_scr, float2 *ck, double *rec, double *P) {
+// One round of the small-state kernel on a thread's amplitudes; writes the
+// round's record (S_k, a_k), the checkpoint chi_k if asked, and *P = P(C=0).
+__device__ __forceinline__ void small_round(float2 (&s)[kSmallPer], const unsigned (&c)[kSmallPer],
+                                            const float2 *T, const double2 al, int N, double inv_n,
+                                            double *s_scr, float2 *ck, double *rec, double *P) {
   double lr = 0.0, li = 0.0;
 #pragma unroll
   for (int j = 0; j < kSmallPer; ++j) {
@@ -623,7 +625,6 @@ __device__ __forceinline__ double small_round(float2 (&s)[kSmallPer], const unsi
   }
   *P = block_sum(lp, s_scr);
   if (threadIdx.x == 0) { rec[0] = Sre; rec[1] = Sim; rec[2] = ar; rec[3] = ai; }
-  return 0.0;
 }
 
 __global__ void __launch_bounds__(kThreads) evolve_small_kernel(const SmallArgs a) {

@@ -47,13 +47,6 @@ struct SweepArgs {
   int rounds[kSweepMaxRounds];  // ascending, 1-based
 };
 
-// Double-float accumulate of a float.
-__device__ __forceinline__ void df_add(float &hi, float &lo, float x) {
-  float s, e;
-  two_sum(hi, x, s, e);
-  hi = s;
-  lo = __fadd_rn(lo, e);
-}
 // Double-float butterfly over the warp (every lane ends with the same sum).
 __device__ __forceinline__ void df_warp(float &hi, float &lo) {
 #pragma unroll
