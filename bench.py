@@ -447,6 +447,7 @@ def run_grad(args, wl):
                          "frac": achieved / peak, "traffic": None, "peak_kind": kind,
                          "kernel": "forward rounds + backward rounds (mean over the step)"},
             "adam_steps_per_s": args.steps / el, "mean_P_after": float(v.mean()),
+            "cpu_baseline": cpu_grad_baseline(wl),
             "gpu_launches": (p + 1 + p + 1 + 1 + 1) * args.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
@@ -480,18 +481,33 @@ def run_sweep(args, wl):
     for _ in range(max(0, args.warmup - 1)):
         plan.replay()
     torch.cuda.synchronize()
-    start = torch.cuda.Event(enable_timing=True)
-    stop = torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
     clocks = ClockSampler(local)
     clocks.start()
-    start.record()
-    for _ in range(args.steps):
-        plan.replay()
-    stop.record()
+    ev[0].record()
+    for i in range(args.steps):
+        plan.graph.replay()                    # on-chip buckets (one graph)
+        ev[2 * i + 1].record()
+        plan.run(onchip=False, stream=True)    # streaming buckets
+        ev[2 * i + 2].record()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    el = start.elapsed_time(stop) / 1e3
+    el = ev[0].elapsed_time(ev[-1]) / 1e3
+    t_on = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)) / 1e3
+    t_st = sum(ev[2 * i + 1].elapsed_time(ev[2 * i + 2]) for i in range(args.steps)) / 1e3
     units = plan.amp_rounds() * args.steps
+    ar_on = sum(c.shape[0] * plan.A * plan.p * (1 << n) for kind, n, m, c, o, x in plan.steps
+                if kind == "onchip") * args.steps
+    ar_st = units - ar_on
+    peak, kind = hbm_peak()
+    # on-chip: issue ceiling from unit counts and clocks: 4 warp-instructions per
+    # clock per SM x 32 lanes x SMs x max SM clock, over the 12 instructions of
+    # one amplitude-round (phase lookup, complex multiply-add, sums, cost byte)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = 4 * 32 * sms * 2.07e9 / 12
+    # streaming: 8 B read + 8 B write per amplitude-round (the shared cost table
+    # stays in L2 across a chunk of 256 angle points)
+    st_gbs = 16 * ar_st / t_st / 1e9 if t_st > 0 else None
     best = {n: float(o[..., -1].max().item()) for n, o in plan.out.items()}
     if rank == 0:
         print(json.dumps({
@@ -502,8 +518,70 @@ def run_sweep(args, wl):
             "config": {"workload": wl["desc"], "instances": count,
                        "amp_rounds_per_step": plan.amp_rounds(),
                        "buckets": {n: int(c.shape[0]) for n, (c, _) in buckets.items()}},
+            "roofline": {"bound": "hbm", "achieved": st_gbs, "peak": peak, "unit": "GB/s",
+                         "frac": (st_gbs / peak) if st_gbs else None, "traffic": None,
+                         "peak_kind": kind, "kernel": "streaming round_kernel (n >= 19 buckets, "
+                         f"{100 * t_st / el:.0f} % of the time)", "alg_bytes_per_amp_round": 16},
+            "roofline_onchip": {"bound": "alu", "achieved": ar_on / t_on if t_on > 0 else None,
+                                "peak": alu_peak, "unit": "amp-rounds/s",
+                                "frac": (ar_on / t_on / alu_peak) if t_on > 0 else None,
+                                "kernel": "sweep_kernel (n <= 18 buckets)",
+                                "peak_derivation": "4 warp-instr/clk/SM x 32 x SMs x 2.07 GHz / 12 "
+                                                   "instructions per amplitude-round"},
+            "cpu_baseline": cpu_sweep_baseline(wl) if world == 1 else None,
+            "gpu_launches": None,
             "per_n_best_P_at_p64": best, "clocks": clk}), flush=True)
     return 0
+
+
+def cpu_sweep_baseline(wl):
+    """The FP64 statevector oracle on a bounded sample of the sweep: one
+    (instance, grid point) per n in 12..20 for all p rounds with the P trace."""
+    from oracle import statevector as sv
+    from paper_2402_02585_gb300 import instances
+    if os.environ.get("GQAOA_BENCH_NO_CPU") == "1":
+        return None
+    done = 0
+    t = 0.0
+    for n in range(12, 21):
+        m = instances.clause_count(n, 4.2)
+        cost, _ = sv.cost_table(instances.random_3sat(n, m, n), n)
+        t0 = time.perf_counter()
+        sv.evolve(cost, n, [0.4] * wl["p"], [2.0] * wl["p"], trace=True)
+        t += time.perf_counter() - t0
+        done += wl["p"] * (1 << n)
+    return {"value": done / t, "unit": UNIT, "cores": _oracle_threads(), "kind": "oracle",
+            "sample": f"one single-angle-pair item per n = 12..20 (m = round(4.2 n)), p = {wl['p']} "
+                      "rounds with the P(C=0) trace, statevector oracle; cost tables untimed"}
+
+
+def _oracle_threads():
+    from oracle import statevector as sv
+    return sv.num_threads()
+
+
+def cpu_grad_baseline(wl):
+    """The oracle's gradient on one instance of the workload: central finite
+    differences (h = 1e-4) of the statevector oracle, 4p evolutions of p rounds.
+    Value in the same unit as the GPU line: p * 2^n amplitude-rounds per gradient."""
+    from oracle import statevector as sv
+    from paper_2402_02585_gb300 import instances
+    if os.environ.get("GQAOA_BENCH_NO_CPU") == "1":
+        return None
+    n, m, p = wl["n"], wl["m"], wl["p"]
+    cost, _ = sv.cost_table(instances.random_3sat(n, m, wl["seed"]), n)
+    g, b = instances.random_angles(p, wl["seed"])
+    t0 = time.perf_counter()
+    for arr in (g, b):
+        for k in range(p):
+            for d in (1e-4, -2e-4):
+                arr[k] += d
+                sv.readout(sv.evolve(cost, n, g, b), cost, n)
+            arr[k] += 1e-4
+    t = time.perf_counter() - t0
+    return {"value": p * (1 << n) / t, "unit": UNIT, "cores": _oracle_threads(), "kind": "oracle",
+            "sample": f"one instance n={n} m={m} p={p}: central-difference gradient of P(C=0) "
+                      f"by the statevector oracle ({4 * p} evolutions, {t:.1f} s)"}
 
 
 def main():
