@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "gqaoa.h"
@@ -21,6 +22,15 @@ namespace gq {
     if ((call) != cudaSuccess) return GQAOA_ECUDA;                             \
   } while (0)
 
+// NVTX range around a C-ABI call, so profilers show each call as one range
+// over its kernels (header-only NVTX; a no-op unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 inline bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -33,9 +43,6 @@ constexpr int kWarps = kThreads / 32;  // warps per CTA
 constexpr int kVecPerThread = 8;       // float4 (2 amplitudes) per thread per tile
 constexpr int kWarpTileAmps = 32 * kVecPerThread * 2;  // 512 amplitudes
 constexpr int kTileAmps = kWarps * kWarpTileAmps;      // 4096 amplitudes per CTA tile
-constexpr int kTileLog2 = 12;
-constexpr int kClusterMax = 8;
-constexpr int kMaxParts = 4096;        // max partial records per reduction
 constexpr int kPartStride = 8;         // doubles per partial record
 
 // ---------------------------------------------------------------------------
@@ -43,9 +50,6 @@ constexpr int kPartStride = 8;         // doubles per partial record
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
 // Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
@@ -139,15 +143,6 @@ __device__ __forceinline__ void cluster_reduce_store(const double *vals, int nva
     out_rec[threadIdx.x] = acc;
   }
   cluster_sync();  // keep every CTA's shared memory alive until rank 0 is done
-}
-
-// Sum slot `j` of `nparts` records of stride kPartStride, in index order
-// split over the CTA; every thread returns the same value in every CTA.
-__device__ __forceinline__ double sum_parts(const double *parts, int nparts, int j,
-                                            double *scratch) {
-  double v = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += parts[(size_t)i * kPartStride + j];
-  return block_sum(v, scratch);
 }
 
 }  // namespace gq

@@ -196,6 +196,7 @@ static const uint32_t kLanePattern[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 
 
 extern "C" int gqaoa_build_cost(const int32_t *lits, int n, int m, uint8_t *cost, uint64_t *hist,
                                 void *stream) {
+  gq::NvtxRange nvtx_range("gqaoa_build_cost");
   if (n < 1 || n > GQAOA_MAX_N || m < 0 || m > GQAOA_MAX_M) return GQAOA_ERANGE;
   if (!cost || (m > 0 && !lits)) return GQAOA_EINVAL;
   for (int i = 0; i < 3 * m; ++i) {

@@ -318,6 +318,7 @@ extern "C" int gqaoa_mlp_workspace_size(int batch, int d_in, int d_h, int d_out,
 extern "C" int gqaoa_mlp_forward(const float *params, int d_in, int d_h, int d_out, const float *x,
                                  int batch, float *angles, void *ws, size_t ws_bytes,
                                  void *stream) {
+  gq::NvtxRange nvtx_range("gqaoa_mlp_forward");
   int rc = check_dims(batch, d_in, d_h, d_out);
   if (rc) return rc;
   if (!params || !x || !angles || !ws) return GQAOA_EINVAL;
@@ -337,6 +338,7 @@ extern "C" int gqaoa_mlp_forward(const float *params, int d_in, int d_h, int d_o
 extern "C" int gqaoa_mlp_backward(const float *params, int d_in, int d_h, int d_out, const float *x,
                                   const float *labels, int batch, float *grads, double *loss,
                                   void *ws, size_t ws_bytes, void *stream) {
+  gq::NvtxRange nvtx_range("gqaoa_mlp_backward");
   int rc = check_dims(batch, d_in, d_h, d_out);
   if (rc) return rc;
   if (!params || !x || !labels || !grads || !loss || !ws) return GQAOA_EINVAL;

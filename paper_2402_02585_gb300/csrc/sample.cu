@@ -341,6 +341,7 @@ extern "C" int gqaoa_sample_workspace_size(int n, int64_t shots, size_t *bytes) 
 
 extern "C" int gqaoa_sample(const void *state, int n, uint64_t seed, int64_t shots,
                             uint64_t *out_idx, void *ws, size_t ws_bytes, void *stream) {
+  gq::NvtxRange nvtx_range("gqaoa_sample");
   if (n < 1 || n > GQAOA_MAX_N || shots < 0 || shots > (1ll << 32)) return GQAOA_ERANGE;
   if (!state || (shots > 0 && !out_idx)) return GQAOA_EINVAL;
   if (!aligned16(state) || (out_idx && !aligned8(out_idx))) return GQAOA_EINVAL;

@@ -972,6 +972,7 @@ extern "C" int gqaoa_evolve_batched_workspace_size(int n, int batch, int p, size
 extern "C" int gqaoa_evolve(const uint8_t *cost, int n, int m, const double *gammas,
                             const double *betas, int p, void *state, double *out, double *trace,
                             void *ws, size_t ws_bytes, unsigned flags, void *stream) {
+  gq::NvtxRange nvtx_range("gqaoa_evolve");
   return evolve_impl(cost, 0, n, m, 1, gammas, betas, p, state, out, trace, ws, ws_bytes, flags,
                      static_cast<cudaStream_t>(stream));
 }
@@ -980,6 +981,7 @@ extern "C" int gqaoa_evolve_batched(const uint8_t *cost, int64_t cost_stride, in
                                     int batch, const double *gammas, const double *betas, int p,
                                     void *state, double *out, double *trace, void *ws,
                                     size_t ws_bytes, unsigned flags, void *stream) {
+  gq::NvtxRange nvtx_range("gqaoa_evolve_batched");
   if (cost_stride < 0) return GQAOA_EINVAL;
   return evolve_impl(cost, (uint64_t)cost_stride, n, m, batch, gammas, betas, p, state, out, trace,
                      ws, ws_bytes, flags, static_cast<cudaStream_t>(stream));
@@ -1000,6 +1002,7 @@ extern "C" int gqaoa_grad_batched_workspace_size(int n, int batch, int p, size_t
 extern "C" int gqaoa_grad(const uint8_t *cost, int n, int m, const double *gammas,
                           const double *betas, int p, int objective, double *value, double *dgamma,
                           double *dbeta, void *ws, size_t ws_bytes, void *stream) {
+  gq::NvtxRange nvtx_range("gqaoa_grad");
   return grad_impl(cost, 0, n, m, 1, gammas, betas, p, objective, value, dgamma, dbeta, ws,
                    ws_bytes, static_cast<cudaStream_t>(stream));
 }
@@ -1008,6 +1011,7 @@ extern "C" int gqaoa_grad_batched(const uint8_t *cost, int64_t cost_stride, int 
                                   int batch, const double *gammas, const double *betas, int p,
                                   int objective, double *value, double *dgamma, double *dbeta,
                                   void *ws, size_t ws_bytes, void *stream) {
+  gq::NvtxRange nvtx_range("gqaoa_grad_batched");
   if (cost_stride < 0) return GQAOA_EINVAL;
   return grad_impl(cost, (uint64_t)cost_stride, n, m, batch, gammas, betas, p, objective, value,
                    dgamma, dbeta, ws, ws_bytes, static_cast<cudaStream_t>(stream));
@@ -1042,6 +1046,7 @@ readout_small_kernel(const float2 *__restrict__ state, const uint8_t *__restrict
 
 extern "C" int gqaoa_prob(const void *state, const uint8_t *cost, int n, double *out, void *ws,
                           size_t ws_bytes, void *stream) {
+  gq::NvtxRange nvtx_range("gqaoa_prob");
   if (n < 1 || n > GQAOA_MAX_N) return GQAOA_ERANGE;
   if (!state || !cost || !out) return GQAOA_EINVAL;
   if (!aligned16(state) || !aligned16(cost) || !aligned8(out)) return GQAOA_EINVAL;

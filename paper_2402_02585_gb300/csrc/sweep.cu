@@ -280,6 +280,7 @@ extern "C" int gqaoa_sweep_workspace_size(int angles, size_t *bytes) {
 extern "C" int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const double *gammas,
                            const double *betas, int angles, int p, const int32_t *rounds,
                            int nrounds, double *out, void *ws, size_t ws_bytes, void *stream) {
+  gq::NvtxRange nvtx_range("gqaoa_sweep");
   if (n < GQAOA_SWEEP_MIN_N || n > GQAOA_SWEEP_MAX_N || m < 0 || m > GQAOA_MAX_M || batch < 1 ||
       angles < 1 || angles > (1 << 24) || p < 1 || p > (1 << 20) || nrounds < 1 ||
       nrounds > kSweepMaxRounds)
