@@ -331,3 +331,47 @@ def test_single_angle_gradient_is_round_sum():
     fb = (reduced.objective_value(h, [gam] * p, [bet + eps] * p)
           - reduced.objective_value(h, [gam] * p, [bet - eps] * p)) / (2 * eps)
     assert abs(dg.sum().item() - fg) < 1e-4 and abs(db.sum().item() - fb) < 1e-4
+
+
+@pytest.mark.parametrize("n", [10, 16])
+def test_cuda_graph_capture_replays_bit_identical(n):
+    # every C-ABI call is asynchronous and allocation-free, so the whole path
+    # (cost table, p rounds with programmatic dependent launches, readout,
+    # shots) can be captured once and replayed
+    from paper_2402_02585_gb300 import _capi as C
+    m, p, shots = 4 * n, 9, 5000
+    lits = np.ascontiguousarray(instances.random_3sat(n, m, 77), dtype=np.int32)
+    g, b = instances.random_angles(p, 77)
+    gd = torch.as_tensor(g, device="cuda")
+    bd = torch.as_tensor(b, device="cuda")
+    cost = torch.empty(1 << n, dtype=torch.uint8, device="cuda")
+    hist = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    state = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    out = torch.empty(3, dtype=torch.float64, device="cuda")
+    sh = torch.empty(shots, dtype=torch.int64, device="cuda")
+    ws = core.workspace(C.gqaoa_evolve_workspace_size(n, p))
+    wss = core.workspace(C.gqaoa_sample_workspace_size(n, shots))
+
+    def path():
+        s = torch.cuda.current_stream().cuda_stream
+        C.gqaoa_build_cost(lits.ctypes.data, n, m, cost.data_ptr(), hist.data_ptr(), s)
+        C.gqaoa_evolve(cost.data_ptr(), n, m, gd.data_ptr(), bd.data_ptr(), p, state.data_ptr(),
+                       out.data_ptr(), None, ws.data_ptr(), ws.numel(), 0, s)
+        C.gqaoa_sample(state.data_ptr(), n, 3, shots, sh.data_ptr(), wss.data_ptr(), wss.numel(), s)
+
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        path()
+    torch.cuda.synchronize()
+    eager = (state.clone(), out.clone(), sh.clone(), cost.clone())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        path()
+    for t in (state, out, sh, cost):
+        t.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(state, eager[0]) and torch.equal(out, eager[1])
+    assert torch.equal(sh, eager[2]) and torch.equal(cost, eager[3])
+    psi = sv.evolve(sv.cost_table(lits, n)[0], n, g, b)
+    assert np.max(np.abs(state.cpu().numpy() - psi)) < AMP_TOL
