@@ -225,12 +225,13 @@ int gqaoa_grad_batched(const uint8_t *cost, int64_t cost_stride, int n, int m, i
  * out     device double [batch][angles][nrounds] written.
  * ws      device workspace of gqaoa_sweep_workspace_size(angles) bytes.
  * n must be in GQAOA_SWEEP_MIN_N..GQAOA_SWEEP_MAX_N (one CTA holds 2^n <=
- * 16384 amplitudes in registers; 15 <= n <= 18 use a cluster of 2..16 CTAs).
+ * 16384 amplitudes in registers; 15 <= n <= 18 use a cluster of 2..16 CTAs;
+ * n = 19 a cluster of 16 CTAs with half the state in shared memory).
  * Precision: complex64 state; the mixer sum is FP32 within a warp and
  * double-float across warps and CTAs; P is formed in FP64.
  */
 #define GQAOA_SWEEP_MIN_N 9
-#define GQAOA_SWEEP_MAX_N 18
+#define GQAOA_SWEEP_MAX_N 19
 int gqaoa_sweep_workspace_size(int angles, size_t *bytes);
 int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const double *gammas,
                 const double *betas, int angles, int p, const int32_t *rounds, int nrounds,

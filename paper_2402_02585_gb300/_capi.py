@@ -26,7 +26,7 @@ GQAOA_OBJ_ENERGY = 1
 GQAOA_MAX_N = 34
 GQAOA_MAX_M = 255
 GQAOA_SWEEP_MIN_N = 9
-GQAOA_SWEEP_MAX_N = 18
+GQAOA_SWEEP_MAX_N = 19
 
 
 class GQAOAError(RuntimeError):

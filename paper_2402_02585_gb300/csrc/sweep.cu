@@ -7,10 +7,11 @@
 // gives every shorter p).
 //
 // One work item = (instance, angle point) and is owned by one CTA (n <= 14)
-// or one thread-block cluster of 2..16 CTAs (n = 15..18). Each thread holds
+// or one thread-block cluster of 2..16 CTAs (n = 15..19). Each thread holds
 // 16 consecutive amplitudes and their 16 cost bytes in registers for the
-// whole evolution, so a round costs no memory traffic at all: per amplitude
-// one shared-memory phase lookup, a complex multiply-add and a partial sum.
+// whole evolution (n = 19: 16 more in shared memory), so a round costs no
+// memory traffic at all: per amplitude one shared-memory phase lookup, a
+// complex multiply-add and a partial sum.
 // The mixer needs S = sum_z chi(z) every round: FP32 over a thread's 16
 // values and the warp's butterfly, then double-float (two FP32 words) across
 // warps and, for clusters, across CTAs through distributed shared memory
@@ -94,12 +95,44 @@ __device__ __forceinline__ void round_body(float2 (&s)[16], const uint32_t (&cw)
   }
 }
 
+// The same round over a thread's 16 shared-memory amplitudes (the second half
+// of the state when it does not fit in registers). Layout [j][thread], so a
+// warp's accesses for one j are consecutive words: no bank conflicts.
+template <bool kExtra, int kThreads>
+__device__ __forceinline__ void round_body_smem(float2 *s_state, const uint32_t *s_cost,
+                                                const float2 *s_T, float2 ad, float (&v)[kSlots],
+                                                bool ro, bool first) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t cw = s_cost[q * kThreads + threadIdx.x];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float2 *sp = s_state + (4 * q + k) * kThreads + threadIdx.x;
+      const unsigned c = (cw >> (8 * k)) & 0xFFu;
+      const float2 y = *sp;
+      const float2 x = cmul(s_T[c], make_float2(y.x + ad.x, y.y + ad.y));
+      *sp = x;
+      v[0] += x.x;
+      v[1] += x.y;
+      if (kExtra && c == 0) {
+        if (ro) { v[2] += x.x * x.x + x.y * x.y; v[3] += x.x; v[4] += x.y; }
+        if (first) v[5] += 1.f;
+      }
+    }
+  }
+}
+
 // 64 registers per thread, so small CTAs run several per SM (1024 threads in
-// all) and one CTA's reduction overlaps another's rounds.
-template <int kThreads, int kCluster>
+// all) and one CTA's reduction overlaps another's rounds. kSmemHalf: the
+// instance's second half lives in shared memory (16 more amplitudes per
+// thread), which lets a 16-CTA cluster hold 2^19 amplitudes.
+template <int kThreads, int kCluster, bool kSmemHalf>
 __global__ void __launch_bounds__(kThreads, (kThreads >= 1024 ? 1 : 1024 / kThreads))
 sweep_kernel(const __grid_constant__ SweepArgs a) {
   constexpr int kW = kThreads / 32;
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  float2 *s_state = reinterpret_cast<float2 *>(s_dyn);                              // [16][kThreads]
+  uint32_t *s_cost = reinterpret_cast<uint32_t *>(s_dyn + 16 * kThreads * sizeof(float2));  // [4][kThreads]
   __shared__ float2 s_T[256];
   __shared__ float s_wp[2][kW][kSlots];        // warp partials (FP32)
   __shared__ float s_cp[2][kSlots][2];         // CTA partials (double-float), read cluster-wide
@@ -117,6 +150,14 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
     const int ai = (int)(item % (uint64_t)a.A);
     const uint4 cw = *reinterpret_cast<const uint4 *>(
         a.cost + b * N + 16ull * ((uint64_t)rank * kThreads + threadIdx.x));
+    if (kSmemHalf) {
+      const uint4 cw2 = *reinterpret_cast<const uint4 *>(
+          a.cost + b * N + N / 2 + 16ull * ((uint64_t)rank * kThreads + threadIdx.x));
+      s_cost[0 * kThreads + threadIdx.x] = cw2.x;
+      s_cost[1 * kThreads + threadIdx.x] = cw2.y;
+      s_cost[2 * kThreads + threadIdx.x] = cw2.z;
+      s_cost[3 * kThreads + threadIdx.x] = cw2.w;
+    }
     for (int i = threadIdx.x; i < 256; i += kThreads) s_T[i] = a.phase[(size_t)ai * 256 + i];
     const double2 ald = a.alpha[ai];
     const float alr = (float)ald.x, ali = (float)ald.y;
@@ -125,6 +166,10 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
     float2 s[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) s[j] = make_float2(amp0, 0.f);
+    if (kSmemHalf) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) s_state[j * kThreads + threadIdx.x] = make_float2(amp0, 0.f);
+    }
     float2 ad = make_float2(0.f, 0.f);  // pending mixer add
     float cnt0 = 0.f;  // C = 0 count of the instance (warp 0 keeps it)
     int ridx = 0;
@@ -134,8 +179,10 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
       float v[kSlots] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (ro || first) {
         round_body<true>(s, cwords, s_T, ad, v, ro, first);
+        if (kSmemHalf) round_body_smem<true, kThreads>(s_state, s_cost, s_T, ad, v, ro, first);
       } else {
         round_body<false>(s, cwords, s_T, ad, v, false, false);
+        if (kSmemHalf) round_body_smem<false, kThreads>(s_state, s_cost, s_T, ad, v, false, false);
       }
       const int nv = (ro || first) ? kSlots : 2;
 #pragma unroll
@@ -202,26 +249,37 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
 struct SweepShape {
   int threads;
   int cluster;
+  bool smem_half;
 };
 
 static SweepShape sweep_shape(int n) {
-  // 16 amplitudes per thread; up to 1024 threads per CTA, then clusters
+  // 16 amplitudes per thread in registers; up to 1024 threads per CTA, then
+  // clusters of up to 16; beyond that the second half goes to shared memory
   const int amps = 1 << n;
   int threads = amps / 16;
   int cluster = 1;
+  bool smem_half = false;
   if (threads > 1024) {
     cluster = threads / 1024;
     threads = 1024;
   }
-  return SweepShape{threads, cluster};
+  if (cluster > 16) {
+    cluster /= 2;
+    smem_half = true;
+  }
+  return SweepShape{threads, cluster, smem_half};
 }
 
-template <int kThreads, int kCluster>
+template <int kThreads, int kCluster, bool kSmemHalf = false>
 static int launch_sweep(const SweepArgs &args, cudaStream_t st) {
-  auto kernel = sweep_kernel<kThreads, kCluster>;
+  auto kernel = sweep_kernel<kThreads, kCluster, kSmemHalf>;
+  const size_t dyn = kSmemHalf ? (size_t)kThreads * (16 * sizeof(float2) + 4 * sizeof(uint32_t)) : 0;
+  if (kSmemHalf &&
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
+    return GQAOA_ECUDA;
   int per_unit = 0;  // resident CTAs (cluster == 1) or clusters
   if (kCluster == 1) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_unit, kernel, kThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_unit, kernel, kThreads, dyn) != cudaSuccess)
       return GQAOA_ECUDA;
     per_unit *= sm_count();
   } else {
@@ -231,6 +289,7 @@ static int launch_sweep(const SweepArgs &args, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kCluster, 1, 1);
     cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = dyn;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = kCluster;
@@ -245,6 +304,7 @@ static int launch_sweep(const SweepArgs &args, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(units * kCluster), 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = dyn;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -312,6 +372,10 @@ extern "C" int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const d
   args.R = nrounds;
   for (int i = 0; i < nrounds; ++i) args.rounds[i] = rounds[i];
   const SweepShape sh = sweep_shape(n);
+  if (sh.smem_half) {
+    if (sh.threads == 1024 && sh.cluster == 16) return launch_sweep<1024, 16, true>(args, st);
+    return GQAOA_ERANGE;
+  }
   switch (sh.threads * 100 + sh.cluster) {
     case 32 * 100 + 1: return launch_sweep<32, 1>(args, st);
     case 64 * 100 + 1: return launch_sweep<64, 1>(args, st);

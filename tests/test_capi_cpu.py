@@ -128,5 +128,5 @@ def test_sweep_rejects_bad_arguments_before_launch():
         C.gqaoa_sweep(fake, 12, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, fake, fake, 1 << 20, None)
     assert e.value.status == C.GQAOA_ERANGE
     with pytest.raises(C.GQAOAError) as e:
-        C.gqaoa_sweep(fake, 19, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, fake, fake, 1 << 20, None)
+        C.gqaoa_sweep(fake, 20, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, fake, fake, 1 << 20, None)
     assert e.value.status == C.GQAOA_ERANGE

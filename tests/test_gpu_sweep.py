@@ -3,8 +3,9 @@
 P(C=0) after the requested round counts must agree with the FP64 oracle
 within 1e-6 for every (instance, angle point): the full statevector oracle at
 small n, the exact cost-class model (pinned against it) at larger n. The
-cases cover one warp per item (n = 9), whole CTAs (n = 12..14) and clusters
-of 2, 4, 8 and 16 CTAs (n = 15..18), and more items than resident CTAs.
+cases cover one warp per item (n = 9), whole CTAs (n = 12..14), clusters
+of 2, 4, 8 and 16 CTAs (n = 15..18), a 16-CTA cluster with half the state in
+shared memory (n = 19), and more items than resident CTAs.
 """
 
 import math
@@ -45,6 +46,7 @@ def run_sweep(costs, n, m, G, Bt, p, rounds):
     (16, 1, 3, 8, [8]),
     (17, 1, 2, 6, [1, 6]),
     (18, 1, 2, 5, [2, 5]),
+    (19, 1, 3, 6, [1, 6]),
 ])
 def test_sweep_matches_oracle(n, B, A, p, rounds):
     m = int(math.floor(4.2 * n + 0.5))
