@@ -224,9 +224,11 @@ int gqaoa_grad_batched(const uint8_t *cost, int64_t cost_stride, int n, int m, i
  * rounds  host int32 [nrounds], strictly ascending, each in 1..p; nrounds <= 16.
  * out     device double [batch][angles][nrounds] written.
  * ws      device workspace of gqaoa_sweep_workspace_size(angles) bytes.
- * n must be in GQAOA_SWEEP_MIN_N..GQAOA_SWEEP_MAX_N (one CTA holds 2^n <=
- * 16384 amplitudes in registers; 15 <= n <= 18 use a cluster of 2..16 CTAs;
- * n = 19 a cluster of 16 CTAs with half the state in shared memory).
+ * amps_per_thread  16: a thread holds 16 amplitudes in registers (n <= 18);
+ *                  32: 16 in registers and 16 in shared memory (n >= 10);
+ *                  0: 16 for n <= 18, 32 for n = 19. A CTA has up to 1024
+ *                  threads; larger states use a cluster of up to 16 CTAs.
+ * n must be in GQAOA_SWEEP_MIN_N..GQAOA_SWEEP_MAX_N.
  * Precision: complex64 state; the mixer sum is FP32 within a warp and
  * double-float across warps and CTAs; P is formed in FP64.
  */
@@ -235,7 +237,7 @@ int gqaoa_grad_batched(const uint8_t *cost, int64_t cost_stride, int n, int m, i
 int gqaoa_sweep_workspace_size(int angles, size_t *bytes);
 int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const double *gammas,
                 const double *betas, int angles, int p, const int32_t *rounds, int nrounds,
-                double *out, void *ws, size_t ws_bytes, void *stream);
+                int amps_per_thread, double *out, void *ws, size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
  * Learned angle proposer (K9). The paper observes that optimal angles

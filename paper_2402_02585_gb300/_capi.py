@@ -64,7 +64,7 @@ SIGNATURES = {
     "gqaoa_grad_batched": [_P, _I64, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P],
     "gqaoa_evolve_noalloc": [_P, _I, _I, _P, _P, _I, _P, _P, _P, _U, _P],
     "gqaoa_sweep_workspace_size": [_I, _SZP],
-    "gqaoa_sweep": [_P, _I, _I, _I, _P, _P, _I, _I, _P, _I, _P, _P, _SZ, _P],
+    "gqaoa_sweep": [_P, _I, _I, _I, _P, _P, _I, _I, _P, _I, _I, _P, _P, _SZ, _P],
     "gqaoa_mlp_param_count": [_I, _I, _I, _SZP],
     "gqaoa_mlp_workspace_size": [_I, _I, _I, _I, _SZP],
     "gqaoa_mlp_forward": [_P, _I, _I, _I, _P, _I, _P, _P, _SZ, _P],
@@ -183,10 +183,10 @@ def gqaoa_sweep_workspace_size(angles) -> int:
     return _size("gqaoa_sweep_workspace_size", angles)
 
 
-def gqaoa_sweep(cost, n, m, batch, gammas, betas, angles, p, rounds, nrounds, out, ws, ws_bytes,
-                stream):
-    _call("gqaoa_sweep", cost, n, m, batch, gammas, betas, angles, p, rounds, nrounds, out, ws,
-          ws_bytes, stream)
+def gqaoa_sweep(cost, n, m, batch, gammas, betas, angles, p, rounds, nrounds, amps_per_thread,
+                out, ws, ws_bytes, stream):
+    _call("gqaoa_sweep", cost, n, m, batch, gammas, betas, angles, p, rounds, nrounds,
+          amps_per_thread, out, ws, ws_bytes, stream)
 
 
 def gqaoa_mlp_param_count(d_in, d_h, d_out) -> int:

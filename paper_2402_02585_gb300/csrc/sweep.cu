@@ -252,22 +252,17 @@ struct SweepShape {
   bool smem_half;
 };
 
-static SweepShape sweep_shape(int n) {
-  // 16 amplitudes per thread in registers; up to 1024 threads per CTA, then
-  // clusters of up to 16; beyond that the second half goes to shared memory
+// amps_per_thread: 16 (all in registers) or 32 (16 more in shared memory);
+// up to 1024 threads per CTA, then clusters of up to 16 CTAs.
+static SweepShape sweep_shape(int n, int amps_per_thread) {
   const int amps = 1 << n;
-  int threads = amps / 16;
+  int threads = amps / amps_per_thread;
   int cluster = 1;
-  bool smem_half = false;
   if (threads > 1024) {
     cluster = threads / 1024;
     threads = 1024;
   }
-  if (cluster > 16) {
-    cluster /= 2;
-    smem_half = true;
-  }
-  return SweepShape{threads, cluster, smem_half};
+  return SweepShape{threads, cluster, amps_per_thread == 32};
 }
 
 template <int kThreads, int kCluster, bool kSmemHalf = false>
@@ -339,7 +334,8 @@ extern "C" int gqaoa_sweep_workspace_size(int angles, size_t *bytes) {
 
 extern "C" int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const double *gammas,
                            const double *betas, int angles, int p, const int32_t *rounds,
-                           int nrounds, double *out, void *ws, size_t ws_bytes, void *stream) {
+                           int nrounds, int amps_per_thread, double *out, void *ws,
+                           size_t ws_bytes, void *stream) {
   gq::NvtxRange nvtx_range("gqaoa_sweep");
   if (n < GQAOA_SWEEP_MIN_N || n > GQAOA_SWEEP_MAX_N || m < 0 || m > GQAOA_MAX_M || batch < 1 ||
       angles < 1 || angles > (1 << 24) || p < 1 || p > (1 << 20) || nrounds < 1 ||
@@ -353,6 +349,9 @@ extern "C" int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const d
     if (rounds[i] < 1 || rounds[i] > p) return GQAOA_ERANGE;
     if (i > 0 && rounds[i] <= rounds[i - 1]) return GQAOA_EINVAL;
   }
+  if (amps_per_thread == 0) amps_per_thread = n <= 18 ? 16 : 32;
+  if (amps_per_thread != 16 && amps_per_thread != 32) return GQAOA_EINVAL;
+  if ((amps_per_thread == 16 && n > 18) || (amps_per_thread == 32 && n < 10)) return GQAOA_ERANGE;
   if (ws_bytes < sweep_ws_layout(angles, nullptr, nullptr, nullptr)) return GQAOA_ENOMEM;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SweepArgs args = {};
@@ -371,10 +370,21 @@ extern "C" int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const d
   args.p = p;
   args.R = nrounds;
   for (int i = 0; i < nrounds; ++i) args.rounds[i] = rounds[i];
-  const SweepShape sh = sweep_shape(n);
+  const SweepShape sh = sweep_shape(n, amps_per_thread);
   if (sh.smem_half) {
-    if (sh.threads == 1024 && sh.cluster == 16) return launch_sweep<1024, 16, true>(args, st);
-    return GQAOA_ERANGE;
+    switch (sh.threads * 100 + sh.cluster) {
+      case 32 * 100 + 1: return launch_sweep<32, 1, true>(args, st);
+      case 64 * 100 + 1: return launch_sweep<64, 1, true>(args, st);
+      case 128 * 100 + 1: return launch_sweep<128, 1, true>(args, st);
+      case 256 * 100 + 1: return launch_sweep<256, 1, true>(args, st);
+      case 512 * 100 + 1: return launch_sweep<512, 1, true>(args, st);
+      case 1024 * 100 + 1: return launch_sweep<1024, 1, true>(args, st);
+      case 1024 * 100 + 2: return launch_sweep<1024, 2, true>(args, st);
+      case 1024 * 100 + 4: return launch_sweep<1024, 4, true>(args, st);
+      case 1024 * 100 + 8: return launch_sweep<1024, 8, true>(args, st);
+      case 1024 * 100 + 16: return launch_sweep<1024, 16, true>(args, st);
+      default: return GQAOA_ERANGE;
+    }
   }
   switch (sh.threads * 100 + sh.cluster) {
     case 32 * 100 + 1: return launch_sweep<32, 1>(args, st);

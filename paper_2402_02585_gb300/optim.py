@@ -127,7 +127,7 @@ def single_angle_grid_start(cost: torch.Tensor, n: int, m: int, p: int, grid: in
         ws = core.workspace(C.gqaoa_sweep_workspace_size(A), cost.device)
         r = np.array([p], dtype=np.int32)
         C.gqaoa_sweep(cost.data_ptr(), n, m, B, gd.data_ptr(), bd.data_ptr(), A, p, r.ctypes.data, 1,
-                      out.data_ptr(), ws.data_ptr(), ws.numel(),
+                      0, out.data_ptr(), ws.data_ptr(), ws.numel(),
                       torch.cuda.current_stream().cuda_stream)
         k = torch.argmax(out[:, :, 0], dim=1).cpu().numpy()
         return G[k], Bt[k]

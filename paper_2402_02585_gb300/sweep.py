@@ -4,7 +4,9 @@ instances of uneven n, as one replayable CUDA graph.
 Instances are bucketed by n. Each bucket runs on the path the tuning table
 chooses for its n:
   * "onchip": gqaoa_sweep, one CTA or thread-block cluster per
-    (instance, angle point) holding the state in registers (9 <= n <= 18);
+    (instance, angle point) holding the state on chip (9 <= n <= 19), with
+    16 amplitudes per thread in registers ("apt": 16) or 16 more in shared
+    memory ("apt": 32);
   * "stream": gqaoa_evolve_batched with the instance's cost table shared by a
     chunk of angle points and a per-round trace of P(C=0); the chunk size is
     chosen so the chunk's states stay resident in L2.
@@ -74,7 +76,7 @@ class SweepPlan:
             self.out[n] = out
             if choice["path"] == "onchip":
                 ws = core.workspace(C.gqaoa_sweep_workspace_size(self.A), self.device)
-                self.steps.append(("onchip", n, m, cost, out, ws))
+                self.steps.append(("onchip", n, m, cost, out, (ws, int(choice.get("apt", 0)))))
             else:
                 S = int(min(self.A, choice["angle_batch"]))
                 state = torch.empty((S, 1 << n), dtype=torch.complex64, device=self.device)
@@ -93,10 +95,10 @@ class SweepPlan:
             if (kind == "onchip" and not onchip) or (kind == "stream" and not stream):
                 continue
             if kind == "onchip":
-                ws = extra
+                ws, apt = extra
                 C.gqaoa_sweep(cost.data_ptr(), n, m, B, self.g.data_ptr(), self.b.data_ptr(),
-                              self.A, self.p, self.rounds.ctypes.data, self.R, out.data_ptr(),
-                              ws.data_ptr(), ws.numel(), s)
+                              self.A, self.p, self.rounds.ctypes.data, self.R, apt,
+                              out.data_ptr(), ws.data_ptr(), ws.numel(), s)
                 continue
             S, state, trace, res, ws = extra
             for i in range(B):

@@ -4,8 +4,9 @@ JSON table that SweepPlan loads.
 
     python -m paper_2402_02585_gb300.tune [--out PATH] [--n 12 13 ...]
 
-Candidates: the on-chip sweep (9 <= n <= 18) and the streaming path with
-chunks of 8..1024 angle points sharing the instance's cost table. The score is
+Candidates: the on-chip sweep with 16 amplitudes per thread in registers
+(9 <= n <= 18) or 16 more in shared memory (10 <= n <= 19), and the streaming
+path with chunks of 16..256 angle points sharing the instance's cost table. The score is
 amplitude-rounds per second on a small synthetic bucket of the workload's
 recipe (d = 4.2, p = 16).
 """
@@ -48,8 +49,10 @@ def tune(n_values, p: int = 16, angles: int = 256, verbose: bool = True) -> dict
         G = rng.uniform(0, np.pi, angles)
         Bt = rng.uniform(0, np.pi, angles)
         cands = []
-        if C.GQAOA_SWEEP_MIN_N <= n <= C.GQAOA_SWEEP_MAX_N:
-            cands.append({"path": "onchip"})
+        if C.GQAOA_SWEEP_MIN_N <= n <= 18:
+            cands.append({"path": "onchip", "apt": 16})
+        if 10 <= n <= C.GQAOA_SWEEP_MAX_N:
+            cands.append({"path": "onchip", "apt": 32})
         for S in (16, 64, 256):
             if S <= angles and (S << n) * 8 <= (4 << 30):
                 cands.append({"path": "stream", "angle_batch": S})

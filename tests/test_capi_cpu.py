@@ -121,12 +121,19 @@ def test_sweep_rejects_bad_arguments_before_launch():
     fake = 1 << 20
     r = np.array([2, 1], dtype=np.int32)
     with pytest.raises(C.GQAOAError) as e:
-        C.gqaoa_sweep(fake, 12, 50, 1, fake, fake, 4, 4, r.ctypes.data, 2, fake, fake, 1 << 20, None)
+        C.gqaoa_sweep(fake, 12, 50, 1, fake, fake, 4, 4, r.ctypes.data, 2, 0, fake, fake, 1 << 20, None)
     assert e.value.status == C.GQAOA_EINVAL
     r = np.array([5], dtype=np.int32)
     with pytest.raises(C.GQAOAError) as e:
-        C.gqaoa_sweep(fake, 12, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, fake, fake, 1 << 20, None)
+        C.gqaoa_sweep(fake, 12, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, 0, fake, fake, 1 << 20, None)
+    assert e.value.status == C.GQAOA_ERANGE
+    r = np.array([4], dtype=np.int32)
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_sweep(fake, 20, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, 0, fake, fake, 1 << 20, None)
+    assert e.value.status == C.GQAOA_ERANGE
+    with pytest.raises(C.GQAOAError) as e:  # 16 per thread cannot hold n = 19
+        C.gqaoa_sweep(fake, 19, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, 16, fake, fake, 1 << 20, None)
     assert e.value.status == C.GQAOA_ERANGE
     with pytest.raises(C.GQAOAError) as e:
-        C.gqaoa_sweep(fake, 20, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, fake, fake, 1 << 20, None)
-    assert e.value.status == C.GQAOA_ERANGE
+        C.gqaoa_sweep(fake, 12, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, 8, fake, fake, 1 << 20, None)
+    assert e.value.status == C.GQAOA_EINVAL

@@ -21,7 +21,7 @@ from paper_2402_02585_gb300 import core, instances
 pytestmark = pytest.mark.gpu
 
 
-def run_sweep(costs, n, m, G, Bt, p, rounds):
+def run_sweep(costs, n, m, G, Bt, p, rounds, apt=0):
     B = costs.shape[0]
     A = len(G)
     gd = torch.as_tensor(np.asarray(G, dtype=np.float64), device="cuda")
@@ -30,12 +30,13 @@ def run_sweep(costs, n, m, G, Bt, p, rounds):
     ws = core.workspace(C.gqaoa_sweep_workspace_size(A))
     r = np.ascontiguousarray(rounds, dtype=np.int32)
     C.gqaoa_sweep(costs.data_ptr(), n, m, B, gd.data_ptr(), bd.data_ptr(), A, p, r.ctypes.data,
-                  len(rounds), out.data_ptr(), ws.data_ptr(), ws.numel(),
+                  len(rounds), apt, out.data_ptr(), ws.data_ptr(), ws.numel(),
                   torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     return out.cpu().numpy()
 
 
+@pytest.mark.parametrize("apt", [0, 32])
 @pytest.mark.parametrize("n,B,A,p,rounds", [
     (9, 3, 7, 12, [1, 4, 12]),
     (10, 2, 5, 8, [2, 8]),
@@ -48,7 +49,9 @@ def run_sweep(costs, n, m, G, Bt, p, rounds):
     (18, 1, 2, 5, [2, 5]),
     (19, 1, 3, 6, [1, 6]),
 ])
-def test_sweep_matches_oracle(n, B, A, p, rounds):
+def test_sweep_matches_oracle(n, B, A, p, rounds, apt):
+    if apt == 32 and n < 10:
+        pytest.skip("32 amplitudes per thread needs n >= 10")
     m = int(math.floor(4.2 * n + 0.5))
     costs, hists, refc = [], [], []
     for i in range(B):
@@ -61,7 +64,7 @@ def test_sweep_matches_oracle(n, B, A, p, rounds):
     rng = np.random.default_rng(n)
     G = rng.uniform(0, np.pi, A)
     Bt = rng.uniform(0, np.pi, A)
-    got = run_sweep(torch.stack(costs), n, m, G, Bt, p, rounds)
+    got = run_sweep(torch.stack(costs), n, m, G, Bt, p, rounds, apt)
     for i in range(B):
         for a in range(A):
             if n <= 12:
