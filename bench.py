@@ -520,12 +520,16 @@ def run_sweep(args, wl):
                        "buckets": {n: int(c.shape[0]) for n, (c, _) in buckets.items()}},
             "roofline": {"bound": "hbm", "achieved": st_gbs, "peak": peak, "unit": "GB/s",
                          "frac": (st_gbs / peak) if st_gbs else None, "traffic": None,
-                         "peak_kind": kind, "kernel": "streaming round_kernel (n >= 19 buckets, "
-                         f"{100 * t_st / el:.0f} % of the time)", "alg_bytes_per_amp_round": 16},
+                         "peak_kind": kind, "kernel": "streaming round_kernel (n = "
+                         + ",".join(str(st[1]) for st in plan.steps if st[0] == "stream")
+                         + f" buckets, {100 * t_st / el:.0f} % of the time)",
+                         "alg_bytes_per_amp_round": 16},
             "roofline_onchip": {"bound": "alu", "achieved": ar_on / t_on if t_on > 0 else None,
                                 "peak": alu_peak, "unit": "amp-rounds/s",
                                 "frac": (ar_on / t_on / alu_peak) if t_on > 0 else None,
-                                "kernel": "sweep_kernel (n <= 18 buckets)",
+                                "kernel": "sweep_kernel (n = " + ",".join(
+                                    str(st[1]) for st in plan.steps if st[0] == "onchip")
+                                + " buckets)",
                                 "peak_derivation": "4 warp-instr/clk/SM x 32 x SMs x 2.07 GHz / 12 "
                                                    "instructions per amplitude-round"},
             "cpu_baseline": cpu_sweep_baseline(wl) if world == 1 else None,
