@@ -150,3 +150,26 @@ def test_trained_proposer_gains_over_plain_optimizer():
     assert ev["hit_rate"] >= 0.9
     assert ev["median_steps_proposer"] < ev["median_steps_plain"]
     assert ev["median_wall_proposer"] < ev["median_wall_plain"]
+
+
+def test_proposer_state_roundtrip_and_optimizer_resume(tmp_path):
+    prop = Proposer(p=3, d_h=32, seed=4)
+    x = torch.rand((5, 130), device="cuda")
+    a0 = prop.predict(x).clone()
+    torch.save(prop.state_dict(), tmp_path / "prop.pt")
+    other = Proposer(p=3, d_h=32, seed=99)
+    other.load_state_dict(torch.load(tmp_path / "prop.pt"))
+    assert torch.equal(other.predict(x), a0)
+    # the optimizer resumes from saved angles: same values from the same angles
+    n, m, p = 11, 46, 3
+    cost = torch.stack([core.build_cost(instances.random_3sat(n, m, 40 + i), n)[0] for i in range(2)])
+    opt = AngleOptimizer(cost, n, m, p)
+    opt.reset(np.full((2, p), 0.4), np.full((2, p), 2.0))
+    opt.run(10)
+    g, b = opt.angles()
+    np.save(tmp_path / "angles.npy", torch.stack([g, b]).cpu().numpy())
+    v_before = opt.evaluate().clone()
+    saved = np.load(tmp_path / "angles.npy")
+    opt2 = AngleOptimizer(cost, n, m, p)
+    opt2.reset(saved[0], saved[1])
+    assert torch.equal(opt2.evaluate(), v_before)
