@@ -189,6 +189,29 @@ class OracleSample:
         self.t_cost = time.perf_counter() - t0
         self.cores = sv.num_threads()
 
+    def one_core(self) -> float:
+        """amp-rounds/s of one statevector round on a single host thread."""
+        sv, wl = self.sv, self.wl
+        full = sv.num_threads()
+        sv.set_threads(1)
+        try:
+            t0 = time.perf_counter()
+            sv.evolve(self.cost, wl["n"], self.g[:1], self.b[:1])
+            t = time.perf_counter() - t0
+        finally:
+            sv.set_threads(full)
+        return (1 << wl["n"]) / t
+
+    def reduced_context(self) -> float:
+        """Seconds of the paper's own method (Appendix C) for the same P:
+        the (m+1)-dimensional cost-class evolution, after the histogram that
+        the cost-table time above already includes."""
+        from oracle import reduced
+        hist = np.bincount(self.cost, minlength=self.wl["m"] + 1)
+        t0 = time.perf_counter()
+        reduced.readout(hist, reduced.evolve(hist, self.g, self.b))
+        return time.perf_counter() - t0
+
     def step(self):
         sv, wl = self.sv, self.wl
         n, p = wl["n"], wl["p"]
@@ -205,6 +228,18 @@ class OracleSample:
                      f"{self.shots} of {wl['shots']} shots ({t3 - t2:.2f} s); step = cost table "
                      f"+ {p} rounds + all shots, extrapolated linearly")
         return p * (1 << n) / step, step
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args, wl):
@@ -227,7 +262,9 @@ def run_reference(args, wl):
         "data": "synthetic", "config": {"workload": wl["desc"], "n": wl["n"], "m": wl["m"],
                                         "p": wl["p"], "shots": wl["shots"]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": sample.cores, "kind": "oracle",
-                         "sample": sample.desc},
+                         "sample": sample.desc, "cpu_model": cpu_model(),
+                         "one_core_round_amp_rounds_per_s": sample.one_core(),
+                         "context_reduced_model_s": sample.reduced_context()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.perf_counter() - total_t0,
     }
@@ -361,7 +398,9 @@ def run_ours(args, wl):
                 osamp = OracleSample(wl)
                 v, _ = osamp.step()
                 cpu = {"value": v, "unit": UNIT, "cores": osamp.cores, "kind": "oracle",
-                       "sample": osamp.desc}
+                       "sample": osamp.desc, "cpu_model": cpu_model(),
+                       "one_core_round_amp_rounds_per_s": osamp.one_core(),
+                       "context_reduced_model_s": osamp.reduced_context()}
             except Exception as exc:  # keep the GPU line even if the host run fails
                 cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                        "sample": f"failed: {exc!r}"}

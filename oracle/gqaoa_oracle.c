@@ -263,3 +263,13 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads used by the OpenMP loops from now on (timing on one core). */
+void oracle_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}

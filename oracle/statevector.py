@@ -68,6 +68,7 @@ def _load():
             lib.oracle_sample.argtypes = [P, ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, P, P]
             lib.oracle_sample.restype = ctypes.c_int
             lib.oracle_num_threads.restype = ctypes.c_int
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -78,6 +79,10 @@ def _ptr(a: np.ndarray):
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_threads(t: int) -> None:
+    _load().oracle_set_threads(int(t))
 
 
 def cost_at(lits: np.ndarray, z: int) -> int:
