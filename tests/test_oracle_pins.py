@@ -356,3 +356,15 @@ def test_uniforms_in_unit_interval():
     u = np.array([sv.shot_uniform(99, s) for s in range(20000)])
     assert u.min() >= 0.0 and u.max() < 1.0
     assert abs(u.mean() - 0.5) < 0.01
+
+
+def test_readout_of_uniform_state():
+    # |+> weighs every assignment 2^-n: P = h[0]/2^n and, each clause being
+    # violated by 1/8 of the assignments, <H_P> = m/8
+    n, m = 9, 37
+    lits = instances.random_3sat(n, m, 14)
+    cost, hist = sv.cost_table(lits, n)
+    r = sv.readout(sv.plus_state(n), cost, n)
+    assert abs(r[0] - hist[0] / (1 << n)) < 1e-15
+    assert abs(r[1] - m / 8) < 1e-12
+    assert abs(r[2] - 1.0) < 1e-14
