@@ -232,6 +232,13 @@ class OracleSample:
 
 def cpu_model() -> str:
     try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
         with open("/proc/cpuinfo") as fh:
             for ln in fh:
                 if ln.lower().startswith(("model name", "cpu part", "hardware")):
