@@ -80,16 +80,21 @@ struct Geometry {
   bool small;       // N < one tile: one CTA per instance, everything on chip
 };
 
-// One wave is 4 CTAs of 256 threads per SM. A single instance gets one wave
-// in clusters of 4; a batch gets about two waves split evenly over
+// One wave is `per_sm` CTAs of 256 threads per SM: 2 for the forward and
+// readout passes (each thread keeps two tiles in flight, ~116 registers) and
+// 4 for the adjoint passes (one tile, <= 64 registers). A single instance gets
+// one wave in clusters of 4; a batch gets about two waves split evenly over
 // instances, each CTA owning whole tiles of one instance.
-static Geometry make_geometry(int n, int B) {
+constexpr int kFwdPerSm = 2;
+constexpr int kBwdPerSm = 4;
+
+static Geometry make_geometry(int n, int B, int per_sm) {
   Geometry g;
   g.N = 1ull << n;
   g.B = B;
   g.small = g.N < (uint64_t)kTileAmps;
   g.ntiles = g.small ? 1 : g.N / kTileAmps;
-  const uint64_t wave = (uint64_t)sm_count() * 4;
+  const uint64_t wave = (uint64_t)sm_count() * (uint64_t)per_sm;
   if (g.small) {
     g.cpi = 1; g.cluster = 1; g.nparts = 1;
     return g;
@@ -125,7 +130,8 @@ struct Ws {
   size_t parts_half;  // doubles in one half of `parts`
 };
 
-static size_t ws_layout(const Geometry &g, int p, bool grad, char *base, Ws *w) {
+static size_t ws_layout(const Geometry &g, int p, bool grad, char *base, Ws *w,
+                        int max_nparts) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -133,7 +139,7 @@ static size_t ws_layout(const Geometry &g, int p, bool grad, char *base, Ws *w) 
     return o;
   };
   const size_t Bp = (size_t)g.B * (size_t)p;
-  const size_t half = (size_t)g.B * (size_t)g.nparts * kPartStride;
+  const size_t half = (size_t)g.B * (size_t)max_nparts * kPartStride;
   size_t o_alpha = take(sizeof(double2) * Bp);
   size_t o_phase = take(sizeof(float2) * 256 * Bp);
   size_t o_parts = take(sizeof(double) * 2 * half);
@@ -197,7 +203,8 @@ struct PassArgs {
   int p;
   int round;                // 0-based round index of this pass
   int cpi;
-  int nparts;
+  int nparts;               // records per instance written by this pass
+  int nparts_in;            // records per instance written by the previous pass
   uint64_t ntiles;          // tiles per instance
   uint64_t N;
   double inv_n;
@@ -217,9 +224,9 @@ __device__ __forceinline__ void pdl_wait_then_release() {
 // Sum slot j of instance b's records in index order within warp 0.
 __device__ __forceinline__ double w0_parts(const PassArgs &a, int b, int j) {
   const int lane = threadIdx.x & 31;
-  const double *base = a.parts_in + (size_t)b * a.nparts * kPartStride;
+  const double *base = a.parts_in + (size_t)b * a.nparts_in * kPartStride;
   double v = 0.0;
-  for (int i = lane; i < a.nparts; i += 32) v += base[(size_t)i * kPartStride + j];
+  for (int i = lane; i < a.nparts_in; i += 32) v += base[(size_t)i * kPartStride + j];
   return warp_sum(v);
 }
 
@@ -252,13 +259,40 @@ __device__ __forceinline__ uint64_t tile_vbase(uint64_t tile, int warp, int lane
   return tile * (kTileAmps / 2) + (uint64_t)warp * (kWarpTileAmps / 2) + lane;
 }
 
+// A thread's share of one tile: 8 float4 (16 amplitudes) and their costs.
+struct TileRegs {
+  float4 v[kVecPerThread];
+  uint16_t c2[kVecPerThread];
+};
+
+// Tiles first, first + stride, ... below ntiles, two in flight per thread:
+// the loads of the next tile are issued before the current one is processed,
+// so each thread keeps ~256 bytes of HBM reads outstanding.
+template <typename Load, typename Proc>
+__device__ __forceinline__ void pipelined_tiles(uint64_t first, uint64_t stride, uint64_t ntiles,
+                                                Load load, Proc proc) {
+  TileRegs A, Bt;
+  uint64_t t = first;
+  if (t < ntiles) load(A, t);
+  for (; t < ntiles; t += 2 * stride) {
+    const uint64_t t2 = t + stride;
+    if (t2 < ntiles) load(Bt, t2);
+    proc(A, t);
+    if (t2 < ntiles) {
+      const uint64_t t3 = t2 + stride;
+      if (t3 < ntiles) load(A, t3);
+      proc(Bt, t2);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K2: fused round
 // ---------------------------------------------------------------------------
 enum RoundMode { kFromPlus = 0, kFromState = 1, kChained = 2 };
 
 template <int kMode, bool kTrace>
-__global__ void __launch_bounds__(kThreads, 4) round_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(kThreads, kFwdPerSm) round_kernel(const PassArgs a) {
   __shared__ float2 s_T[256];
   __shared__ float2 s_a;
   __shared__ double s_w[kWarps][kPartStride];
@@ -303,17 +337,20 @@ __global__ void __launch_bounds__(kThreads, 4) round_kernel(const PassArgs a) {
   const float4 *__restrict__ src = a.src + (size_t)b * (a.N / 2);
   float4 *dst = a.dst + (size_t)b * (a.N / 2);
   const bool reverse = (a.round & 1) != 0;  // alternate sweep direction: L2 reuse across rounds
-  for (uint64_t t = local; t < a.ntiles; t += a.cpi) {
-    const uint64_t tt = reverse ? (a.ntiles - 1 - t) : t;
-    const uint64_t vb = tile_vbase(tt, warp, lane);
-    float4 v[kVecPerThread];
-    uint16_t c2[kVecPerThread];
+  auto vbase = [&](uint64_t t) {
+    return tile_vbase(reverse ? (a.ntiles - 1 - t) : t, warp, lane);
+  };
+  auto load = [&](TileRegs &T, uint64_t t) {
+    const uint64_t vb = vbase(t);
 #pragma unroll
-    for (int j = 0; j < kVecPerThread; ++j) c2[j] = cost2[vb + 32 * j];
+    for (int j = 0; j < kVecPerThread; ++j) T.c2[j] = cost2[vb + 32 * j];
     if (kMode != kFromPlus) {
 #pragma unroll
-      for (int j = 0; j < kVecPerThread; ++j) v[j] = src[vb + 32 * j];
+      for (int j = 0; j < kVecPerThread; ++j) T.v[j] = src[vb + 32 * j];
     }
+  };
+  auto proc = [&](TileRegs &T, uint64_t t) {
+    const uint64_t vb = vbase(t);
     float tr = 0.f, ti = 0.f, ta = 0.f, tbr = 0.f, tbi = 0.f, tc = 0.f;
 #pragma unroll
     for (int j = 0; j < kVecPerThread; ++j) {
@@ -322,13 +359,13 @@ __global__ void __launch_bounds__(kThreads, 4) round_kernel(const PassArgs a) {
         p0 = make_float2(a.amp0, 0.f);
         p1 = p0;
       } else {
-        p0 = make_float2(v[j].x + ad.x, v[j].y + ad.y);
-        p1 = make_float2(v[j].z + ad.x, v[j].w + ad.y);
+        p0 = make_float2(T.v[j].x + ad.x, T.v[j].y + ad.y);
+        p1 = make_float2(T.v[j].z + ad.x, T.v[j].w + ad.y);
       }
-      const unsigned c_0 = c2[j] & 0xFFu, c_1 = c2[j] >> 8;
+      const unsigned c_0 = T.c2[j] & 0xFFu, c_1 = T.c2[j] >> 8;
       const float2 x0 = cmul(s_T[c_0], p0);
       const float2 x1 = cmul(s_T[c_1], p1);
-      v[j] = make_float4(x0.x, x0.y, x1.x, x1.y);
+      T.v[j] = make_float4(x0.x, x0.y, x1.x, x1.y);
       tr += x0.x + x1.x;
       ti += x0.y + x1.y;
       if (kTrace) {
@@ -337,11 +374,12 @@ __global__ void __launch_bounds__(kThreads, 4) round_kernel(const PassArgs a) {
       }
     }
 #pragma unroll
-    for (int j = 0; j < kVecPerThread; ++j) dst[vb + 32 * j] = v[j];
+    for (int j = 0; j < kVecPerThread; ++j) dst[vb + 32 * j] = T.v[j];
     acc[0].add(tr);
     acc[1].add(ti);
     if (kTrace) { acc[2].add(ta); acc[3].add(tbr); acc[4].add(tbi); acc[5 % kVals].add(tc); }
-  }
+  };
+  pipelined_tiles(local, a.cpi, a.ntiles, load, proc);
   reduce_to_record<kVals>(a, b, local, acc, s_w, s_vals);
 }
 
@@ -349,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 4) round_kernel(const PassArgs a) {
 // K4: readout. kPending: dst <- psi_p = src + a_p first (materialise).
 // ---------------------------------------------------------------------------
 template <bool kPending>
-__global__ void __launch_bounds__(kThreads, 4) readout_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(kThreads, kFwdPerSm) readout_kernel(const PassArgs a) {
   __shared__ float2 s_a;
   __shared__ double s_w[kWarps][kPartStride];
   __shared__ double s_vals[kPartStride];
@@ -380,35 +418,40 @@ __global__ void __launch_bounds__(kThreads, 4) readout_kernel(const PassArgs a) 
   const float4 *__restrict__ src = a.src + (size_t)b * (a.N / 2);
   float4 *dst = a.dst + (size_t)b * (a.N / 2);
   const bool reverse = kPending && ((a.round + 1) & 1) != 0;
-  for (uint64_t t = local; t < a.ntiles; t += a.cpi) {
-    const uint64_t tt = reverse ? (a.ntiles - 1 - t) : t;
-    const uint64_t vb = tile_vbase(tt, warp, lane);
-    float4 v[kVecPerThread];
-    uint16_t c2[kVecPerThread];
+  auto vbase = [&](uint64_t t) {
+    return tile_vbase(reverse ? (a.ntiles - 1 - t) : t, warp, lane);
+  };
+  auto load = [&](TileRegs &T, uint64_t t) {
+    const uint64_t vb = vbase(t);
 #pragma unroll
     for (int j = 0; j < kVecPerThread; ++j) {
-      c2[j] = cost2[vb + 32 * j];
-      v[j] = src[vb + 32 * j];
+      T.c2[j] = cost2[vb + 32 * j];
+      T.v[j] = src[vb + 32 * j];
     }
+  };
+  auto proc = [&](TileRegs &T, uint64_t t) {
     float tp = 0.f, te = 0.f, tn = 0.f;
 #pragma unroll
     for (int j = 0; j < kVecPerThread; ++j) {
-      if (kPending) v[j] = make_float4(v[j].x + ad.x, v[j].y + ad.y, v[j].z + ad.x, v[j].w + ad.y);
-      const float w0 = v[j].x * v[j].x + v[j].y * v[j].y;
-      const float w1 = v[j].z * v[j].z + v[j].w * v[j].w;
-      const unsigned c_0 = c2[j] & 0xFFu, c_1 = c2[j] >> 8;
+      if (kPending)
+        T.v[j] = make_float4(T.v[j].x + ad.x, T.v[j].y + ad.y, T.v[j].z + ad.x, T.v[j].w + ad.y);
+      const float w0 = T.v[j].x * T.v[j].x + T.v[j].y * T.v[j].y;
+      const float w1 = T.v[j].z * T.v[j].z + T.v[j].w * T.v[j].w;
+      const unsigned c_0 = T.c2[j] & 0xFFu, c_1 = T.c2[j] >> 8;
       tn += w0 + w1;
       te += (float)c_0 * w0 + (float)c_1 * w1;
       tp += (c_0 == 0 ? w0 : 0.f) + (c_1 == 0 ? w1 : 0.f);
     }
     if (kPending) {
+      const uint64_t vb = vbase(t);
 #pragma unroll
-      for (int j = 0; j < kVecPerThread; ++j) dst[vb + 32 * j] = v[j];
+      for (int j = 0; j < kVecPerThread; ++j) dst[vb + 32 * j] = T.v[j];
     }
     acc[0].add(tp);
     acc[1].add(te);
     acc[2].add(tn);
-  }
+  };
+  pipelined_tiles(local, a.cpi, a.ntiles, load, proc);
   reduce_to_record<3>(a, b, local, acc, s_w, s_vals);
 }
 
@@ -436,7 +479,7 @@ __global__ void finalize_readout_kernel(const double *__restrict__ parts, int np
 // Records: 0,1 = Lambda_p; 2 = L = sum O |psi_p|^2.
 // ---------------------------------------------------------------------------
 template <int kObj>
-__global__ void __launch_bounds__(kThreads, 4) lambda_init_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(kThreads, kBwdPerSm) lambda_init_kernel(const PassArgs a) {
   __shared__ float2 s_a;
   __shared__ double s_w[kWarps][kPartStride];
   __shared__ double s_vals[kPartStride];
@@ -492,7 +535,7 @@ __global__ void __launch_bounds__(kThreads, 4) lambda_init_kernel(const PassArgs
 // chi = checkpoint chi_r. Records in: 0,1 = Lambda_r; 2 = G_{r+1} (or L when
 // r = p-1). Records out: 0,1 = Lambda_{r-1}; 2 = G_r.
 template <bool kFirst, bool kLast>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, kBwdPerSm)
 backward_kernel(const PassArgs a, const float4 *__restrict__ chi_base) {
   __shared__ float2 s_T[256];
   __shared__ float2 s_b;
@@ -782,6 +825,7 @@ static void init_pass(PassArgs &pa, const Geometry &g, const Ws &w, const uint8_
   pa.p = p;
   pa.cpi = g.cpi;
   pa.nparts = g.nparts;
+  pa.nparts_in = g.nparts;
   pa.ntiles = g.ntiles;
   pa.N = g.N;
   pa.inv_n = 1.0 / (double)g.N;
@@ -854,11 +898,11 @@ static int evolve_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m,
   if (!aligned16(state) || !aligned16(cost) || !aligned8(gammas) || !aligned8(betas) ||
       (out && !aligned8(out)) || (trace && !aligned8(trace)) || !aligned16(ws))
     return GQAOA_EINVAL;
-  const Geometry g = make_geometry(n, B);
+  const Geometry g = make_geometry(n, B, kFwdPerSm);
   if (!g.small && cost_bstride % 16 != 0) return GQAOA_EINVAL;
-  if (ws_bytes < ws_layout(g, p, false, nullptr, nullptr)) return GQAOA_ENOMEM;
+  if (ws_bytes < ws_layout(g, p, false, nullptr, nullptr, g.nparts)) return GQAOA_ENOMEM;
   Ws w;
-  ws_layout(g, p, false, static_cast<char *>(ws), &w);
+  ws_layout(g, p, false, static_cast<char *>(ws), &w, g.nparts);
   const bool from_state = (flags & GQAOA_STATE_IN) != 0;
   rc = launch_phase_tables(gammas, betas, (int64_t)B * p, w, st);
   if (rc) return rc;
@@ -895,11 +939,13 @@ static int grad_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m, i
   if (!aligned16(cost) || !aligned8(gammas) || !aligned8(betas) || !aligned8(value) ||
       !aligned8(dgamma) || !aligned8(dbeta) || !aligned16(ws))
     return GQAOA_EINVAL;
-  const Geometry g = make_geometry(n, B);
+  const Geometry g = make_geometry(n, B, kFwdPerSm);   // forward passes
+  const Geometry gb = make_geometry(n, B, kBwdPerSm);  // adjoint passes
   if (!g.small && cost_bstride % 16 != 0) return GQAOA_EINVAL;
-  if (ws_bytes < ws_layout(g, p, true, nullptr, nullptr)) return GQAOA_ENOMEM;
+  const int maxp = g.nparts > gb.nparts ? g.nparts : gb.nparts;
+  if (ws_bytes < ws_layout(g, p, true, nullptr, nullptr, maxp)) return GQAOA_ENOMEM;
   Ws w;
-  ws_layout(g, p, true, static_cast<char *>(ws), &w);
+  ws_layout(g, p, true, static_cast<char *>(ws), &w, maxp);
   rc = launch_phase_tables(gammas, betas, (int64_t)B * p, w, st);
   if (rc) return rc;
   if (g.small) {
@@ -916,19 +962,21 @@ static int grad_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m, i
   if (rc) return rc;
   const size_t inst = (size_t)g.B * g.N;
   PassArgs pa;
-  init_pass(pa, g, w, cost, cost_bstride, p);
+  init_pass(pa, gb, w, cost, cost_bstride, p);
   pa.value = value;
   pa.dgamma = dgamma;
   pa.dbeta = dbeta;
-  // lambda_p = O psi_p
+  // lambda_p = O psi_p (reads the last forward pass's records)
+  pa.nparts_in = g.nparts;
   pa.round = p - 1;
   pa.parts_in = parts_half(w, p - 1);
   pa.parts_out = parts_half(w, p);
   pa.src = reinterpret_cast<const float4 *>(w.ckpt + (size_t)(p - 1) * inst);
   pa.dst = reinterpret_cast<float4 *>(w.lambda);
-  cudaError_t e = objective == GQAOA_OBJ_P0 ? launch_pass(g, lambda_init_kernel<GQAOA_OBJ_P0>, st, pa)
-                                            : launch_pass(g, lambda_init_kernel<GQAOA_OBJ_ENERGY>, st, pa);
+  cudaError_t e = objective == GQAOA_OBJ_P0 ? launch_pass(gb, lambda_init_kernel<GQAOA_OBJ_P0>, st, pa)
+                                            : launch_pass(gb, lambda_init_kernel<GQAOA_OBJ_ENERGY>, st, pa);
   if (e != cudaSuccess) return GQAOA_ECUDA;
+  pa.nparts_in = gb.nparts;
   int half = p;
   for (int r = p - 1; r >= 0; --r) {
     pa.round = r;
@@ -939,13 +987,13 @@ static int grad_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m, i
     pa.dst = reinterpret_cast<float4 *>(w.lambda);
     const float4 *chi = reinterpret_cast<const float4 *>(w.ckpt + (size_t)r * inst);
     const bool first = r == p - 1, last = r == 0;
-    if (first && last) e = launch_pass(g, backward_kernel<true, true>, st, pa, chi);
-    else if (first) e = launch_pass(g, backward_kernel<true, false>, st, pa, chi);
-    else if (last) e = launch_pass(g, backward_kernel<false, true>, st, pa, chi);
-    else e = launch_pass(g, backward_kernel<false, false>, st, pa, chi);
+    if (first && last) e = launch_pass(gb, backward_kernel<true, true>, st, pa, chi);
+    else if (first) e = launch_pass(gb, backward_kernel<true, false>, st, pa, chi);
+    else if (last) e = launch_pass(gb, backward_kernel<false, true>, st, pa, chi);
+    else e = launch_pass(gb, backward_kernel<false, false>, st, pa, chi);
     if (e != cudaSuccess) return GQAOA_ECUDA;
   }
-  finalize_grad_kernel<<<B, 32, 0, st>>>(parts_half(w, half), g.nparts, p, dgamma);
+  finalize_grad_kernel<<<B, 32, 0, st>>>(parts_half(w, half), gb.nparts, p, dgamma);
   GQ_CHECK_LAUNCH();
   return GQAOA_OK;
 }
@@ -965,7 +1013,8 @@ extern "C" int gqaoa_evolve_batched_workspace_size(int n, int batch, int p, size
   if (!bytes) return GQAOA_EINVAL;
   int rc = check_common(n, 0, batch, p);
   if (rc) return rc;
-  *bytes = ws_layout(make_geometry(n, batch), p, false, nullptr, nullptr);
+  const Geometry g = make_geometry(n, batch, kFwdPerSm);
+  *bytes = ws_layout(g, p, false, nullptr, nullptr, g.nparts);
   return GQAOA_OK;
 }
 
@@ -995,7 +1044,9 @@ extern "C" int gqaoa_grad_batched_workspace_size(int n, int batch, int p, size_t
   if (!bytes) return GQAOA_EINVAL;
   int rc = check_common(n, 0, batch, p);
   if (rc) return rc;
-  *bytes = ws_layout(make_geometry(n, batch), p, true, nullptr, nullptr);
+  const Geometry g = make_geometry(n, batch, kFwdPerSm);
+  const Geometry gb = make_geometry(n, batch, kBwdPerSm);
+  *bytes = ws_layout(g, p, true, nullptr, nullptr, g.nparts > gb.nparts ? g.nparts : gb.nparts);
   return GQAOA_OK;
 }
 
@@ -1020,7 +1071,7 @@ extern "C" int gqaoa_grad_batched(const uint8_t *cost, int64_t cost_stride, int 
 extern "C" int gqaoa_prob_workspace_size(int n, size_t *bytes) {
   if (!bytes) return GQAOA_EINVAL;
   if (n < 1 || n > GQAOA_MAX_N) return GQAOA_ERANGE;
-  const Geometry g = make_geometry(n, 1);
+  const Geometry g = make_geometry(n, 1, kFwdPerSm);
   *bytes = sizeof(double) * (size_t)g.nparts * kPartStride;
   return GQAOA_OK;
 }
@@ -1051,7 +1102,7 @@ extern "C" int gqaoa_prob(const void *state, const uint8_t *cost, int n, double 
   if (!state || !cost || !out) return GQAOA_EINVAL;
   if (!aligned16(state) || !aligned16(cost) || !aligned8(out)) return GQAOA_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const Geometry g = make_geometry(n, 1);
+  const Geometry g = make_geometry(n, 1, kFwdPerSm);
   if (g.small) {
     readout_small_kernel<<<1, kThreads, 0, st>>>(static_cast<const float2 *>(state), cost, n, out);
     GQ_CHECK_LAUNCH();
@@ -1067,6 +1118,7 @@ extern "C" int gqaoa_prob(const void *state, const uint8_t *cost, int n, double 
   pa.p = 1;
   pa.cpi = g.cpi;
   pa.nparts = g.nparts;
+  pa.nparts_in = g.nparts;
   pa.ntiles = g.ntiles;
   pa.N = g.N;
   pa.inv_n = 1.0 / (double)g.N;
