@@ -88,6 +88,14 @@ struct Geometry {
 constexpr int kFwdPerSm = 2;
 constexpr int kBwdPerSm = 4;
 
+// CTAs of one full wave of a clustered streaming pass: the number of clusters
+// of kClusterSize the device keeps resident at once (clusters are placed
+// within a GPC, so this can be fewer than SMs x per_sm / kClusterSize) times
+// the cluster size. Queried once per device and pass kind; falls back to
+// SMs x per_sm when no device answers (e.g. sizing a workspace on a host
+// without a GPU, which then errs on the large side).
+static int resident_cluster_ctas(int per_sm);
+
 static Geometry make_geometry(int n, int B, int per_sm) {
   Geometry g;
   g.N = 1ull << n;
@@ -100,7 +108,8 @@ static Geometry make_geometry(int n, int B, int per_sm) {
     return g;
   }
   if (B == 1) {
-    uint64_t c = g.ntiles < wave ? g.ntiles : wave;
+    const uint64_t full = (uint64_t)resident_cluster_ctas(per_sm);
+    uint64_t c = g.ntiles < full ? g.ntiles : full;
     c = (c + kClusterSize - 1) / kClusterSize * kClusterSize;
     if (c > kMaxCpi) c = kMaxCpi;
     g.cpi = (int)c;
@@ -782,6 +791,42 @@ grad_small_kernel(const SmallArgs a, int objective, double *__restrict__ value,
 // ---------------------------------------------------------------------------
 // host-side launch helpers
 // ---------------------------------------------------------------------------
+static std::once_flag g_res_once[kMaxDevices][2];
+static int g_res_ctas[kMaxDevices][2];
+
+template <typename Kernel>
+static int query_cluster_ctas(Kernel kernel, int per_sm) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterSize, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterSize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg) != cudaSuccess || clusters < 1) {
+    cudaGetLastError();  // clear a failed query: fall back to the SM count
+    return sm_count() * per_sm;
+  }
+  return clusters * kClusterSize;
+}
+
+static int resident_cluster_ctas(int per_sm) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return sm_count() * per_sm;
+  }
+  const int kind = per_sm == kFwdPerSm ? 0 : 1;
+  std::call_once(g_res_once[dev][kind], [dev, kind, per_sm]() {
+    g_res_ctas[dev][kind] = kind == 0 ? query_cluster_ctas(round_kernel<kChained, false>, per_sm)
+                                      : query_cluster_ctas(backward_kernel<false, false>, per_sm);
+  });
+  return g_res_ctas[dev][kind];
+}
 template <typename Kernel, typename... Args>
 static cudaError_t launch_pass(const Geometry &g, Kernel kernel, cudaStream_t st, Args... args) {
   cudaLaunchConfig_t cfg = {};
