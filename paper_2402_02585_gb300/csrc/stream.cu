@@ -115,11 +115,23 @@ static Geometry make_geometry(int n, int B, int per_sm) {
     g.cpi = (int)c;
     g.cluster = kClusterSize;
   } else {
-    uint64_t c = (2 * wave + B - 1) / (uint64_t)B;
-    if (c < 1) c = 1;
-    if (c > g.ntiles) c = g.ntiles;
-    if (c > kMaxCpi) c = kMaxCpi;
-    g.cpi = (int)c;
+    // CTAs per instance: enough for at least two waves, chosen so the last
+    // wave is nearly full (B * cpi close to a multiple of the wave), since a
+    // half-empty last wave of a streaming pass idles the HBM for its length.
+    const uint64_t cmax = g.ntiles < (uint64_t)kMaxCpi ? g.ntiles : (uint64_t)kMaxCpi;
+    uint64_t c0 = (2 * wave + B - 1) / (uint64_t)B;
+    if (c0 < 1) c0 = 1;
+    if (c0 > cmax) c0 = cmax;
+    uint64_t best = c0;
+    double best_eff = 0.0;
+    for (uint64_t c = c0; c <= cmax && c <= 4 * c0 + 8; ++c) {
+      const uint64_t ctas = (uint64_t)B * c;
+      const double waves = (double)ctas / (double)wave;
+      const double eff = waves / (double)((ctas + wave - 1) / wave);
+      if (eff > best_eff + 1e-9) { best_eff = eff; best = c; }
+      if (eff >= 0.97) break;
+    }
+    g.cpi = (int)best;
     g.cluster = 1;
   }
   g.nparts = g.cpi / g.cluster;
