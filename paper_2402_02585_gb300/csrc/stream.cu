@@ -129,7 +129,7 @@ static Geometry make_geometry(int n, int B, int per_sm) {
       const double waves = (double)ctas / (double)wave;
       const double eff = waves / (double)((ctas + wave - 1) / wave);
       if (eff > best_eff + 1e-9) { best_eff = eff; best = c; }
-      if (eff >= 0.97) break;
+      if (eff >= 0.95) break;
     }
     g.cpi = (int)best;
     g.cluster = 1;
