@@ -508,10 +508,44 @@ def run_grad(args, wl):
     return 0
 
 
+def l2_rmw_peak(device) -> float:
+    """Read-modify-write bandwidth of a 64 MiB L2-resident buffer, measured
+    live (GB/s, read + write bytes): torch's in-place multiply, 100 launches
+    replayed from a CUDA graph so no host launch gap sits between them."""
+    import torch
+
+    x = torch.ones(16 << 20, dtype=torch.float32, device=device)
+    s = torch.cuda.Stream(device)
+    s.wait_stream(torch.cuda.current_stream(device))
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            x.mul_(0.999999)
+    torch.cuda.current_stream(device).wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(100):
+            x.mul_(0.999999)
+    g.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return 2.0 * x.numel() * 4 * 100 / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+
+# on-chip share of the state on the cluster-resident sweep path:
+# 16 CTAs x 512 threads x (8 float4 in registers + 24 in shared memory) x 2
+L2_PATH_ONCHIP_AMPS = 16 * 512 * (8 + 24) * 2
+
+
 def run_sweep(args, wl):
     """Workload "sweep": all instances x all grid points through SweepPlan (the
-    on-chip sweep for n <= 18, L2/HBM streaming chunks above), replayed as one
-    CUDA graph. Metric: amplitude-rounds per second, sum over items of p * 2^n."""
+    on-chip sweep for n <= 19, the cluster-resident sweep with L2-resident
+    slots for n = 20; streaming chunks where the tuning table says so), each
+    path's persistent launches replayed as one CUDA graph. Metric:
+    amplitude-rounds per second, sum over items of p * 2^n."""
     import torch
 
     from paper_2402_02585_gb300 import core, instances
@@ -533,63 +567,104 @@ def run_sweep(args, wl):
     G, B = grid_angles(wl["grid"])
     plan = SweepPlan(buckets, G, B, wl["p"], wl["rounds"])
     plan.capture()  # includes one eager run
+    kinds = plan.kinds()
+
+    def one_step(marks):
+        for j, kind in enumerate(kinds):
+            if kind in plan.graphs:
+                plan.graphs[kind].replay()
+            else:
+                plan.run(kinds=(kind,))
+            if marks is not None:
+                marks[j + 1].record()
+
     for _ in range(max(0, args.warmup - 1)):
-        plan.replay()
+        one_step(None)
+    l2_peak = l2_rmw_peak(local) if "l2" in kinds else None
     torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(kinds) + 1)]
+          for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
-    ev[0].record()
     for i in range(args.steps):
-        plan.graph.replay()                    # on-chip buckets (one graph)
-        ev[2 * i + 1].record()
-        plan.run(onchip=False, stream=True)    # streaming buckets
-        ev[2 * i + 2].record()
+        ev[i][0].record()
+        one_step(ev[i])
     torch.cuda.synchronize()
     clk = clocks.stop()
-    el = ev[0].elapsed_time(ev[-1]) / 1e3
-    t_on = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)) / 1e3
-    t_st = sum(ev[2 * i + 1].elapsed_time(ev[2 * i + 2]) for i in range(args.steps)) / 1e3
+    el = ev[0][0].elapsed_time(ev[-1][-1]) / 1e3
+    t_kind = {kind: sum(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(args.steps)) / 1e3
+              for j, kind in enumerate(kinds)}
+    ar_kind = {kind: plan.amp_rounds_of(kind) * args.steps for kind in kinds}
     units = plan.amp_rounds() * args.steps
-    ar_on = sum(c.shape[0] * plan.A * plan.p * (1 << n) for kind, n, m, c, o, x in plan.steps
-                if kind == "onchip") * args.steps
-    ar_st = units - ar_on
-    peak, kind = hbm_peak()
-    # on-chip: issue ceiling from unit counts and clocks: 4 warp-instructions per
-    # clock per SM x 32 lanes x SMs x max SM clock, over the 12 instructions of
-    # one amplitude-round (phase lookup, complex multiply-add, sums, cost byte)
+    peak, peak_kind = hbm_peak()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_peak = 4 * 32 * sms * 2.07e9 / 12
-    # streaming: 8 B read + 8 B write per amplitude-round (the shared cost table
-    # stays in L2 across a chunk of 256 angle points)
-    st_gbs = 16 * ar_st / t_st / 1e9 if t_st > 0 else None
+
+    def bucket_list(kind):
+        return ",".join(str(st[1]) for st in plan.steps if st[0] == kind)
+
+    def share(kind):
+        return f"{100 * t_kind[kind] / el:.0f} % of the time"
+
+    roof = {}
+    if "onchip" in kinds:
+        # issue ceiling from unit counts and clocks: 4 warp-instructions per clock
+        # per SM x 32 lanes x SMs x max SM clock, over the 12 instructions of one
+        # amplitude-round (phase lookup, complex multiply-add, sums, cost byte)
+        alu_peak = 4 * 32 * sms * 2.07e9 / 12
+        a = ar_kind["onchip"] / t_kind["onchip"]
+        roof["onchip"] = {"bound": "alu", "achieved": a, "peak": alu_peak, "unit": "amp-rounds/s",
+                          "frac": a / alu_peak, "kernel": f"sweep_kernel (n = {bucket_list('onchip')}"
+                          f" buckets, {share('onchip')})",
+                          "peak_derivation": "4 warp-instr/clk/SM x 32 x SMs x 2.07 GHz / 12 "
+                                             "instructions per amplitude-round"}
+    if "l2" in kinds:
+        # 8 B read + 8 B write + 1 B cost per amplitude-round outside shared memory
+        l2_bytes = sum(17.0 * st[3].shape[0] * plan.A * plan.p * max(0, (1 << st[1]) - L2_PATH_ONCHIP_AMPS)
+                       for st in plan.steps if st[0] == "l2") * args.steps
+        a = l2_bytes / t_kind["l2"] / 1e9
+        roof["l2"] = {"bound": "l2", "achieved": a, "peak": l2_peak, "unit": "GB/s",
+                      "frac": a / l2_peak, "traffic": None,
+                      "peak_kind": "measured live: in-place multiply of a 64 MiB tensor "
+                                   "(L2-resident), 100 launches from a CUDA graph",
+                      "kernel": f"sweep_l2_kernel (n = {bucket_list('l2')} buckets, {share('l2')})",
+                      "alg_bytes": "17 B per amplitude-round outside registers and shared "
+                                   f"memory ({L2_PATH_ONCHIP_AMPS} amplitudes per item stay on chip)",
+                      "amp_rounds_per_s": ar_kind["l2"] / t_kind["l2"]}
+    if "stream" in kinds:
+        # 8 B read + 8 B write per amplitude-round (the shared cost table stays in
+        # L2 across a chunk of angle points)
+        a = 16 * ar_kind["stream"] / t_kind["stream"] / 1e9
+        roof["stream"] = {"bound": "hbm", "achieved": a, "peak": peak, "unit": "GB/s",
+                          "frac": a / peak, "traffic": None, "peak_kind": peak_kind,
+                          "kernel": f"streaming round_kernel (n = {bucket_list('stream')} buckets, "
+                                    f"{share('stream')})", "alg_bytes_per_amp_round": 16}
+    dominant = max(kinds, key=lambda k: t_kind[k])
+    launches = 0
+    for kind, n, m, c, o, x in plan.steps:
+        if kind == "stream":
+            S = x[0]
+            launches += c.shape[0] * -(-plan.A // S) * (plan.p + 3)
+        else:
+            launches += 2  # phase tables + the persistent sweep kernel
     best = {n: float(o[..., -1].max().item()) for n, o in plan.out.items()}
     if rank == 0:
-        print(json.dumps({
+        line = {
             "metric": METRIC, "value": units / el, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64+f32/f64 sums", "data": "synthetic",
             "config": {"workload": wl["desc"], "instances": count,
                        "amp_rounds_per_step": plan.amp_rounds(),
-                       "buckets": {n: int(c.shape[0]) for n, (c, _) in buckets.items()}},
-            "roofline": {"bound": "hbm", "achieved": st_gbs, "peak": peak, "unit": "GB/s",
-                         "frac": (st_gbs / peak) if st_gbs else None, "traffic": None,
-                         "peak_kind": kind, "kernel": "streaming round_kernel (n = "
-                         + ",".join(str(st[1]) for st in plan.steps if st[0] == "stream")
-                         + f" buckets, {100 * t_st / el:.0f} % of the time)",
-                         "alg_bytes_per_amp_round": 16},
-            "roofline_onchip": {"bound": "alu", "achieved": ar_on / t_on if t_on > 0 else None,
-                                "peak": alu_peak, "unit": "amp-rounds/s",
-                                "frac": (ar_on / t_on / alu_peak) if t_on > 0 else None,
-                                "kernel": "sweep_kernel (n = " + ",".join(
-                                    str(st[1]) for st in plan.steps if st[0] == "onchip")
-                                + " buckets)",
-                                "peak_derivation": "4 warp-instr/clk/SM x 32 x SMs x 2.07 GHz / 12 "
-                                                   "instructions per amplitude-round"},
-            "cpu_baseline": cpu_sweep_baseline(wl) if world == 1 else None,
-            "gpu_launches": None,
-            "per_n_best_P_at_p64": best, "clocks": clk}), flush=True)
+                       "buckets": {n: int(c.shape[0]) for n, (c, _) in buckets.items()},
+                       "paths": {str(st[1]): st[0] for st in plan.steps}},
+            "roofline": roof[dominant]}
+        for kind in kinds:
+            if kind != dominant:
+                line[f"roofline_{kind}"] = roof[kind]
+        line.update({"cpu_baseline": cpu_sweep_baseline(wl) if world == 1 else None,
+                     "gpu_launches": launches * args.steps,
+                     "per_n_best_P_at_p64": best, "clocks": clk})
+        print(json.dumps(line), flush=True)
     return 0
 
 

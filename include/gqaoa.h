@@ -215,26 +215,38 @@ int gqaoa_grad_batched(const uint8_t *cost, int64_t cost_stride, int n, int m, i
                        void *stream);
 
 /*
- * Single-angle-pair sweep (Eq. 5; Appendix C's grid scan) with the state held
- * on chip: `batch` instances of equal n times `angles` angle points, each
- * evolved p rounds from |+> with gamma_k = gammas[a], beta_k = betas[a], and
- * P(C=0) read out after each round count listed in `rounds`.
+ * Single-angle-pair sweep (Eq. 5; Appendix C's grid scan): `batch` instances
+ * of equal n times `angles` angle points, each evolved p rounds from |+> with
+ * gamma_k = gammas[a], beta_k = betas[a], and P(C=0) read out after each
+ * round count listed in `rounds`. One persistent launch; each work item
+ * (instance, angle point) is owned by one CTA or thread-block cluster.
  * cost    device uint8 [batch][2^n] (16-byte aligned).
  * gammas, betas  device double [angles].
  * rounds  host int32 [nrounds], strictly ascending, each in 1..p; nrounds <= 16.
  * out     device double [batch][angles][nrounds] written.
- * ws      device workspace of gqaoa_sweep_workspace_size(angles) bytes.
- * amps_per_thread  16: a thread holds 16 amplitudes in registers (n <= 18);
- *                  32: 16 in registers and 16 in shared memory (n >= 10);
- *                  0: 16 for n <= 18, 32 for n = 19. A CTA has up to 1024
- *                  threads; larger states use a cluster of up to 16 CTAs.
- * n must be in GQAOA_SWEEP_MIN_N..GQAOA_SWEEP_MAX_N.
- * Precision: complex64 state; the mixer sum is FP32 within a warp and
- * double-float across warps and CTAs; P is formed in FP64.
+ * ws      device workspace of gqaoa_sweep_workspace_size(n, angles,
+ *         amps_per_thread) bytes (16-byte aligned), caller-owned.
+ * amps_per_thread  selects where the state lives:
+ *   16  a thread holds 16 amplitudes in registers (n in 9..18);
+ *   32  16 in registers and 16 in shared memory (n in 10..19);
+ *   GQAOA_SWEEP_L2  cluster-resident: one 16-CTA cluster per item keeps
+ *       up to 2^19 amplitudes on chip (2^17 in registers, 3 * 2^17 in shared
+ *       memory: half of an n = 20 state) and the rest in its slot of the
+ *       workspace (16 slots of 2^n * 8 bytes), which stays in L2 while the
+ *       items in flight fit there (n = 20: 4 MiB touched per item, at most
+ *       16 items); n in GQAOA_SWEEP_L2_MIN_N..GQAOA_SWEEP_L2_MAX_N;
+ *   0   16 for n <= 18, 32 for n = 19, GQAOA_SWEEP_L2 for n >= 20.
+ *   Other values: GQAOA_EINVAL; n outside the selected range: GQAOA_ERANGE.
+ * Precision: complex64 state; the mixer sum is FP32 within a warp
+ * (GQAOA_SWEEP_L2: double-float within a thread, then FP32 across the warp)
+ * and double-float above that; P is formed in FP64.
  */
 #define GQAOA_SWEEP_MIN_N 9
 #define GQAOA_SWEEP_MAX_N 19
-int gqaoa_sweep_workspace_size(int angles, size_t *bytes);
+#define GQAOA_SWEEP_L2 1
+#define GQAOA_SWEEP_L2_MIN_N 17
+#define GQAOA_SWEEP_L2_MAX_N 24
+int gqaoa_sweep_workspace_size(int n, int angles, int amps_per_thread, size_t *bytes);
 int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const double *gammas,
                 const double *betas, int angles, int p, const int32_t *rounds, int nrounds,
                 int amps_per_thread, double *out, void *ws, size_t ws_bytes, void *stream);

@@ -27,6 +27,9 @@ GQAOA_MAX_N = 34
 GQAOA_MAX_M = 255
 GQAOA_SWEEP_MIN_N = 9
 GQAOA_SWEEP_MAX_N = 19
+GQAOA_SWEEP_L2 = 1
+GQAOA_SWEEP_L2_MIN_N = 17
+GQAOA_SWEEP_L2_MAX_N = 24
 
 
 class GQAOAError(RuntimeError):
@@ -63,7 +66,7 @@ SIGNATURES = {
     "gqaoa_grad_batched_workspace_size": [_I, _I, _I, _SZP],
     "gqaoa_grad_batched": [_P, _I64, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P],
     "gqaoa_evolve_noalloc": [_P, _I, _I, _P, _P, _I, _P, _P, _P, _U, _P],
-    "gqaoa_sweep_workspace_size": [_I, _SZP],
+    "gqaoa_sweep_workspace_size": [_I, _I, _I, _SZP],
     "gqaoa_sweep": [_P, _I, _I, _I, _P, _P, _I, _I, _P, _I, _I, _P, _P, _SZ, _P],
     "gqaoa_mlp_param_count": [_I, _I, _I, _SZP],
     "gqaoa_mlp_workspace_size": [_I, _I, _I, _I, _SZP],
@@ -179,8 +182,8 @@ def gqaoa_grad_batched(cost, cost_stride, n, m, batch, gammas, betas, p, objecti
           dgamma, dbeta, ws, ws_bytes, stream)
 
 
-def gqaoa_sweep_workspace_size(angles) -> int:
-    return _size("gqaoa_sweep_workspace_size", angles)
+def gqaoa_sweep_workspace_size(n, angles, amps_per_thread=0) -> int:
+    return _size("gqaoa_sweep_workspace_size", n, angles, amps_per_thread)
 
 
 def gqaoa_sweep(cost, n, m, batch, gammas, betas, angles, p, rounds, nrounds, amps_per_thread,

@@ -40,6 +40,7 @@ struct SweepArgs {
   const float2 *phase;   // [A][256]
   const double2 *alpha;  // [A]
   double *out;           // [B][A][R]
+  float4 *scratch;       // cluster-resident path: [kL2Slots][N / 2]
   uint64_t nitems;       // B * A
   int n;
   int A;
@@ -246,6 +247,298 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
   if (kCluster > 1) cluster_sync();  // no CTA leaves while a peer may read its shared memory
 }
 
+// ---------------------------------------------------------------------------
+// Cluster-resident sweep: states too large for a cluster's registers and
+// shared memory (n >= 17 here; n = 20 is the case that matters). One item per
+// 16-CTA cluster of 512-thread CTAs, one CTA per SM. CTA r owns the r-th
+// sixteenth of the state; thread t owns the float4 (two amplitudes)
+// r N/32 + j 512 + t for j = 0..V-1, so every warp access is 512 contiguous
+// bytes. Of a thread's V float4 the first kL2RegVec stay in registers and
+// the next (up to) kL2SmemVec in shared memory for the whole evolution; the
+// rest live in the cluster's slot of the workspace and stream through a
+// small register ring, interleaved with the shared-memory part so the SM's
+// L2 port stays busy all round. Each thread rereads only what it wrote, so
+// the slot needs no synchronisation beyond program order. At most kL2Slots
+// items are in flight (one per resident cluster, seven on GB300), whose
+// slots total 28 MiB at n = 20 (half the state is on chip): the
+// per-round read-modify-write of them
+// is served by the 129 MB L2, whose read-modify-write bandwidth is about
+// twice that of HBM (and per SM about 95 GB/s, whatever the loads in
+// flight, which is why the on-chip share matters).
+//
+// The mixer sum: FP32 over at most 8 amplitudes, double-float per thread,
+// FP32 across a warp's lanes (butterfly), double-float per CTA (warp 0). Warp 0 then pushes its CTA's
+// partial into the shared memory of every CTA of the cluster (lane r stores
+// to CTA r), one cluster barrier (release/acquire) makes the kL2Cluster
+// partials visible locally, and every warp sums them in rank order, so all
+// warps of all CTAs hold the same a_k bit for bit with no further barrier.
+// ---------------------------------------------------------------------------
+constexpr int kL2Threads = 512;
+constexpr int kL2Warps = kL2Threads / 32;
+constexpr int kL2Cluster = 16;
+constexpr int kL2Slots = 16;
+constexpr int kL2RegVec = 8;    // float4 per thread held in registers
+constexpr int kL2SmemVec = 24;  // float4 per thread held in shared memory (at most)
+constexpr int kL2Batch = 2;     // float4 per thread per global batch
+constexpr int kL2Depth = 2;     // batches in the register ring
+constexpr size_t kL2DynSmem = (size_t)kL2SmemVec * kL2Threads * (sizeof(float4) + sizeof(uint16_t));
+
+__device__ __forceinline__ void st_dsmem_f32x2(float2 *p, unsigned rank, float2 v) {
+  uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(remote), "f"(v.x), "f"(v.y)
+               : "memory");
+}
+
+// chi = T[c] (psi + a) for one float4 (two amplitudes, cost bytes in c2),
+// adding to the FP32 partials v.
+template <bool kExtra>
+__device__ __forceinline__ void l2_vec(float4 &x, unsigned c2, const float2 *s_T, float2 ad,
+                                       float (&v)[kSlots], bool ro, bool first) {
+  const unsigned c0 = c2 & 0xFFu, c1 = (c2 >> 8) & 0xFFu;
+  const float2 x0 = cmul(s_T[c0], make_float2(x.x + ad.x, x.y + ad.y));
+  const float2 x1 = cmul(s_T[c1], make_float2(x.z + ad.x, x.w + ad.y));
+  x = make_float4(x0.x, x0.y, x1.x, x1.y);
+  v[0] += x0.x + x1.x;
+  v[1] += x0.y + x1.y;
+  if (kExtra) {
+    if (c0 == 0) {
+      if (ro) { v[2] += x0.x * x0.x + x0.y * x0.y; v[3] += x0.x; v[4] += x0.y; }
+      if (first) v[5] += 1.f;
+    }
+    if (c1 == 0) {
+      if (ro) { v[2] += x1.x * x1.x + x1.y * x1.y; v[3] += x1.x; v[4] += x1.y; }
+      if (first) v[5] += 1.f;
+    }
+  }
+}
+
+template <bool kExtra>
+__device__ __forceinline__ void l2_fold(float (&v)[kSlots], DF (&acc)[kSlots]) {
+#pragma unroll
+  for (int k = 0; k < kSlots; ++k)
+    if (kExtra || k < 2) {
+      acc[k].add(v[k]);
+      v[k] = 0.f;
+    }
+}
+
+// One round over a thread's V = kL2RegVec + S + kL2Batch G float4: the
+// global batches (each followed by a shared-memory pair while any remain),
+// the rest of shared memory, then the registers.
+template <bool kExtra>
+__device__ __forceinline__ void l2_round(float4 (&xr)[kL2RegVec],
+                                         const uint32_t (&cr)[kL2RegVec / 2], float4 *s_state,
+                                         const uint16_t *s_cost, float4 *gbase,
+                                         const uint16_t *gcost, int S, int G, const float2 *s_T,
+                                         float2 ad, float amp0, DF (&acc)[kSlots], bool ro,
+                                         bool first) {
+  constexpr int T = kL2Threads;
+  const int t = threadIdx.x;
+  const float4 plus = make_float4(amp0, 0.f, amp0, 0.f);
+  // walking pointers (next batch to load, next to store): every access is a
+  // base plus an immediate offset
+  const float4 *lp = gbase;
+  const uint16_t *lc = gcost;
+  float4 *sp = gbase;
+  float v[kSlots] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float4 x[kL2Depth][kL2Batch];
+  uint32_t c[kL2Depth][kL2Batch];
+  auto load = [&](float4 (&xx)[kL2Batch], uint32_t (&cc)[kL2Batch]) {
+#pragma unroll
+    for (int k = 0; k < kL2Batch; ++k) cc[k] = lc[k * T];
+#pragma unroll
+    for (int k = 0; k < kL2Batch; ++k) xx[k] = first ? plus : __ldcg(lp + k * T);
+    lp += kL2Batch * T;
+    lc += kL2Batch * T;
+  };
+  auto smem_pair = [&](int j) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      float4 y = first ? plus : s_state[(j + k) * T + t];
+      l2_vec<kExtra>(y, s_cost[(j + k) * T + t], s_T, ad, v, ro, first);
+      s_state[(j + k) * T + t] = y;
+    }
+  };
+#pragma unroll
+  for (int d = 0; d + 1 < kL2Depth; ++d)
+    if (d < G) load(x[d], c[d]);
+  // global batches, each followed by a shared-memory pair while any remain
+  int js = 0;
+#pragma unroll 1
+  for (int g0 = 0; g0 < G; g0 += kL2Depth) {
+#pragma unroll
+    for (int d = 0; d < kL2Depth; ++d) {
+      const int g = g0 + d;
+      if (g < G) {
+        constexpr int kAhead = kL2Depth - 1;
+        const int slot = (d + kAhead) % kL2Depth;  // freed by batch g - 1
+        if (g + kAhead < G) load(x[slot], c[slot]);
+#pragma unroll
+        for (int k = 0; k < kL2Batch; ++k) l2_vec<kExtra>(x[d][k], c[d][k], s_T, ad, v, ro, first);
+#pragma unroll
+        for (int k = 0; k < kL2Batch; ++k) __stcg(sp + k * T, x[d][k]);
+        sp += kL2Batch * T;
+        if (js < S) {
+          smem_pair(js);
+          js += 2;
+        }
+        l2_fold<kExtra>(v, acc);
+      }
+    }
+  }
+#pragma unroll 1
+  for (; js < S; js += 2) {
+    smem_pair(js);
+    l2_fold<kExtra>(v, acc);
+  }
+  // registers last: the final global stores complete meanwhile
+#pragma unroll
+  for (int k = 0; k < kL2RegVec; ++k) {
+    if (first) xr[k] = plus;
+    l2_vec<kExtra>(xr[k], cr[k >> 1] >> (16 * (k & 1)), s_T, ad, v, ro, first);
+    if ((k & 3) == 3) l2_fold<kExtra>(v, acc);
+  }
+}
+
+__global__ void __launch_bounds__(kL2Threads, 1) sweep_l2_kernel(const __grid_constant__ SweepArgs a) {
+  constexpr int T = kL2Threads;
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  float4 *s_state = reinterpret_cast<float4 *>(s_dyn);  // [kL2SmemVec][T]
+  uint16_t *s_cost =
+      reinterpret_cast<uint16_t *>(s_dyn + sizeof(float4) * kL2SmemVec * T);  // [kL2SmemVec][T]
+  __shared__ float2 s_T[256];
+  __shared__ float2 s_wp[2][kL2Warps][kSlots];    // warp partials (double-float)
+  __shared__ float2 s_ps[2][kL2Cluster][kSlots];  // CTA partials, pushed by every CTA
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned rank = cluster_ctarank();
+  const uint64_t cluster_id = blockIdx.x / kL2Cluster, nclusters = gridDim.x / kL2Cluster;
+  const uint64_t N = 1ull << a.n, Nv = N / 2;
+  const int V = (int)(Nv / ((uint64_t)kL2Cluster * T));  // float4 per thread (>= 8)
+  const int S = V - kL2RegVec < kL2SmemVec ? V - kL2RegVec : kL2SmemVec;
+  const int G = (V - kL2RegVec - S) / kL2Batch;
+  const float inv_n = (float)(1.0 / (double)N);
+  const float amp0 = (float)(1.0 / sqrt((double)N));
+  const uint64_t seg0 = (uint64_t)rank * (Nv / kL2Cluster);
+  float4 *gbase = a.scratch + cluster_id * Nv + seg0 + (uint64_t)(kL2RegVec + S) * T + threadIdx.x;
+  int buf = 0;
+
+  for (uint64_t item = cluster_id; item < a.nitems; item += nclusters) {
+    const uint64_t b = item / (uint64_t)a.A;
+    const int ai = (int)(item % (uint64_t)a.A);
+    const uint16_t *cseg = reinterpret_cast<const uint16_t *>(a.cost + b * N) + seg0 + threadIdx.x;
+    uint32_t cr[kL2RegVec / 2];
+#pragma unroll
+    for (int k = 0; k < kL2RegVec / 2; ++k)
+      cr[k] = (uint32_t)cseg[(2 * k) * T] | ((uint32_t)cseg[(2 * k + 1) * T] << 16);
+    for (int j = 0; j < S; ++j) s_cost[j * T + threadIdx.x] = cseg[(kL2RegVec + j) * T];
+    const uint16_t *gcost = cseg + (kL2RegVec + S) * T;
+    for (int i = threadIdx.x; i < 256; i += T) s_T[i] = a.phase[(size_t)ai * 256 + i];
+    const double2 ald = a.alpha[ai];
+    const float alr = (float)ald.x, ali = (float)ald.y;
+    __syncthreads();
+    float4 xr[kL2RegVec];
+    float2 ad = make_float2(0.f, 0.f);  // pending mixer add
+    float cnt0 = 0.f;                   // C = 0 count of the instance
+    int ridx = 0;
+    for (int r = 0; r < a.p; ++r) {
+      const bool ro = ridx < a.R && a.rounds[ridx] == r + 1;
+      const bool first = r == 0;
+      const bool extra = ro || first;
+      const int nv = extra ? kSlots : 2;
+      DF acc[kSlots];
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k) acc[k].zero();
+      if (extra)
+        l2_round<true>(xr, cr, s_state, s_cost, gbase, gcost, S, G, s_T, ad, amp0, acc, ro, first);
+      else
+        l2_round<false>(xr, cr, s_state, s_cost, gbase, gcost, S, G, s_T, ad, amp0, acc, false,
+                        false);
+      float hi[kSlots], lo[kSlots];
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k) {
+        hi[k] = k < nv ? warp_fsum(acc[k].hi + acc[k].lo) : 0.f;
+        lo[k] = 0.f;
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k)
+          if (k < nv) s_wp[buf][warp][k] = make_float2(hi[k], lo[k]);
+      }
+      __syncthreads();
+      if (warp == 0) {
+        // this CTA's partial, pushed to every CTA of the cluster
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k) {
+          const float2 d = (k < nv && lane < kL2Warps) ? s_wp[buf][lane][k] : make_float2(0.f, 0.f);
+          hi[k] = d.x;
+          lo[k] = d.y;
+          if (k < nv) df_warp(hi[k], lo[k]);
+        }
+        if (lane < kL2Cluster) {
+#pragma unroll
+          for (int k = 0; k < kSlots; ++k)
+            if (k < nv) st_dsmem_f32x2(&s_ps[buf][rank][k], (unsigned)lane, make_float2(hi[k], lo[k]));
+        }
+      }
+      cluster_sync();  // release/acquire: every CTA's partial visible locally
+      // every warp: the cluster sum in rank order
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k) {
+        const float2 d = (k < nv && lane < kL2Cluster) ? s_ps[buf][lane][k] : make_float2(0.f, 0.f);
+        hi[k] = d.x;
+        lo[k] = d.y;
+        if (k < nv) df_warp(hi[k], lo[k]);
+      }
+      const float Sr = hi[0] + lo[0], Si = hi[1] + lo[1];
+      const float ar = (alr * Sr - ali * Si) * inv_n, aim = (alr * Si + ali * Sr) * inv_n;
+      if (first) cnt0 = hi[5] + lo[5];
+      if (ro && rank == 0 && threadIdx.x == 0) {
+        // sum_{C=0} |chi + a|^2 = A0 + 2 Re(conj(a) B0) + h[0] |a|^2
+        const double A0 = (double)hi[2] + lo[2], Br = (double)hi[3] + lo[3],
+                     Bi = (double)hi[4] + lo[4];
+        const double P = A0 + 2.0 * ((double)ar * Br + (double)aim * Bi) +
+                         (double)cnt0 * ((double)ar * ar + (double)aim * aim);
+        a.out[(b * (uint64_t)a.A + ai) * a.R + ridx] = P;
+      }
+      ad = make_float2(ar, aim);
+      if (ro) ++ridx;
+      buf ^= 1;
+    }
+    __syncthreads();  // s_T and s_cost are rewritten for the next item
+  }
+  cluster_sync();  // no CTA leaves while a peer may still store into its shared memory
+}
+
+static int launch_sweep_l2(const SweepArgs &args, cudaStream_t st) {
+  auto kernel = sweep_l2_kernel;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kL2DynSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return GQAOA_ECUDA;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kL2Cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kL2Cluster, 1, 1);
+  cfg.blockDim = dim3(kL2Threads, 1, 1);
+  cfg.dynamicSmemBytes = kL2DynSmem;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg) != cudaSuccess) return GQAOA_ECUDA;
+  if (clusters < 1) return GQAOA_ECUDA;
+  uint64_t units = clusters < kL2Slots ? (uint64_t)clusters : (uint64_t)kL2Slots;
+  if (args.nitems < units) units = args.nitems;
+  cfg.gridDim = dim3((unsigned)(units * kL2Cluster), 1, 1);
+  cfg.stream = st;
+  if (cudaLaunchKernelEx(&cfg, kernel, args) != cudaSuccess) return GQAOA_ECUDA;
+  return GQAOA_OK;
+}
+
 struct SweepShape {
   int threads;
   int cluster;
@@ -312,23 +605,45 @@ static int launch_sweep(const SweepArgs &args, cudaStream_t st) {
   return GQAOA_OK;
 }
 
-static size_t sweep_ws_layout(int A, char *base, float2 **phase, double2 **alpha) {
+static size_t sweep_ws_layout(int n, int A, bool resident, char *base, float2 **phase,
+                              double2 **alpha, float4 **scratch) {
   const size_t o_alpha = round_up(sizeof(float2) * 256 * (size_t)A, 256);
+  const size_t o_scratch = o_alpha + round_up(sizeof(double2) * (size_t)A, 256);
+  const size_t scratch_bytes = resident ? (size_t)kL2Slots * (sizeof(float2) << n) : 0;
   if (base) {
     *phase = reinterpret_cast<float2 *>(base);
     *alpha = reinterpret_cast<double2 *>(base + o_alpha);
+    *scratch = resident ? reinterpret_cast<float4 *>(base + o_scratch) : nullptr;
   }
-  return o_alpha + round_up(sizeof(double2) * (size_t)A, 256);
+  return o_scratch + scratch_bytes;
+}
+
+// 0 picks 16 (n <= 18), 32 (n = 19) or the cluster-resident path (n >= 20).
+static int sweep_mode(int n, int amps_per_thread) {
+  if (amps_per_thread != 0) return amps_per_thread;
+  return n <= 18 ? 16 : (n == 19 ? 32 : GQAOA_SWEEP_L2);
+}
+
+static int sweep_check_n(int n, int mode) {
+  if (mode == GQAOA_SWEEP_L2)
+    return (n < GQAOA_SWEEP_L2_MIN_N || n > GQAOA_SWEEP_L2_MAX_N) ? GQAOA_ERANGE : GQAOA_OK;
+  if (mode != 16 && mode != 32) return GQAOA_EINVAL;
+  if (n < GQAOA_SWEEP_MIN_N || n > GQAOA_SWEEP_MAX_N) return GQAOA_ERANGE;
+  if ((mode == 16 && n > 18) || (mode == 32 && n < 10)) return GQAOA_ERANGE;
+  return GQAOA_OK;
 }
 
 }  // namespace gq
 
 using namespace gq;
 
-extern "C" int gqaoa_sweep_workspace_size(int angles, size_t *bytes) {
+extern "C" int gqaoa_sweep_workspace_size(int n, int angles, int amps_per_thread, size_t *bytes) {
   if (!bytes) return GQAOA_EINVAL;
   if (angles < 1 || angles > (1 << 24)) return GQAOA_ERANGE;
-  *bytes = sweep_ws_layout(angles, nullptr, nullptr, nullptr);
+  const int mode = sweep_mode(n, amps_per_thread);
+  const int rc = sweep_check_n(n, mode);
+  if (rc) return rc;
+  *bytes = sweep_ws_layout(n, angles, mode == GQAOA_SWEEP_L2, nullptr, nullptr, nullptr, nullptr);
   return GQAOA_OK;
 }
 
@@ -337,10 +652,13 @@ extern "C" int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const d
                            int nrounds, int amps_per_thread, double *out, void *ws,
                            size_t ws_bytes, void *stream) {
   gq::NvtxRange nvtx_range("gqaoa_sweep");
-  if (n < GQAOA_SWEEP_MIN_N || n > GQAOA_SWEEP_MAX_N || m < 0 || m > GQAOA_MAX_M || batch < 1 ||
-      angles < 1 || angles > (1 << 24) || p < 1 || p > (1 << 20) || nrounds < 1 ||
-      nrounds > kSweepMaxRounds)
+  if (m < 0 || m > GQAOA_MAX_M || batch < 1 || angles < 1 || angles > (1 << 24) || p < 1 ||
+      p > (1 << 20) || nrounds < 1 || nrounds > kSweepMaxRounds)
     return GQAOA_ERANGE;
+  if (n < GQAOA_SWEEP_MIN_N || n > GQAOA_SWEEP_L2_MAX_N) return GQAOA_ERANGE;
+  const int mode = sweep_mode(n, amps_per_thread);
+  int rc = sweep_check_n(n, mode);
+  if (rc) return rc;
   if (!cost || !gammas || !betas || !rounds || !out || !ws) return GQAOA_EINVAL;
   if (!aligned16(cost) || !aligned8(gammas) || !aligned8(betas) || !aligned8(out) ||
       !aligned16(ws))
@@ -349,28 +667,30 @@ extern "C" int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const d
     if (rounds[i] < 1 || rounds[i] > p) return GQAOA_ERANGE;
     if (i > 0 && rounds[i] <= rounds[i - 1]) return GQAOA_EINVAL;
   }
-  if (amps_per_thread == 0) amps_per_thread = n <= 18 ? 16 : 32;
-  if (amps_per_thread != 16 && amps_per_thread != 32) return GQAOA_EINVAL;
-  if ((amps_per_thread == 16 && n > 18) || (amps_per_thread == 32 && n < 10)) return GQAOA_ERANGE;
-  if (ws_bytes < sweep_ws_layout(angles, nullptr, nullptr, nullptr)) return GQAOA_ENOMEM;
+  const bool resident = mode == GQAOA_SWEEP_L2;
+  if (ws_bytes < sweep_ws_layout(n, angles, resident, nullptr, nullptr, nullptr, nullptr))
+    return GQAOA_ENOMEM;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SweepArgs args = {};
   float2 *phase = nullptr;
   double2 *alpha = nullptr;
-  sweep_ws_layout(angles, static_cast<char *>(ws), &phase, &alpha);
-  int rc = phase_tables(gammas, betas, angles, phase, alpha, st);
+  float4 *scratch = nullptr;
+  sweep_ws_layout(n, angles, resident, static_cast<char *>(ws), &phase, &alpha, &scratch);
+  rc = phase_tables(gammas, betas, angles, phase, alpha, st);
   if (rc) return rc;
   args.cost = cost;
   args.phase = phase;
   args.alpha = alpha;
   args.out = out;
+  args.scratch = scratch;
   args.nitems = (uint64_t)batch * (uint64_t)angles;
   args.n = n;
   args.A = angles;
   args.p = p;
   args.R = nrounds;
   for (int i = 0; i < nrounds; ++i) args.rounds[i] = rounds[i];
-  const SweepShape sh = sweep_shape(n, amps_per_thread);
+  if (resident) return launch_sweep_l2(args, st);
+  const SweepShape sh = sweep_shape(n, mode);
   if (sh.smem_half) {
     switch (sh.threads * 100 + sh.cluster) {
       case 32 * 100 + 1: return launch_sweep<32, 1, true>(args, st);

@@ -112,7 +112,7 @@ def single_angle_grid_start(cost: torch.Tensor, n: int, m: int, p: int, grid: in
                             objective: str = "p0"):
     """Best single angle pair (Eq. 5) on a grid x grid lattice of [0, 2pi) x [0, pi)
     per instance (cost [B, 2^n]). P(C=0) of every lattice point comes from one
-    on-chip sweep (gqaoa_sweep) when n allows, else from batched evolution with
+    persistent sweep (gqaoa_sweep) when n allows, else from batched evolution with
     the instance's cost table shared by the lattice. Returns gammas [B], betas [B]."""
     B = cost.shape[0]
     gs = (np.arange(grid) + 0.5) * (2 * np.pi / grid)
@@ -120,11 +120,11 @@ def single_angle_grid_start(cost: torch.Tensor, n: int, m: int, p: int, grid: in
     G = np.repeat(gs, grid)
     Bt = np.tile(bs, grid)
     A = grid * grid
-    if objective == "p0" and C.GQAOA_SWEEP_MIN_N <= n <= C.GQAOA_SWEEP_MAX_N:
+    if objective == "p0" and C.GQAOA_SWEEP_MIN_N <= n <= C.GQAOA_SWEEP_L2_MAX_N:
         gd = torch.as_tensor(G, device=cost.device)
         bd = torch.as_tensor(Bt, device=cost.device)
         out = torch.empty((B, A, 1), dtype=torch.float64, device=cost.device)
-        ws = core.workspace(C.gqaoa_sweep_workspace_size(A), cost.device)
+        ws = core.workspace(C.gqaoa_sweep_workspace_size(n, A, 0), cost.device)
         r = np.array([p], dtype=np.int32)
         C.gqaoa_sweep(cost.data_ptr(), n, m, B, gd.data_ptr(), bd.data_ptr(), A, p, r.ctypes.data, 1,
                       0, out.data_ptr(), ws.data_ptr(), ws.numel(),

@@ -7,14 +7,17 @@ chooses for its n:
     (instance, angle point) holding the state on chip (9 <= n <= 19), with
     16 amplitudes per thread in registers ("apt": 16) or 16 more in shared
     memory ("apt": 32);
+  * "l2": gqaoa_sweep's cluster-resident path (17 <= n <= 24): one 16-CTA
+    cluster per item keeps part of the state in shared memory and the rest in
+    a workspace slot that stays in L2 while the few items in flight fit there;
   * "stream": gqaoa_evolve_batched with the instance's cost table shared by a
-    chunk of angle points and a per-round trace of P(C=0); the chunk size is
-    chosen so the chunk's states stay resident in L2.
-Every buffer and workspace is allocated when the plan is built. The on-chip
-buckets (one persistent launch each) are captured into one CUDA graph and
-replayed; the streaming buckets issue p + 3 launches per chunk of several GB
-each, so they run eagerly after the graph (launch overhead ~2 % there, and a
-graph of hundreds of thousands of nodes would cost more than it saves).
+    chunk of angle points and a per-round trace of P(C=0).
+Every buffer and workspace is allocated when the plan is built. The
+gqaoa_sweep buckets (one persistent launch each) are captured into one CUDA
+graph and replayed; the streaming buckets issue p + 3 launches per chunk of
+several GB each, so they run eagerly after the graph (launch overhead ~2 %
+there, and a graph of hundreds of thousands of nodes would cost more than it
+saves).
 """
 
 from __future__ import annotations
@@ -42,8 +45,16 @@ def load_table(path: str = TABLE_PATH) -> dict:
 def default_choice(n: int) -> dict:
     if C.GQAOA_SWEEP_MIN_N <= n <= C.GQAOA_SWEEP_MAX_N:
         return {"path": "onchip"}
-    # keep a chunk of states within ~64 MiB of L2
-    return {"path": "stream", "angle_batch": max(1, (64 << 20) // ((1 << n) * 8))}
+    if n <= C.GQAOA_SWEEP_L2_MAX_N:
+        return {"path": "l2"}
+    return {"path": "stream", "angle_batch": max(1, (1 << 30) // ((1 << n) * 8))}
+
+
+def sweep_apt(choice: dict) -> int:
+    """The amps_per_thread argument of gqaoa_sweep for an "onchip" or "l2" choice."""
+    if choice["path"] == "l2":
+        return C.GQAOA_SWEEP_L2
+    return int(choice.get("apt", 0))
 
 
 class SweepPlan:
@@ -74,9 +85,10 @@ class SweepPlan:
             choice = self.table.get(n, default_choice(n))
             out = torch.empty((B, self.A, self.R), dtype=torch.float64, device=self.device)
             self.out[n] = out
-            if choice["path"] == "onchip":
-                ws = core.workspace(C.gqaoa_sweep_workspace_size(self.A), self.device)
-                self.steps.append(("onchip", n, m, cost, out, (ws, int(choice.get("apt", 0)))))
+            if choice["path"] in ("onchip", "l2"):
+                apt = sweep_apt(choice)
+                ws = core.workspace(C.gqaoa_sweep_workspace_size(n, self.A, apt), self.device)
+                self.steps.append((choice["path"], n, m, cost, out, (ws, apt)))
             else:
                 S = int(min(self.A, choice["angle_batch"]))
                 state = torch.empty((S, 1 << n), dtype=torch.complex64, device=self.device)
@@ -88,13 +100,21 @@ class SweepPlan:
     def amp_rounds(self) -> int:
         return sum(st[3].shape[0] * self.A * self.p * (1 << st[1]) for st in self.steps)
 
-    def run(self, onchip: bool = True, stream: bool = True):
+    def kinds(self) -> list:
+        """The paths this plan uses, in launch order."""
+        return [k for k in ("onchip", "l2", "stream") if any(st[0] == k for st in self.steps)]
+
+    def amp_rounds_of(self, kind: str) -> int:
+        return sum(st[3].shape[0] * self.A * self.p * (1 << st[1]) for st in self.steps
+                   if st[0] == kind)
+
+    def run(self, kinds=("onchip", "l2", "stream")):
         s = torch.cuda.current_stream().cuda_stream
         for kind, n, m, cost, out, extra in self.steps:
             B = cost.shape[0]
-            if (kind == "onchip" and not onchip) or (kind == "stream" and not stream):
+            if kind not in kinds:
                 continue
-            if kind == "onchip":
+            if kind in ("onchip", "l2"):
                 ws, apt = extra
                 C.gqaoa_sweep(cost.data_ptr(), n, m, B, self.g.data_ptr(), self.b.data_ptr(),
                               self.A, self.p, self.rounds.ctypes.data, self.R, apt,
@@ -112,18 +132,23 @@ class SweepPlan:
         return self.out
 
     def capture(self):
-        """Record the on-chip launches into a CUDA graph (after one eager
-        warm-up run of everything)."""
+        """Record the persistent gqaoa_sweep launches into one CUDA graph per
+        path ("onchip", "l2"), after one eager warm-up run of everything."""
         self.run()
         torch.cuda.synchronize()
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph):
-            self.run(onchip=True, stream=False)
-        return self.graph
+        self.graphs = {}
+        for kind in ("onchip", "l2"):
+            if kind in self.kinds():
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    self.run(kinds=(kind,))
+                self.graphs[kind] = g
+        return self.graphs
 
     def replay(self):
-        self.graph.replay()
-        self.run(onchip=False, stream=True)
+        for g in self.graphs.values():
+            g.replay()
+        self.run(kinds=("stream",))
         return self.out
 
 

@@ -5,8 +5,10 @@ JSON table that SweepPlan loads.
     python -m paper_2402_02585_gb300.tune [--out PATH] [--n 12 13 ...]
 
 Candidates: the on-chip sweep with 16 amplitudes per thread in registers
-(9 <= n <= 18) or 16 more in shared memory (10 <= n <= 19), and the streaming
-path with chunks of 16..256 angle points sharing the instance's cost table. The score is
+(9 <= n <= 18) or 16 more in shared memory (10 <= n <= 19), the
+cluster-resident sweep with L2-resident workspace slots (17 <= n <= 24), and
+the streaming path with chunks of 16..256 angle points sharing the instance's
+cost table. The score is
 amplitude-rounds per second on a small synthetic bucket of the workload's
 recipe (d = 4.2, p = 16).
 """
@@ -53,6 +55,8 @@ def tune(n_values, p: int = 16, angles: int = 256, verbose: bool = True) -> dict
             cands.append({"path": "onchip", "apt": 16})
         if 10 <= n <= C.GQAOA_SWEEP_MAX_N:
             cands.append({"path": "onchip", "apt": 32})
+        if C.GQAOA_SWEEP_L2_MIN_N <= n <= C.GQAOA_SWEEP_L2_MAX_N:
+            cands.append({"path": "l2"})
         for S in (16, 64, 256):
             if S <= angles and (S << n) * 8 <= (4 << 30):
                 cands.append({"path": "stream", "angle_batch": S})

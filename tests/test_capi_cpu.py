@@ -117,6 +117,22 @@ def test_sample_and_grad_reject_bad_arguments_before_launch():
     assert e.value.status == C.GQAOA_ENOMEM
 
 
+def test_sweep_workspace_sizes():
+    small = C.gqaoa_sweep_workspace_size(12, 4, 0)
+    assert 0 < small < 1 << 16
+    assert C.gqaoa_sweep_workspace_size(19, 4, 32) == small
+    resident = C.gqaoa_sweep_workspace_size(20, 4, C.GQAOA_SWEEP_L2)
+    assert resident == small + 16 * 8 * (1 << 20)       # 16 slots of 2^20 complex64
+    assert C.gqaoa_sweep_workspace_size(20, 4, 0) == resident
+    for n, apt in ((20, 16), (20, 32), (25, 0), (16, C.GQAOA_SWEEP_L2)):
+        with pytest.raises(C.GQAOAError) as e:
+            C.gqaoa_sweep_workspace_size(n, 4, apt)
+        assert e.value.status == C.GQAOA_ERANGE
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_sweep_workspace_size(12, 4, 8)
+    assert e.value.status == C.GQAOA_EINVAL
+
+
 def test_sweep_rejects_bad_arguments_before_launch():
     fake = 1 << 20
     r = np.array([2, 1], dtype=np.int32)
@@ -129,8 +145,15 @@ def test_sweep_rejects_bad_arguments_before_launch():
     assert e.value.status == C.GQAOA_ERANGE
     r = np.array([4], dtype=np.int32)
     with pytest.raises(C.GQAOAError) as e:
-        C.gqaoa_sweep(fake, 20, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, 0, fake, fake, 1 << 20, None)
+        C.gqaoa_sweep(fake, 25, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, 0, fake, fake, 1 << 20, None)
     assert e.value.status == C.GQAOA_ERANGE
+    with pytest.raises(C.GQAOAError) as e:  # the cluster-resident path starts at n = 17
+        C.gqaoa_sweep(fake, 16, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, C.GQAOA_SWEEP_L2, fake,
+                      fake, 1 << 30, None)
+    assert e.value.status == C.GQAOA_ERANGE
+    with pytest.raises(C.GQAOAError) as e:  # 16 slots of 2^20 amplitudes do not fit in 1 MiB
+        C.gqaoa_sweep(fake, 20, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, 0, fake, fake, 1 << 20, None)
+    assert e.value.status == C.GQAOA_ENOMEM
     with pytest.raises(C.GQAOAError) as e:  # 16 per thread cannot hold n = 19
         C.gqaoa_sweep(fake, 19, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, 16, fake, fake, 1 << 20, None)
     assert e.value.status == C.GQAOA_ERANGE

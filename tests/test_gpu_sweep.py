@@ -1,11 +1,14 @@
-"""The on-chip single-angle-pair sweep (gqaoa_sweep) against the oracle.
+"""The single-angle-pair sweep (gqaoa_sweep) against the oracle.
 
 P(C=0) after the requested round counts must agree with the FP64 oracle
 within 1e-6 for every (instance, angle point): the full statevector oracle at
 small n, the exact cost-class model (pinned against it) at larger n. The
-cases cover one warp per item (n = 9), whole CTAs (n = 12..14), clusters
-of 2, 4, 8 and 16 CTAs (n = 15..18), a 16-CTA cluster with half the state in
-shared memory (n = 19), and more items than resident CTAs.
+on-chip cases cover one warp per item (n = 9), whole CTAs (n = 12..14),
+clusters of 2, 4, 8 and 16 CTAs (n = 15..18), a 16-CTA cluster with half the
+state in shared memory (n = 19), and more items than resident CTAs. The
+cluster-resident path (GQAOA_SWEEP_L2) covers states held entirely in shared
+memory (n = 17, 18), split between shared memory and the workspace
+(n = 19..22), and more items than resident clusters.
 """
 
 import math
@@ -27,7 +30,7 @@ def run_sweep(costs, n, m, G, Bt, p, rounds, apt=0):
     gd = torch.as_tensor(np.asarray(G, dtype=np.float64), device="cuda")
     bd = torch.as_tensor(np.asarray(Bt, dtype=np.float64), device="cuda")
     out = torch.full((B, A, len(rounds)), -1.0, dtype=torch.float64, device="cuda")
-    ws = core.workspace(C.gqaoa_sweep_workspace_size(A))
+    ws = core.workspace(C.gqaoa_sweep_workspace_size(n, A, apt))
     r = np.ascontiguousarray(rounds, dtype=np.int32)
     C.gqaoa_sweep(costs.data_ptr(), n, m, B, gd.data_ptr(), bd.data_ptr(), A, p, r.ctypes.data,
                   len(rounds), apt, out.data_ptr(), ws.data_ptr(), ws.numel(),
@@ -73,6 +76,48 @@ def test_sweep_matches_oracle(n, B, A, p, rounds, apt):
                 _, tr = reduced.evolve(hists[i], [G[a]] * p, [Bt[a]] * p, trace=True)
             ref = tr[np.asarray(rounds) - 1]
             assert np.max(np.abs(got[i, a] - ref)) < 1e-6, (i, a, got[i, a], ref)
+
+
+@pytest.mark.parametrize("n,B,A,p,rounds", [
+    (17, 2, 13, 6, [1, 6]),      # 26 items: more than the resident clusters
+    (18, 1, 2, 5, [2, 5]),
+    (19, 1, 3, 8, [1, 4, 8]),    # 3/4 of the state in shared memory
+    (20, 2, 3, 10, [1, 5, 10]),  # 3/8 in shared memory, the rest in the workspace
+    (21, 1, 2, 6, [6]),
+    (22, 1, 2, 4, [1, 4]),
+])
+def test_sweep_cluster_resident_matches_oracle(n, B, A, p, rounds):
+    m = int(math.floor(4.2 * n + 0.5))
+    costs, hists = [], []
+    for i in range(B):
+        c, h = core.build_cost(instances.random_3sat(n, m, 1700 + 10 * n + i), n)
+        costs.append(c)
+        hists.append(h.cpu().numpy())
+    rng = np.random.default_rng(100 + n)
+    G = rng.uniform(0, np.pi, A)
+    Bt = rng.uniform(0, np.pi, A)
+    G[0] = 0.0  # gamma = 0 keeps the random-guess probability h[0] / 2^n
+    got = run_sweep(torch.stack(costs), n, m, G, Bt, p, rounds, C.GQAOA_SWEEP_L2)
+    for i in range(B):
+        assert np.max(np.abs(got[i, 0] - hists[i][0] / (1 << n))) < 1e-6
+        for a in range(A):
+            _, tr = reduced.evolve(hists[i], [G[a]] * p, [Bt[a]] * p, trace=True)
+            ref = tr[np.asarray(rounds) - 1]
+            assert np.max(np.abs(got[i, a] - ref)) < 1e-6, (n, i, a, got[i, a], ref)
+
+
+def test_sweep_cluster_resident_agrees_with_on_chip():
+    # n = 19 runs on both paths: same P within the tolerance, items of two instances
+    n, p, rounds = 19, 12, [1, 6, 12]
+    m = int(math.floor(4.2 * n + 0.5))
+    costs = torch.stack([core.build_cost(instances.random_3sat(n, m, 1900 + i), n)[0]
+                         for i in range(2)])
+    rng = np.random.default_rng(19)
+    G = rng.uniform(0, np.pi, 20)
+    Bt = rng.uniform(0, np.pi, 20)
+    a = run_sweep(costs, n, m, G, Bt, p, rounds, 32)
+    b = run_sweep(costs, n, m, G, Bt, p, rounds, C.GQAOA_SWEEP_L2)
+    assert np.max(np.abs(a - b)) < 1e-6
 
 
 def test_sweep_many_items_and_grid_left_endpoints():
