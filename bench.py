@@ -535,9 +535,9 @@ def l2_rmw_peak(device) -> float:
     return 2.0 * x.numel() * 4 * 100 / (e0.elapsed_time(e1) / 1e3) / 1e9
 
 
-# on-chip share of the state on the cluster-resident sweep path:
-# 16 CTAs x 512 threads x (8 float4 in registers + 24 in shared memory) x 2
-L2_PATH_ONCHIP_AMPS = 16 * 512 * (8 + 24) * 2
+# on-chip share of the state on the cluster-resident sweep path: 16 CTAs x
+# 256 on-chip threads x (20 float4 in registers + 48 in shared memory) x 2
+L2_PATH_ONCHIP_AMPS = 16 * 256 * (20 + 48) * 2
 
 
 def run_sweep(args, wl):

@@ -230,11 +230,12 @@ int gqaoa_grad_batched(const uint8_t *cost, int64_t cost_stride, int n, int m, i
  *   16  a thread holds 16 amplitudes in registers (n in 9..18);
  *   32  16 in registers and 16 in shared memory (n in 10..19);
  *   GQAOA_SWEEP_L2  cluster-resident: one 16-CTA cluster per item keeps
- *       up to 2^19 amplitudes on chip (2^17 in registers, 3 * 2^17 in shared
- *       memory: half of an n = 20 state) and the rest in its slot of the
- *       workspace (16 slots of 2^n * 8 bytes), which stays in L2 while the
- *       items in flight fit there (n = 20: 4 MiB touched per item, at most
- *       16 items); n in GQAOA_SWEEP_L2_MIN_N..GQAOA_SWEEP_L2_MAX_N;
+ *       557056 amplitudes on chip (163840 in registers, 393216 in shared
+ *       memory: 53 % of an n = 20 state) and streams the rest through its
+ *       slot of the workspace (16 slots of 2^n * 8 bytes), which stays in L2
+ *       while the items in flight fit there (n = 20: 3.75 MiB touched per
+ *       item, at most 16 items); n in GQAOA_SWEEP_L2_MIN_N..
+ *       GQAOA_SWEEP_L2_MAX_N;
  *   0   16 for n <= 18, 32 for n = 19, GQAOA_SWEEP_L2 for n >= 20.
  *   Other values: GQAOA_EINVAL; n outside the selected range: GQAOA_ERANGE.
  * Precision: complex64 state; the mixer sum is FP32 within a warp
@@ -244,7 +245,7 @@ int gqaoa_grad_batched(const uint8_t *cost, int64_t cost_stride, int n, int m, i
 #define GQAOA_SWEEP_MIN_N 9
 #define GQAOA_SWEEP_MAX_N 19
 #define GQAOA_SWEEP_L2 1
-#define GQAOA_SWEEP_L2_MIN_N 17
+#define GQAOA_SWEEP_L2_MIN_N 20
 #define GQAOA_SWEEP_L2_MAX_N 24
 int gqaoa_sweep_workspace_size(int n, int angles, int amps_per_thread, size_t *bytes);
 int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const double *gammas,

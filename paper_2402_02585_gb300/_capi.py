@@ -28,7 +28,7 @@ GQAOA_MAX_M = 255
 GQAOA_SWEEP_MIN_N = 9
 GQAOA_SWEEP_MAX_N = 19
 GQAOA_SWEEP_L2 = 1
-GQAOA_SWEEP_L2_MIN_N = 17
+GQAOA_SWEEP_L2_MIN_N = 20
 GQAOA_SWEEP_L2_MAX_N = 24
 
 

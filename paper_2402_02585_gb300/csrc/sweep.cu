@@ -249,39 +249,47 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
 
 // ---------------------------------------------------------------------------
 // Cluster-resident sweep: states too large for a cluster's registers and
-// shared memory (n >= 17 here; n = 20 is the case that matters). One item per
-// 16-CTA cluster of 512-thread CTAs, one CTA per SM. CTA r owns the r-th
-// sixteenth of the state; thread t owns the float4 (two amplitudes)
-// r N/32 + j 512 + t for j = 0..V-1, so every warp access is 512 contiguous
-// bytes. Of a thread's V float4 the first kL2RegVec stay in registers and
-// the next (up to) kL2SmemVec in shared memory for the whole evolution; the
-// rest live in the cluster's slot of the workspace and stream through a
-// small register ring, interleaved with the shared-memory part so the SM's
-// L2 port stays busy all round. Each thread rereads only what it wrote, so
-// the slot needs no synchronisation beyond program order. At most kL2Slots
-// items are in flight (one per resident cluster, seven on GB300), whose
-// slots total 28 MiB at n = 20 (half the state is on chip): the
-// per-round read-modify-write of them
-// is served by the 129 MB L2, whose read-modify-write bandwidth is about
-// twice that of HBM (and per SM about 95 GB/s, whatever the loads in
-// flight, which is why the on-chip share matters).
+// shared memory (n >= 20). One item per 16-CTA cluster of 512-thread CTAs,
+// one CTA per SM; CTA r owns the r-th sixteenth of the state (Q float4, two
+// amplitudes each). The CTA's warps split into two roles that run side by
+// side, so the SM's L2 port and its ALUs are busy at the same time:
+//  * on-chip warps (8): thread u holds the float4 j 256 + u of the sixteenth
+//    for j < kL2RegVec in registers and for kL2RegVec <= j < kL2OnChip in
+//    shared memory, for the whole evolution (17408 float4 per CTA, 53 % of an
+//    n = 20 state);
+//  * streaming warps (8): thread u owns the float4 kL2OnChip 256 + j 256 + u
+//    for the rest of the sixteenth; they live in the cluster's slot of the
+//    workspace and stream through a ring of kL2RegVec / kL2Batch register
+//    batches (the same registers that hold state in the on-chip warps).
+// Every warp access is 512 contiguous bytes, and each thread rereads only
+// what it wrote, so the slot needs no synchronisation beyond program order.
+// At most kL2Slots items are in flight (one per resident cluster, seven on
+// GB300), whose slots total 27 MiB at n = 20: the per-round
+// read-modify-write of them is served by the 129 MB L2, whose
+// read-modify-write bandwidth is about twice that of HBM (and per SM about
+// 95 GB/s, whatever the loads in flight, which is why the on-chip share
+// matters).
 //
 // The mixer sum: FP32 over at most 8 amplitudes, double-float per thread,
-// FP32 across a warp's lanes (butterfly), double-float per CTA (warp 0). Warp 0 then pushes its CTA's
-// partial into the shared memory of every CTA of the cluster (lane r stores
-// to CTA r), one cluster barrier (release/acquire) makes the kL2Cluster
-// partials visible locally, and every warp sums them in rank order, so all
-// warps of all CTAs hold the same a_k bit for bit with no further barrier.
+// FP32 across a warp's lanes (butterfly), double-float per CTA (warp 0).
+// Warp 0 then pushes its CTA's partial into the shared memory of every CTA
+// of the cluster (lane r stores to CTA r), one cluster barrier
+// (release/acquire) makes the kL2Cluster partials visible locally, and
+// every warp sums them in rank order, so all warps of all CTAs hold the
+// same a_k bit for bit with no further barrier.
 // ---------------------------------------------------------------------------
 constexpr int kL2Threads = 512;
 constexpr int kL2Warps = kL2Threads / 32;
+constexpr int kL2RoleThreads = kL2Threads / 2;  // threads per role
 constexpr int kL2Cluster = 16;
 constexpr int kL2Slots = 16;
-constexpr int kL2RegVec = 8;    // float4 per thread held in registers
-constexpr int kL2SmemVec = 24;  // float4 per thread held in shared memory (at most)
-constexpr int kL2Batch = 2;     // float4 per thread per global batch
-constexpr int kL2Depth = 2;     // batches in the register ring
-constexpr size_t kL2DynSmem = (size_t)kL2SmemVec * kL2Threads * (sizeof(float4) + sizeof(uint16_t));
+constexpr int kL2RegVec = 20;   // float4 per on-chip thread held in registers
+constexpr int kL2SmemVec = 48;  // float4 per on-chip thread held in shared memory
+constexpr int kL2OnChip = kL2RegVec + kL2SmemVec;
+constexpr int kL2Batch = 2;     // float4 per streaming batch
+constexpr int kL2Ring = kL2RegVec / kL2Batch;  // batches in a streaming thread's ring
+constexpr size_t kL2DynSmem =
+    (size_t)kL2SmemVec * kL2RoleThreads * (sizeof(float4) + sizeof(uint16_t));
 
 __device__ __forceinline__ void st_dsmem_f32x2(float2 *p, unsigned rank, float2 v) {
   uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -324,86 +332,85 @@ __device__ __forceinline__ void l2_fold(float (&v)[kSlots], DF (&acc)[kSlots]) {
     }
 }
 
-// One round over a thread's V = kL2RegVec + S + kL2Batch G float4: the
-// global batches (each followed by a shared-memory pair while any remain),
-// the rest of shared memory, then the registers.
+// A streaming thread's round: nb batches of kL2Batch float4 from its slot
+// (gp: its first float4; gc: their cost bytes), kL2Ring - 1 batches ahead.
 template <bool kExtra>
-__device__ __forceinline__ void l2_round(float4 (&xr)[kL2RegVec],
-                                         const uint32_t (&cr)[kL2RegVec / 2], float4 *s_state,
-                                         const uint16_t *s_cost, float4 *gbase,
-                                         const uint16_t *gcost, int S, int G, const float2 *s_T,
-                                         float2 ad, float amp0, DF (&acc)[kSlots], bool ro,
-                                         bool first) {
-  constexpr int T = kL2Threads;
-  const int t = threadIdx.x;
+__device__ __forceinline__ void l2_stream_round(float4 (&ring)[kL2RegVec],
+                                                uint32_t (&cring)[kL2Ring], float4 *gp,
+                                                const uint16_t *gc, int nb, const float2 *s_T,
+                                                float2 ad, float amp0, DF (&acc)[kSlots],
+                                                bool ro, bool first) {
+  constexpr int T = kL2RoleThreads;
+  constexpr int kStep = kL2Batch * T;
   const float4 plus = make_float4(amp0, 0.f, amp0, 0.f);
-  // walking pointers (next batch to load, next to store): every access is a
-  // base plus an immediate offset
-  const float4 *lp = gbase;
-  const uint16_t *lc = gcost;
-  float4 *sp = gbase;
+  const float4 *lp = gp;  // next batch to load
+  const uint16_t *lc = gc;
+  float4 *sp = gp;        // next batch to store
   float v[kSlots] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  float4 x[kL2Depth][kL2Batch];
-  uint32_t c[kL2Depth][kL2Batch];
-  auto load = [&](float4 (&xx)[kL2Batch], uint32_t (&cc)[kL2Batch]) {
+  auto load = [&](int slot) {
+    cring[slot] = (uint32_t)lc[0] | ((uint32_t)lc[T] << 16);
 #pragma unroll
-    for (int k = 0; k < kL2Batch; ++k) cc[k] = lc[k * T];
-#pragma unroll
-    for (int k = 0; k < kL2Batch; ++k) xx[k] = first ? plus : __ldcg(lp + k * T);
-    lp += kL2Batch * T;
-    lc += kL2Batch * T;
-  };
-  auto smem_pair = [&](int j) {
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      float4 y = first ? plus : s_state[(j + k) * T + t];
-      l2_vec<kExtra>(y, s_cost[(j + k) * T + t], s_T, ad, v, ro, first);
-      s_state[(j + k) * T + t] = y;
-    }
+    for (int k = 0; k < kL2Batch; ++k)
+      ring[slot * kL2Batch + k] = first ? plus : __ldcg(lp + k * T);
+    lp += kStep;
+    lc += kStep;
   };
 #pragma unroll
-  for (int d = 0; d + 1 < kL2Depth; ++d)
-    if (d < G) load(x[d], c[d]);
-  // global batches, each followed by a shared-memory pair while any remain
-  int js = 0;
+  for (int d = 0; d + 1 < kL2Ring; ++d)
+    if (d < nb) load(d);
 #pragma unroll 1
-  for (int g0 = 0; g0 < G; g0 += kL2Depth) {
+  for (int g0 = 0; g0 < nb; g0 += kL2Ring) {
 #pragma unroll
-    for (int d = 0; d < kL2Depth; ++d) {
+    for (int d = 0; d < kL2Ring; ++d) {
       const int g = g0 + d;
-      if (g < G) {
-        constexpr int kAhead = kL2Depth - 1;
-        const int slot = (d + kAhead) % kL2Depth;  // freed by batch g - 1
-        if (g + kAhead < G) load(x[slot], c[slot]);
+      if (g < nb) {
+        constexpr int kAhead = kL2Ring - 1;
+        if (g + kAhead < nb) load((d + kAhead) % kL2Ring);  // the slot batch g - 1 freed
 #pragma unroll
-        for (int k = 0; k < kL2Batch; ++k) l2_vec<kExtra>(x[d][k], c[d][k], s_T, ad, v, ro, first);
+        for (int k = 0; k < kL2Batch; ++k)
+          l2_vec<kExtra>(ring[d * kL2Batch + k], cring[d] >> (16 * k), s_T, ad, v, ro, first);
 #pragma unroll
-        for (int k = 0; k < kL2Batch; ++k) __stcg(sp + k * T, x[d][k]);
-        sp += kL2Batch * T;
-        if (js < S) {
-          smem_pair(js);
-          js += 2;
-        }
-        l2_fold<kExtra>(v, acc);
+        for (int k = 0; k < kL2Batch; ++k) __stcg(sp + k * T, ring[d * kL2Batch + k]);
+        sp += kStep;
+        if (d & 1) l2_fold<kExtra>(v, acc);
       }
     }
   }
-#pragma unroll 1
-  for (; js < S; js += 2) {
-    smem_pair(js);
-    l2_fold<kExtra>(v, acc);
-  }
-  // registers last: the final global stores complete meanwhile
+  l2_fold<kExtra>(v, acc);
+}
+
+// An on-chip thread's round: its kL2RegVec register float4, then its
+// kL2SmemVec shared-memory float4 ([j][thread] layout: conflict-free).
+template <bool kExtra>
+__device__ __forceinline__ void l2_onchip_round(float4 (&xr)[kL2RegVec],
+                                                const uint32_t (&cr)[kL2Ring], float4 *s_state,
+                                                const uint16_t *s_cost, int u, const float2 *s_T,
+                                                float2 ad, float amp0, DF (&acc)[kSlots],
+                                                bool ro, bool first) {
+  constexpr int T = kL2RoleThreads;
+  const float4 plus = make_float4(amp0, 0.f, amp0, 0.f);
+  float v[kSlots] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < kL2RegVec; ++k) {
     if (first) xr[k] = plus;
     l2_vec<kExtra>(xr[k], cr[k >> 1] >> (16 * (k & 1)), s_T, ad, v, ro, first);
     if ((k & 3) == 3) l2_fold<kExtra>(v, acc);
   }
+#pragma unroll 1
+  for (int j0 = 0; j0 < kL2SmemVec; j0 += 4) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float4 y = first ? plus : s_state[(j0 + k) * T + u];
+      l2_vec<kExtra>(y, s_cost[(j0 + k) * T + u], s_T, ad, v, ro, first);
+      s_state[(j0 + k) * T + u] = y;
+    }
+    l2_fold<kExtra>(v, acc);
+  }
+  l2_fold<kExtra>(v, acc);
 }
 
 __global__ void __launch_bounds__(kL2Threads, 1) sweep_l2_kernel(const __grid_constant__ SweepArgs a) {
-  constexpr int T = kL2Threads;
+  constexpr int T = kL2RoleThreads;
   extern __shared__ __align__(16) unsigned char s_dyn[];
   float4 *s_state = reinterpret_cast<float4 *>(s_dyn);  // [kL2SmemVec][T]
   uint16_t *s_cost =
@@ -412,33 +419,36 @@ __global__ void __launch_bounds__(kL2Threads, 1) sweep_l2_kernel(const __grid_co
   __shared__ float2 s_wp[2][kL2Warps][kSlots];    // warp partials (double-float)
   __shared__ float2 s_ps[2][kL2Cluster][kSlots];  // CTA partials, pushed by every CTA
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool streaming = threadIdx.x < T;          // warps 0..7 stream, 8..15 stay on chip
+  const int u = streaming ? threadIdx.x : threadIdx.x - T;
   const unsigned rank = cluster_ctarank();
   const uint64_t cluster_id = blockIdx.x / kL2Cluster, nclusters = gridDim.x / kL2Cluster;
   const uint64_t N = 1ull << a.n, Nv = N / 2;
-  const int V = (int)(Nv / ((uint64_t)kL2Cluster * T));  // float4 per thread (>= 8)
-  const int S = V - kL2RegVec < kL2SmemVec ? V - kL2RegVec : kL2SmemVec;
-  const int G = (V - kL2RegVec - S) / kL2Batch;
+  const uint64_t Q = Nv / kL2Cluster;                         // float4 per CTA
+  const int nb = (int)(Q / T - kL2OnChip) / kL2Batch;         // streaming batches per thread
   const float inv_n = (float)(1.0 / (double)N);
   const float amp0 = (float)(1.0 / sqrt((double)N));
-  const uint64_t seg0 = (uint64_t)rank * (Nv / kL2Cluster);
-  float4 *gbase = a.scratch + cluster_id * Nv + seg0 + (uint64_t)(kL2RegVec + S) * T + threadIdx.x;
+  const uint64_t seg0 = (uint64_t)rank * Q;
+  float4 *gp = a.scratch + cluster_id * Nv + seg0 + (uint64_t)kL2OnChip * T + u;
   int buf = 0;
 
   for (uint64_t item = cluster_id; item < a.nitems; item += nclusters) {
     const uint64_t b = item / (uint64_t)a.A;
     const int ai = (int)(item % (uint64_t)a.A);
-    const uint16_t *cseg = reinterpret_cast<const uint16_t *>(a.cost + b * N) + seg0 + threadIdx.x;
-    uint32_t cr[kL2RegVec / 2];
+    const uint16_t *cseg = reinterpret_cast<const uint16_t *>(a.cost + b * N) + seg0 + u;
+    const uint16_t *gc = cseg + kL2OnChip * T;
+    float4 xr[kL2RegVec];   // on-chip: state; streaming: the load ring
+    uint32_t cr[kL2Ring];   // on-chip: cost pairs of xr; streaming: the ring's
+    if (!streaming) {
 #pragma unroll
-    for (int k = 0; k < kL2RegVec / 2; ++k)
-      cr[k] = (uint32_t)cseg[(2 * k) * T] | ((uint32_t)cseg[(2 * k + 1) * T] << 16);
-    for (int j = 0; j < S; ++j) s_cost[j * T + threadIdx.x] = cseg[(kL2RegVec + j) * T];
-    const uint16_t *gcost = cseg + (kL2RegVec + S) * T;
-    for (int i = threadIdx.x; i < 256; i += T) s_T[i] = a.phase[(size_t)ai * 256 + i];
+      for (int k = 0; k < kL2Ring; ++k)
+        cr[k] = (uint32_t)cseg[(2 * k) * T] | ((uint32_t)cseg[(2 * k + 1) * T] << 16);
+      for (int j = 0; j < kL2SmemVec; ++j) s_cost[j * T + u] = cseg[(kL2RegVec + j) * T];
+    }
+    for (int i = threadIdx.x; i < 256; i += kL2Threads) s_T[i] = a.phase[(size_t)ai * 256 + i];
     const double2 ald = a.alpha[ai];
     const float alr = (float)ald.x, ali = (float)ald.y;
     __syncthreads();
-    float4 xr[kL2RegVec];
     float2 ad = make_float2(0.f, 0.f);  // pending mixer add
     float cnt0 = 0.f;                   // C = 0 count of the instance
     int ridx = 0;
@@ -450,11 +460,17 @@ __global__ void __launch_bounds__(kL2Threads, 1) sweep_l2_kernel(const __grid_co
       DF acc[kSlots];
 #pragma unroll
       for (int k = 0; k < kSlots; ++k) acc[k].zero();
-      if (extra)
-        l2_round<true>(xr, cr, s_state, s_cost, gbase, gcost, S, G, s_T, ad, amp0, acc, ro, first);
-      else
-        l2_round<false>(xr, cr, s_state, s_cost, gbase, gcost, S, G, s_T, ad, amp0, acc, false,
-                        false);
+      if (streaming) {
+        if (extra)
+          l2_stream_round<true>(xr, cr, gp, gc, nb, s_T, ad, amp0, acc, ro, first);
+        else
+          l2_stream_round<false>(xr, cr, gp, gc, nb, s_T, ad, amp0, acc, false, false);
+      } else {
+        if (extra)
+          l2_onchip_round<true>(xr, cr, s_state, s_cost, u, s_T, ad, amp0, acc, ro, first);
+        else
+          l2_onchip_round<false>(xr, cr, s_state, s_cost, u, s_T, ad, amp0, acc, false, false);
+      }
       float hi[kSlots], lo[kSlots];
 #pragma unroll
       for (int k = 0; k < kSlots; ++k) {

@@ -7,9 +7,10 @@ chooses for its n:
     (instance, angle point) holding the state on chip (9 <= n <= 19), with
     16 amplitudes per thread in registers ("apt": 16) or 16 more in shared
     memory ("apt": 32);
-  * "l2": gqaoa_sweep's cluster-resident path (17 <= n <= 24): one 16-CTA
-    cluster per item keeps part of the state in shared memory and the rest in
-    a workspace slot that stays in L2 while the few items in flight fit there;
+  * "l2": gqaoa_sweep's cluster-resident path (20 <= n <= 24): one 16-CTA
+    cluster per item keeps part of the state in registers and shared memory
+    and streams the rest through a workspace slot that stays in L2 while the
+    few items in flight fit there;
   * "stream": gqaoa_evolve_batched with the instance's cost table shared by a
     chunk of angle points and a per-round trace of P(C=0).
 Every buffer and workspace is allocated when the plan is built. The

@@ -6,7 +6,7 @@ JSON table that SweepPlan loads.
 
 Candidates: the on-chip sweep with 16 amplitudes per thread in registers
 (9 <= n <= 18) or 16 more in shared memory (10 <= n <= 19), the
-cluster-resident sweep with L2-resident workspace slots (17 <= n <= 24), and
+cluster-resident sweep with L2-resident workspace slots (20 <= n <= 24), and
 the streaming path with chunks of 16..256 angle points sharing the instance's
 cost table. The score is
 amplitude-rounds per second on a small synthetic bucket of the workload's

@@ -124,7 +124,7 @@ def test_sweep_workspace_sizes():
     resident = C.gqaoa_sweep_workspace_size(20, 4, C.GQAOA_SWEEP_L2)
     assert resident == small + 16 * 8 * (1 << 20)       # 16 slots of 2^20 complex64
     assert C.gqaoa_sweep_workspace_size(20, 4, 0) == resident
-    for n, apt in ((20, 16), (20, 32), (25, 0), (16, C.GQAOA_SWEEP_L2)):
+    for n, apt in ((20, 16), (20, 32), (25, 0), (19, C.GQAOA_SWEEP_L2)):
         with pytest.raises(C.GQAOAError) as e:
             C.gqaoa_sweep_workspace_size(n, 4, apt)
         assert e.value.status == C.GQAOA_ERANGE
@@ -147,8 +147,8 @@ def test_sweep_rejects_bad_arguments_before_launch():
     with pytest.raises(C.GQAOAError) as e:
         C.gqaoa_sweep(fake, 25, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, 0, fake, fake, 1 << 20, None)
     assert e.value.status == C.GQAOA_ERANGE
-    with pytest.raises(C.GQAOAError) as e:  # the cluster-resident path starts at n = 17
-        C.gqaoa_sweep(fake, 16, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, C.GQAOA_SWEEP_L2, fake,
+    with pytest.raises(C.GQAOAError) as e:  # the cluster-resident path starts at n = 20
+        C.gqaoa_sweep(fake, 19, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, C.GQAOA_SWEEP_L2, fake,
                       fake, 1 << 30, None)
     assert e.value.status == C.GQAOA_ERANGE
     with pytest.raises(C.GQAOAError) as e:  # 16 slots of 2^20 amplitudes do not fit in 1 MiB

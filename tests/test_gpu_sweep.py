@@ -6,9 +6,9 @@ small n, the exact cost-class model (pinned against it) at larger n. The
 on-chip cases cover one warp per item (n = 9), whole CTAs (n = 12..14),
 clusters of 2, 4, 8 and 16 CTAs (n = 15..18), a 16-CTA cluster with half the
 state in shared memory (n = 19), and more items than resident CTAs. The
-cluster-resident path (GQAOA_SWEEP_L2) covers states held entirely in shared
-memory (n = 17, 18), split between shared memory and the workspace
-(n = 19..22), and more items than resident clusters.
+cluster-resident path (GQAOA_SWEEP_L2) covers n = 20..22 (53 % of an n = 20
+state on chip, the rest streamed through the workspace) and more items than
+resident clusters.
 """
 
 import math
@@ -79,10 +79,8 @@ def test_sweep_matches_oracle(n, B, A, p, rounds, apt):
 
 
 @pytest.mark.parametrize("n,B,A,p,rounds", [
-    (17, 2, 13, 6, [1, 6]),      # 26 items: more than the resident clusters
-    (18, 1, 2, 5, [2, 5]),
-    (19, 1, 3, 8, [1, 4, 8]),    # 3/4 of the state in shared memory
-    (20, 2, 3, 10, [1, 5, 10]),  # 3/8 in shared memory, the rest in the workspace
+    (20, 2, 3, 10, [1, 5, 10]),
+    (20, 1, 15, 6, [1, 6]),      # 15 items: more than the resident clusters
     (21, 1, 2, 6, [6]),
     (22, 1, 2, 4, [1, 4]),
 ])
@@ -106,17 +104,20 @@ def test_sweep_cluster_resident_matches_oracle(n, B, A, p, rounds):
             assert np.max(np.abs(got[i, a] - ref)) < 1e-6, (n, i, a, got[i, a], ref)
 
 
-def test_sweep_cluster_resident_agrees_with_on_chip():
-    # n = 19 runs on both paths: same P within the tolerance, items of two instances
-    n, p, rounds = 19, 12, [1, 6, 12]
+def test_sweep_cluster_resident_agrees_with_streaming():
+    # n = 20 on the cluster-resident sweep and on batched streaming evolution
+    # (independent kernels): the same P within the tolerance
+    n, p, rounds = 20, 12, [1, 6, 12]
     m = int(math.floor(4.2 * n + 0.5))
-    costs = torch.stack([core.build_cost(instances.random_3sat(n, m, 1900 + i), n)[0]
-                         for i in range(2)])
-    rng = np.random.default_rng(19)
-    G = rng.uniform(0, np.pi, 20)
-    Bt = rng.uniform(0, np.pi, 20)
-    a = run_sweep(costs, n, m, G, Bt, p, rounds, 32)
-    b = run_sweep(costs, n, m, G, Bt, p, rounds, C.GQAOA_SWEEP_L2)
+    cost = core.build_cost(instances.random_3sat(n, m, 1900), n)[0]
+    rng = np.random.default_rng(20)
+    G = rng.uniform(0, np.pi, 9)
+    Bt = rng.uniform(0, np.pi, 9)
+    a = run_sweep(cost[None], n, m, G, Bt, p, rounds, C.GQAOA_SWEEP_L2)[0]
+    gd = torch.as_tensor(np.repeat(G[:, None], p, 1), device="cuda")
+    bd = torch.as_tensor(np.repeat(Bt[:, None], p, 1), device="cuda")
+    _, _, trace = core.evolve_batched(cost, n, m, gd, bd, shared_cost=True, trace=True)
+    b = trace.cpu().numpy()[:, np.asarray(rounds) - 1]
     assert np.max(np.abs(a - b)) < 1e-6
 
 
