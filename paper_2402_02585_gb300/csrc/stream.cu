@@ -80,13 +80,14 @@ struct Geometry {
   bool small;       // N < one tile: one CTA per instance, everything on chip
 };
 
-// One wave is `per_sm` CTAs of 256 threads per SM: 2 for the forward and
-// readout passes (each thread keeps two tiles in flight, ~116 registers) and
-// 4 for the adjoint passes (one tile, <= 64 registers). A single instance gets
+// One wave is `per_sm` CTAs of 256 threads per SM: 2 for every streaming
+// pass (each thread keeps a tile, or for the adjoint a half-tile of lambda
+// and of chi, in flight while it processes the previous one; <= 128
+// registers). A single instance gets
 // one wave in clusters of 4; a batch gets about two waves split evenly over
 // instances, each CTA owning whole tiles of one instance.
 constexpr int kFwdPerSm = 2;
-constexpr int kBwdPerSm = 4;
+constexpr int kBwdPerSm = 2;
 
 // CTAs of one full wave of a clustered streaming pass: the number of clusters
 // of kClusterSize the device keeps resident at once (clusters are placed
@@ -185,22 +186,35 @@ static size_t ws_layout(const Geometry &g, int p, bool grad, char *base, Ws *w,
 // ---------------------------------------------------------------------------
 // K10: phase tables and mixer coefficients, FP64 sincos rounded to complex64
 // ---------------------------------------------------------------------------
-__global__ void phase_table_kernel(const double *__restrict__ gammas,
-                                   const double *__restrict__ betas, int64_t bp,
-                                   float2 *__restrict__ phase, double2 *__restrict__ alpha) {
-  const int64_t total = bp * 256;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = i >> 8;
-    const int c = (int)(i & 255);
-    double s, co;
-    sincos(gammas[k] * (double)c, &s, &co);
-    phase[i] = make_float2((float)co, (float)(-s));
-    if (c == 0) {
-      double sb, cb;
-      sincos(betas[k], &sb, &cb);
-      alpha[k] = make_double2(cb - 1.0, -sb);
+__global__ void __launch_bounds__(kThreads) phase_table_kernel(const double *__restrict__ gammas,
+                                                               const double *__restrict__ betas,
+                                                               int64_t bp, float2 *__restrict__ phase,
+                                                               double2 *__restrict__ alpha) {
+  // One table per CTA at a time: 32 FP64 sincos give e^{-i gamma r} and
+  // e^{-i gamma 16 q} (r, q = 0..15), and T[16 q + r] is their FP64 product
+  // rounded to FP32. The product is within a few FP64 ulps of the directly
+  // evaluated exponential, far below the FP32 rounding of the table, and it
+  // costs 8x fewer sincos (FP64 is a small fraction of GB300's FP32 rate).
+  __shared__ double2 s_e[32];  // [0, 16): e^{-i gamma r}; [16, 32): e^{-i gamma 16 q}
+  for (int64_t k = blockIdx.x; k < bp; k += gridDim.x) {
+    if (threadIdx.x < 32) {
+      const int j = threadIdx.x;
+      const double c = j < 16 ? (double)j : 16.0 * (double)(j - 16);
+      double s, co;
+      sincos(gammas[k] * c, &s, &co);
+      s_e[j] = make_double2(co, -s);
+      if (j == 0) {
+        double sb, cb;
+        sincos(betas[k], &sb, &cb);
+        alpha[k] = make_double2(cb - 1.0, -sb);
+      }
     }
+    __syncthreads();
+    const int c = threadIdx.x;
+    const double2 e1 = s_e[c & 15], e16 = s_e[16 + (c >> 4)];
+    phase[k * 256 + c] = make_float2((float)(e16.x * e1.x - e16.y * e1.y),
+                                     (float)(e16.x * e1.y + e16.y * e1.x));
+    __syncthreads();  // s_e is rewritten for the next table
   }
 }
 
@@ -495,6 +509,15 @@ __global__ void finalize_readout_kernel(const double *__restrict__ parts, int np
   }
 }
 
+// A thread's share of half a tile of an adjoint pass: 4 float4 of lambda,
+// 4 of the checkpoint chi, and their costs.
+constexpr int kHalfVec = kVecPerThread / 2;
+struct HalfRegs {
+  float4 l[kHalfVec];
+  float4 x[kHalfVec];
+  uint16_t c2[kHalfVec];
+};
+
 // ---------------------------------------------------------------------------
 // K6: adjoint. lambda_p = O psi_p, psi_p = chi_p + a_p (chi_p = checkpoint).
 // Records: 0,1 = Lambda_p; 2 = L = sum O |psi_p|^2.
@@ -528,13 +551,26 @@ __global__ void __launch_bounds__(kThreads, kBwdPerSm) lambda_init_kernel(const 
       reinterpret_cast<const uint16_t *>(a.cost + (size_t)b * a.cost_bstride);
   const float4 *__restrict__ src = a.src + (size_t)b * (a.N / 2);
   float4 *dst = a.dst + (size_t)b * (a.N / 2);
-  for (uint64_t t = local; t < a.ntiles; t += a.cpi) {
-    const uint64_t vb = tile_vbase(t, warp, lane);
+  // against the last forward pass's direction: its tail is still in L2
+  const bool reverse = ((a.round + 1) & 1) != 0;
+  auto vbase = [&](uint64_t t) {
+    return tile_vbase(reverse ? (a.ntiles - 1 - t) : t, warp, lane);
+  };
+  auto load = [&](TileRegs &T, uint64_t t) {
+    const uint64_t vb = vbase(t);
+#pragma unroll
+    for (int j = 0; j < kVecPerThread; ++j) {
+      T.c2[j] = cost2[vb + 32 * j];
+      T.v[j] = src[vb + 32 * j];
+    }
+  };
+  auto proc = [&](TileRegs &T, uint64_t t) {
+    const uint64_t vb = vbase(t);
     float tlr = 0.f, tli = 0.f, tL = 0.f;
 #pragma unroll
     for (int j = 0; j < kVecPerThread; ++j) {
-      const uint16_t c2 = cost2[vb + 32 * j];
-      const float4 v = src[vb + 32 * j];
+      const uint16_t c2 = T.c2[j];
+      const float4 v = T.v[j];
       const float o0 = kObj == GQAOA_OBJ_P0 ? ((c2 & 0xFFu) == 0 ? 1.f : 0.f) : (float)(c2 & 0xFFu);
       const float o1 = kObj == GQAOA_OBJ_P0 ? ((c2 >> 8) == 0 ? 1.f : 0.f) : (float)(c2 >> 8);
       const float2 p0 = make_float2(v.x + ad.x, v.y + ad.y);
@@ -548,7 +584,8 @@ __global__ void __launch_bounds__(kThreads, kBwdPerSm) lambda_init_kernel(const 
     acc[0].add(tlr);
     acc[1].add(tli);
     acc[2].add(tL);
-  }
+  };
+  pipelined_tiles(local, a.cpi, a.ntiles, load, proc);
   reduce_to_record<3>(a, b, local, acc, s_w, s_vals);
 }
 
@@ -596,15 +633,34 @@ backward_kernel(const PassArgs a, const float4 *__restrict__ chi_base) {
   const float4 *__restrict__ lam = a.src + (size_t)b * (a.N / 2);
   const float4 *__restrict__ chi = chi_base + (size_t)b * (a.N / 2);
   float4 *dst = a.dst + (size_t)b * (a.N / 2);
-  for (uint64_t t = local; t < a.ntiles; t += a.cpi) {
-    const uint64_t vb = tile_vbase(t, warp, lane);
+  // Half-tile units (4 float4 of lambda and of chi per thread), two in
+  // flight: the loads of the next unit are issued before the current one is
+  // processed. Alternate direction per pass: the previous pass's tail of
+  // lambda is still in L2.
+  const bool reverse = (a.round & 1) != 0;
+  const uint64_t mine = a.ntiles > (uint64_t)local ? (a.ntiles - 1 - local) / a.cpi + 1 : 0;
+  const uint64_t nu = 2 * mine;
+  auto vbase = [&](uint64_t u) {
+    const uint64_t t = local + (u >> 1) * a.cpi;
+    return tile_vbase(reverse ? (a.ntiles - 1 - t) : t, warp, lane) +
+           (u & 1) * (32 * kHalfVec);
+  };
+  auto load = [&](HalfRegs &H, uint64_t u) {
+    const uint64_t vb = vbase(u);
+#pragma unroll
+    for (int j = 0; j < kHalfVec; ++j) H.c2[j] = cost2[vb + 32 * j];
+#pragma unroll
+    for (int j = 0; j < kHalfVec; ++j) H.l[j] = lam[vb + 32 * j];
+#pragma unroll
+    for (int j = 0; j < kHalfVec; ++j) H.x[j] = chi[vb + 32 * j];
+  };
+  auto proc = [&](HalfRegs &H, uint64_t u) {
+    const uint64_t vb = vbase(u);
     float tg = 0.f, tlr = 0.f, tli = 0.f;
 #pragma unroll
-    for (int j = 0; j < kVecPerThread; ++j) {
-      const uint16_t c2 = cost2[vb + 32 * j];
-      const float4 l = lam[vb + 32 * j];
-      const float4 x = chi[vb + 32 * j];
-      const unsigned c_0 = c2 & 0xFFu, c_1 = c2 >> 8;
+    for (int j = 0; j < kHalfVec; ++j) {
+      const float4 l = H.l[j], x = H.x[j];
+      const unsigned c_0 = H.c2[j] & 0xFFu, c_1 = H.c2[j] >> 8;
       const float2 m0 = make_float2(l.x + bd.x, l.y + bd.y);
       const float2 m1 = make_float2(l.z + bd.x, l.w + bd.y);
       // Im(conj(mu) chi) = mu.re chi.im - mu.im chi.re
@@ -622,6 +678,17 @@ backward_kernel(const PassArgs a, const float4 *__restrict__ chi_base) {
     acc[0].add(tlr);
     acc[1].add(tli);
     acc[2].add(tg);
+  };
+  HalfRegs A, Bh;
+  uint64_t u = 0;
+  if (u < nu) load(A, u);
+  for (; u < nu; u += 2) {
+    if (u + 1 < nu) load(Bh, u + 1);
+    proc(A, u);
+    if (u + 1 < nu) {
+      if (u + 2 < nu) load(A, u + 2);
+      proc(Bh, u + 1);
+    }
   }
   reduce_to_record<3>(a, b, local, acc, s_w, s_vals);
 }
@@ -895,9 +962,7 @@ static double *parts_half(const Ws &w, int i) { return w.parts + (size_t)(i & 1)
 // `count` angle pairs (also used by the on-chip sweep).
 int phase_tables(const double *gammas, const double *betas, int64_t count, float2 *phase,
                  double2 *alpha, cudaStream_t st) {
-  const int64_t total = count * 256;
-  int64_t grid = (total + kThreads - 1) / kThreads;
-  if (grid > 4096) grid = 4096;
+  int64_t grid = count < 4096 ? count : 4096;
   phase_table_kernel<<<(unsigned)grid, kThreads, 0, st>>>(gammas, betas, count, phase, alpha);
   GQ_CHECK_LAUNCH();
   return GQAOA_OK;
