@@ -51,6 +51,11 @@ WORKLOADS = {
     "grad": dict(kind="grad", n=16, m=67, p=32, batch=1024, seed=0, lr=0.05,
                  desc="1024 random 3-SAT instances n=16 m=67 (d~4.2), p=32 random angles; "
                       "one step = adjoint gradient of P(C=0) for all + one Adam update (lr 0.05)"),
+    # the gradient's profiling case: same recipe, 512 instances, p = 4 (256 MiB per
+    # state pass, 1 GiB of checkpoints: larger than L2, small enough for ncu)
+    "grad_profile": dict(kind="grad", n=16, m=67, p=4, batch=512, seed=0, lr=0.05,
+                         desc="512 random 3-SAT instances n=16 m=67 (d~4.2), p=4 random angles; "
+                              "one step = adjoint gradient of P(C=0) for all + one Adam update"),
     # the profiling case: same recipe, state (512 MiB) still far larger than L2
     "profile": dict(n=26, m=109, p=8, shots=100_000, seed=0,
                     desc="random 3-SAT n=26 m=109 (d~4.2) seed 0, p=8 random angles, 1e5 shots"),
@@ -427,7 +432,8 @@ def run_ours(args, wl):
             "data": "synthetic",
             "config": {"workload": wl["desc"], "n": n, "m": m, "p": p, "shots": shots,
                        "parallelism": f"replicas x{world} (independent instances)",
-                       "l2": "inputs larger than L2 (2 GiB state, 256 MiB cost table)"
+                       "l2": f"inputs larger than L2 ({(8 << n) >> 20} MiB state, "
+                             f"{(1 << n) >> 20} MiB cost table)"
                        if n >= 26 else "small case: L2-resident"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -497,7 +503,8 @@ def run_grad(args, wl):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
             "data": "synthetic", "config": {"workload": wl["desc"], "n": n, "m": m, "p": p,
                                             "batch": B, "l2": "inputs larger than L2 "
-                                            "(512 MiB states, 16 GiB checkpoints)"},
+                                            f"({(B * N * 8) >> 20} MiB states, "
+                                            f"{(p * B * N * 8) >> 20} MiB checkpoints)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": kind,
                          "kernel": "forward rounds + backward rounds (mean over the step)"},
