@@ -55,6 +55,33 @@ def evolve(hist, gammas, betas, trace: bool = False):
     return (f, np.array(tr)) if trace else f
 
 
+def min_class(hist) -> int:
+    """The lowest cost value with a non-empty manifold: the number of clauses
+    a Max-SAT assignment leaves unsatisfied (0 for a satisfiable instance)."""
+    h = np.asarray(hist)
+    nz = np.nonzero(h)[0]
+    return int(nz[0])
+
+
+def readouts_trace(hist, gammas, betas):
+    """[p][3]: after every round k, P(C=0), <H_P> and D = sum over the lowest
+    non-empty class c* of |psi_k|^2 = h[c*] |f_k(c*)|^2 (the probability of
+    measuring a Max-SAT assignment; D = P when the instance is satisfiable)."""
+    h = np.asarray(hist, dtype=np.float64)
+    N = h.sum()
+    c = np.arange(h.shape[0], dtype=np.float64)
+    cs = min_class(hist)
+    f = np.full(h.shape[0], 1.0 / np.sqrt(N), dtype=np.complex128)
+    out = []
+    for g, b in zip(np.asarray(gammas, np.float64), np.asarray(betas, np.float64)):
+        gk = np.exp(-1j * g * c) * f
+        S = np.sum(h * gk)
+        f = gk + (np.exp(-1j * b) - 1.0) * S / N
+        w = h * np.abs(f) ** 2
+        out.append((w[0], np.sum(c * w), w[cs]))
+    return np.array(out).reshape(-1, 3)
+
+
 def readout(hist, f):
     """[P(C=0), <H_P>, norm] of the class-amplitude vector f."""
     h = np.asarray(hist, dtype=np.float64)

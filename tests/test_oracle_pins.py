@@ -249,6 +249,42 @@ def test_reduced_grad_matches_statevector_fd():
             assert abs((up - dn) / (2 * h) - ref[k]) < 1e-7
 
 
+def test_reduced_readouts_trace_matches_statevector_unsat():
+    # n = 7 at density 9: unsatisfiable, so the lowest class c* > 0 and
+    # D = sum over C(z) = c* of |psi|^2 is read off the statevector directly
+    n, m, p = 7, 63, 6
+    lits = instances.random_3sat(n, m, 21)
+    cost, hist = sv.cost_table(lits, n)
+    cs = reduced.min_class(hist)
+    assert cs > 0 and hist[cs] > 0 and np.all(np.asarray(hist)[:cs] == 0)
+    assert cs == int(np.min(cost))
+    g, b = instances.random_angles(p, 21)
+    tr = reduced.readouts_trace(hist, g, b)
+    for k in range(1, p + 1):
+        psi = sv.evolve(cost, n, g[:k], b[:k])
+        w = np.abs(psi) ** 2
+        assert abs(tr[k - 1, 0] - w[cost == 0].sum()) < 1e-14      # P = 0 here
+        assert abs(tr[k - 1, 1] - np.sum(cost * w)) < 1e-12
+        assert abs(tr[k - 1, 2] - w[cost == cs].sum()) < 1e-14
+
+
+def test_reduced_readouts_trace_satisfiable_and_gamma_zero():
+    n, m, p = 9, 38, 5
+    lits = instances.random_3sat(n, m, 21)   # satisfiable (4 solutions)
+    cost, hist = sv.cost_table(lits, n)
+    assert hist[0] > 0 and reduced.min_class(hist) == 0
+    g, b = instances.random_angles(p, 21)
+    tr = reduced.readouts_trace(hist, g, b)
+    assert np.array_equal(tr[:, 0], tr[:, 2])                        # D = P when satisfiable
+    _, trp = reduced.evolve(hist, g, b, trace=True)
+    assert np.max(np.abs(tr[:, 0] - trp)) < 1e-15
+    # gamma = 0: the phase is the identity and |+> is the mixer's fixed point,
+    # so <H_P> stays the mean cost, m / 8 for clauses over distinct variables
+    tr0 = reduced.readouts_trace(hist, np.zeros(p), b)
+    assert np.max(np.abs(tr0[:, 1] - m / 8)) < 1e-12
+    assert np.max(np.abs(tr0[:, 0] - hist[0] / 2 ** n)) < 1e-15
+
+
 def test_single_angle_gradient_is_sum_over_rounds():
     n, m, p = 9, 38, 7
     lits = instances.random_3sat(n, m, 13)
