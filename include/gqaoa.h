@@ -252,6 +252,43 @@ int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const double *gamm
                 const double *betas, int angles, int p, const int32_t *rounds, int nrounds,
                 int amps_per_thread, double *out, void *ws, size_t ws_bytes, void *stream);
 
+/*
+ * Cost-class (reduced) model of single-angle-pair G-QAOA (Appendix C): from
+ * |+> the state stays a function of the cost value, psi_k(z) = f_k(C(z)), so
+ * a round (Eq. 3) acts on the class amplitudes f(c), c < hist_stride,
+ * weighted by the manifold sizes h[c]. This is the paper's own simulation
+ * method and the fast path of its angle grid searches; the statevector
+ * entry points above remain the evolution itself.
+ * For every instance b < batch and angle point a < angles it evolves p
+ * rounds with gamma_k = gammas[a], beta_k = betas[a] from |+> and writes,
+ * after every round k (0-based),
+ *   out[((b * angles + a) * p + k) * 3 + 0] = P(C=0),
+ *   out[... + 1] = <H_P> (Eq. 4),
+ *   out[... + 2] = D, the probability of the lowest non-empty cost class
+ *                  (a Max-SAT assignment; D = P for a satisfiable instance).
+ * hist   device uint64 [batch][hist_stride] (8-byte aligned): h[b][c], the
+ *        number of assignments with cost c; each row sums to 2^n.
+ *        hist_stride in 1..256 (m + 1 for m clauses).
+ * gammas, betas  device double [angles].
+ * out    device double [batch][angles][p][3], written.
+ * best   optional device int32 [batch][p]: the angle point with the smallest
+ *        <H_P> after round k (the smallest index among equal values);
+ *        batch * p must stay below 2^31. NULL skips it.
+ * ws     device workspace of gqaoa_reduced_sweep_workspace_size(angles)
+ *        bytes (16-byte aligned, caller-owned): the phase tables.
+ * Precision: complex64 class amplitudes and FP64 phases rounded to
+ * complex64 (as the statevector path); the class sums are FP32 per lane and
+ * double-float across a warp.
+ * Errors: GQAOA_ERANGE for n outside 1..GQAOA_MAX_N, hist_stride outside
+ * 1..256, batch < 1, angles outside 1..2^24, p outside 1..2^20;
+ * GQAOA_EINVAL for NULL or misaligned pointers; GQAOA_ENOMEM for a short
+ * workspace.
+ */
+int gqaoa_reduced_sweep_workspace_size(int angles, size_t *bytes);
+int gqaoa_reduced_sweep(const uint64_t *hist, int hist_stride, int n, int batch,
+                        const double *gammas, const double *betas, int angles, int p,
+                        double *out, int32_t *best, void *ws, size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * Learned angle proposer (K9). The paper observes that optimal angles
  * cluster with the instance size and clause count (Section III.B, Fig. 2;

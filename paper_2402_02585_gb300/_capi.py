@@ -67,6 +67,8 @@ SIGNATURES = {
     "gqaoa_grad_batched": [_P, _I64, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P],
     "gqaoa_evolve_noalloc": [_P, _I, _I, _P, _P, _I, _P, _P, _P, _U, _P],
     "gqaoa_sweep_workspace_size": [_I, _I, _I, _SZP],
+    "gqaoa_reduced_sweep_workspace_size": [_I, _SZP],
+    "gqaoa_reduced_sweep": [_P, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P, _SZ, _P],
     "gqaoa_sweep": [_P, _I, _I, _I, _P, _P, _I, _I, _P, _I, _I, _P, _P, _SZ, _P],
     "gqaoa_mlp_param_count": [_I, _I, _I, _SZP],
     "gqaoa_mlp_workspace_size": [_I, _I, _I, _I, _SZP],
@@ -190,6 +192,16 @@ def gqaoa_sweep(cost, n, m, batch, gammas, betas, angles, p, rounds, nrounds, am
                 out, ws, ws_bytes, stream):
     _call("gqaoa_sweep", cost, n, m, batch, gammas, betas, angles, p, rounds, nrounds,
           amps_per_thread, out, ws, ws_bytes, stream)
+
+
+def gqaoa_reduced_sweep_workspace_size(angles) -> int:
+    return _size("gqaoa_reduced_sweep_workspace_size", angles)
+
+
+def gqaoa_reduced_sweep(hist, hist_stride, n, batch, gammas, betas, angles, p, out, best, ws,
+                        ws_bytes, stream):
+    _call("gqaoa_reduced_sweep", hist, hist_stride, n, batch, gammas, betas, angles, p, out, best,
+          ws, ws_bytes, stream)
 
 
 def gqaoa_mlp_param_count(d_in, d_h, d_out) -> int:

@@ -169,6 +169,29 @@ def grad_batched(cost: torch.Tensor, n: int, m: int, gammas, betas, objective: s
     return value, dg, db
 
 
+def reduced_sweep(hist: torch.Tensor, n: int, gammas, betas, p: int, best: bool = True,
+                  ws: torch.Tensor | None = None):
+    """Cost-class model (Appendix C) over angle points: hist [B, m + 1] (int64,
+    each row summing to 2^n), gammas/betas [A] single angle pairs. Returns
+    out [B, A, p, 3] (P, <H_P>, Max-SAT weight D after every round) and, with
+    best=True, best [B, p] (the angle point of smallest <H_P> per round)."""
+    _require_cuda(hist)
+    device = hist.device
+    hist = hist.reshape(-1, hist.shape[-1]).contiguous()
+    B, stride = hist.shape
+    g = _angles(gammas, device).reshape(-1)
+    b = _angles(betas, device).reshape(-1)
+    A = g.numel()
+    out = torch.empty((B, A, p, 3), dtype=torch.float64, device=device)
+    bst = torch.empty((B, p), dtype=torch.int32, device=device) if best else None
+    need = C.gqaoa_reduced_sweep_workspace_size(A)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, device)
+    C.gqaoa_reduced_sweep(_ptr(hist), stride, n, B, _ptr(g), _ptr(b), A, p, _ptr(out), _ptr(bst),
+                          _ptr(ws), ws.numel(), _stream())
+    return out, bst
+
+
 class GQAOAObjective(torch.autograd.Function):
     """L(gamma, beta) = P(C=0) or <H_P> of Eq. 3, differentiable in the angles.
 

@@ -117,6 +117,24 @@ def test_sample_and_grad_reject_bad_arguments_before_launch():
     assert e.value.status == C.GQAOA_ENOMEM
 
 
+def test_reduced_sweep_rejects_bad_arguments_before_launch():
+    fake = 1 << 20
+    for args in ((fake, 257, 10, 1, fake, fake, 4, 4, fake, None, fake, 1 << 20, None),   # stride
+                 (fake, 43, 0, 1, fake, fake, 4, 4, fake, None, fake, 1 << 20, None),     # n
+                 (fake, 43, 10, 1, fake, fake, 4, 0, fake, None, fake, 1 << 20, None)):   # p
+        with pytest.raises(C.GQAOAError) as e:
+            C.gqaoa_reduced_sweep(*args)
+        assert e.value.status == C.GQAOA_ERANGE
+    with pytest.raises(C.GQAOAError) as e:  # misaligned output
+        C.gqaoa_reduced_sweep(fake, 43, 10, 1, fake, fake, 4, 4, fake + 4, None, fake, 1 << 20, None)
+    assert e.value.status == C.GQAOA_EINVAL
+    need = C.gqaoa_reduced_sweep_workspace_size(4)
+    assert need == 8192 + 256
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_reduced_sweep(fake, 43, 10, 1, fake, fake, 4, 4, fake, None, fake, need - 1, None)
+    assert e.value.status == C.GQAOA_ENOMEM
+
+
 def test_sweep_workspace_sizes():
     small = C.gqaoa_sweep_workspace_size(12, 4, 0)
     assert 0 < small < 1 << 16
