@@ -28,6 +28,7 @@ import numpy as np
 _STREAM_CLAUSES = 0
 _STREAM_ANGLES = 1
 _STREAM_SHAPE = 2
+_STREAM_PROTOCOL = 5
 
 
 def _raw(seed: int, stream: int) -> np.random.PCG64:
@@ -99,6 +100,24 @@ def random_angles(p: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
     """gamma_k, beta_k uniform in [0, pi), k = 1..p (float64 [p] each)."""
     u = _unit(_raw(seed, _STREAM_ANGLES), 2 * p)
     return np.pi * u[:p], np.pi * u[p:]
+
+
+def protocol_grid(step_deg: int = 1) -> tuple[np.ndarray, np.ndarray]:
+    """The angle grid of the paper's protocol (Appendix C: spacing pi/180):
+    gamma = i pi/180, i = 0..180, times beta = j pi/180, j = 0..359
+    (gamma-major). The conjugation (gamma, beta) -> (2 pi - gamma, 2 pi - beta)
+    leaves P and <H_P> unchanged, so gamma in [0, pi] covers the torus.
+    step_deg > 1 thins both axes (for small tests)."""
+    gi = np.arange(0, 181, step_deg) * (np.pi / 180)
+    bj = np.arange(0, 360, step_deg) * (np.pi / 180)
+    return np.repeat(gi, bj.size), np.tile(bj, gi.size)
+
+
+def protocol_random_angles(count: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """count angle pairs uniform on [0, pi) x [0, 2 pi) (the protocol's sampled
+    alternative to the grid above n = 20)."""
+    u = _unit(_raw(seed, _STREAM_PROTOCOL), 2 * count)
+    return np.pi * u[:count], 2 * np.pi * u[count:]
 
 
 def sweep_shapes(count: int, seed: int, n_values=range(12, 21),

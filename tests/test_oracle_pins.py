@@ -13,7 +13,7 @@ import pytest
 import scipy.linalg
 import scipy.optimize
 
-from oracle import reduced, statevector as sv
+from oracle import protocol, reduced, statevector as sv
 from paper_2402_02585_gb300 import instances
 from tests.golden_io import paper_instances
 
@@ -304,31 +304,66 @@ def test_single_angle_gradient_is_sum_over_rounds():
 # --------------------------------------------------------------------------
 
 def _energy_optimal_P(hist, p):
-    """Minimise <H_P> (Eq. 4) the way Appendix C describes: a grid over the
-    single angle pair, then L-BFGS-B over all 2p angles from the best seeds;
-    return P at the lowest energy found."""
-    def energy(x):
-        return reduced.readout(hist, reduced.evolve(hist, x[:p], x[p:]))[1]
-
-    def jac(x):
-        _, dg, db = reduced.grad(hist, x[:p], x[p:], reduced.OBJ_ENERGY)
-        return np.concatenate([dg, db])
-
-    grid = np.arange(0, 2 * np.pi, np.pi / 90)
-    vals = []
-    for gam in grid:
-        for bet in grid:
-            vals.append((energy(np.array([gam] * p + [bet] * p)), gam, bet))
-    vals.sort()
+    """Minimise <H_P> (Eq. 4) the way Appendix C describes, with the protocol
+    oracle's steps: a grid over the single angle pair (pi/90 here), then
+    L-BFGS-B over all 2p angles. The paper does not print its angles, so the
+    40 best grid seeds are refined and the lowest energy kept (one more
+    local optimum of the same landscape would otherwise decide the test)."""
+    G, B = instances.protocol_grid(2)
+    G = np.concatenate([G, 2 * np.pi - G])  # both halves of the torus
+    B = np.concatenate([B, (2 * np.pi - B) % (2 * np.pi)])
+    E, _, _ = protocol.grid_readouts(hist, G, B, p)
     best = None
-    for _, gam, bet in vals[:40]:
-        x0 = np.array([gam] * p + [bet] * p)
-        r = scipy.optimize.minimize(energy, x0, jac=jac, method="L-BFGS-B",
-                                    options=dict(ftol=1e-12, gtol=1e-10))
-        if best is None or r.fun < best.fun - 1e-12:
-            best = r
-    f = reduced.evolve(hist, best.x[:p], best.x[p:])
+    for a in np.argsort(E[:, p - 1], kind="stable")[:40]:
+        g, b, e, _ = protocol.refine(hist, [G[a]] * p, [B[a]] * p, single=False)
+        if best is None or e < best[2] - 1e-12:
+            best = (g, b, e)
+    f = reduced.evolve(hist, best[0], best[1])
     return reduced.readout(hist, f)[0]
+
+
+def _two_class(M: int, N: int) -> np.ndarray:
+    """A cost-class histogram with M solutions and N - M assignments of cost 1."""
+    return np.array([M, N - M], dtype=np.int64)
+
+
+def test_two_class_model_is_grover_at_pi_pi():
+    # costs in {0, 1}: e^{-i pi C} = -(-1)^{[C=0]} and e^{-i pi} - 1 = -2, so a
+    # round at (gamma, beta) = (pi, pi) is Grover's iteration up to a global
+    # sign and P after k rounds is sin^2((2k + 1) theta), sin^2 theta = M / N
+    M, N, p = 3, 1024, 12
+    theta = math.asin(math.sqrt(M / N))
+    tr = reduced.readouts_trace(_two_class(M, N), [math.pi] * p, [math.pi] * p)
+    k = np.arange(1, p + 1)
+    assert np.max(np.abs(tr[:, 0] - np.sin((2 * k + 1) * theta) ** 2)) < 1e-12
+    assert np.max(np.abs(tr[:, 1] - (1 - tr[:, 0]))) < 1e-12        # <H_P> = 1 - P
+
+
+def test_protocol_min_rounds_two_class_closed_form():
+    # Two classes: <H_P> = 1 - P, so the protocol maximises P; with k oracle
+    # rounds no choice of phases beats sin^2((2k + 1) theta) while
+    # (2k + 1) theta <= pi/2, and (pi, pi) on the grid attains it, so the fewest
+    # rounds reaching P >= 1/2 is the smallest k with (2k + 1) theta >= pi/4
+    M, N = 3, 1024
+    theta = math.asin(math.sqrt(M / N))
+    k_star = math.ceil((math.pi / (4 * theta) - 1) / 2)
+    G, B = instances.protocol_grid(4)
+    k, g, b, val, e = protocol.min_rounds(_two_class(M, N), G, B, S=0.5, p_max=16)
+    assert k == k_star == 7
+    assert abs(val - math.sin((2 * k + 1) * theta) ** 2) < 1e-9
+    assert abs(e - (1 - val)) < 1e-9
+
+
+def test_protocol_grid_readouts_match_single_evolutions():
+    n, m, p = 8, 34, 9
+    _, hist = sv.cost_table(instances.random_3sat(n, m, 31), n)
+    G, B = instances.protocol_random_angles(6, 31)
+    E, P, D = protocol.grid_readouts(hist, G, B, p)
+    for a in range(6):
+        tr = reduced.readouts_trace(hist, [G[a]] * p, [B[a]] * p)
+        assert np.max(np.abs(P[a] - tr[:, 0])) < 1e-13
+        assert np.max(np.abs(E[a] - tr[:, 1])) < 1e-12
+        assert np.max(np.abs(D[a] - tr[:, 2])) < 1e-13
 
 
 def test_table1_noiseless_solution_probability():
