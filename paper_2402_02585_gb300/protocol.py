@@ -1,0 +1,152 @@
+"""The paper's angle protocol on the GPU (Appendix C, "Optimization"; Section III).
+
+For one instance and a target probability S:
+
+  1. <H_P> (Eq. 4) of single-angle-pair G-QAOA on the pi/180 grid of
+     (gamma, beta) (n <= 20; 4000 sampled angle pairs above) at every depth
+     k <= p_max at once, from one cost-class evolution per angle pair
+     (gqaoa_reduced_sweep, Appendix C's own simulation method), with the
+     grid point of lowest <H_P> per depth from the same call;
+  2. from that seed, L-BFGS-B on <H_P> with 1e-6 relative change as the
+     stopping rule, the gradient from the statevector adjoint kernels
+     (gqaoa_grad, the per-round gradients summed for the single angle pair;
+     all 2k angles for G-QAOA with per-round angles);
+  3. the solution probability P of the refined state on the statevector
+     (gqaoa_evolve); the answer is the fewest rounds with P >= S.
+
+A depth is refined only where its grid seed already reaches S/2 (the
+refinement is local and does not double the probability); the cost-class
+and statevector evaluations agree to complex64 precision (tested), so the
+grid ranks candidates and the statevector decides.
+"""
+
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.optimize
+import torch
+
+from . import _capi as C
+from . import core, instances
+
+
+@dataclass
+class MinRounds:
+    p: int | None                 # fewest rounds reaching S (None: not within p_max)
+    gammas: np.ndarray | None     # refined angles at p
+    betas: np.ndarray | None
+    prob: float | None            # P on the statevector at p
+    energy: float | None          # <H_P> at the refined angles
+    grid_prob: np.ndarray = field(default_factory=lambda: np.zeros(0))  # per depth, at the seed
+    evaluations: int = 0          # statevector gradient evaluations
+    seconds: float = 0.0
+
+
+def grid_for(n: int, seed: int = 0):
+    """The protocol's angle set: the pi/180 grid for n <= 20, 4000 sampled
+    angle pairs above."""
+    if n <= 20:
+        return instances.protocol_grid()
+    return instances.protocol_random_angles(4000, seed)
+
+
+class Protocol:
+    """The protocol for one instance: cost [2^n] uint8 and hist [m + 1] int64
+    on the device (core.build_cost)."""
+
+    def __init__(self, cost: torch.Tensor, hist: torch.Tensor, n: int, m: int):
+        core._require_cuda(cost, hist)
+        self.cost, self.hist, self.n, self.m = cost, hist, n, m
+        self._ws = {}
+        self.evaluations = 0
+
+    def _workspace(self, kind: str, p: int) -> torch.Tensor:
+        key = (kind, p)
+        if key not in self._ws:
+            size = (C.gqaoa_grad_workspace_size(self.n, p) if kind == "grad"
+                    else C.gqaoa_evolve_workspace_size(self.n, p))
+            self._ws[key] = core.workspace(size, self.cost.device)
+        return self._ws[key]
+
+    def energy_and_grad(self, gammas, betas):
+        v, dg, db = core.grad(self.cost, self.n, self.m, gammas, betas, "energy",
+                              ws=self._workspace("grad", len(gammas)))
+        self.evaluations += 1
+        return float(v), dg.cpu().numpy(), db.cpu().numpy()
+
+    def refine(self, gammas0, betas0, single: bool):
+        """L-BFGS-B on <H_P> (relative change 1e-6). Returns (gammas, betas,
+        <H_P>, evaluations)."""
+        g0 = np.asarray(gammas0, np.float64)
+        b0 = np.asarray(betas0, np.float64)
+        p = g0.shape[0]
+        if single:
+            def fun(x):
+                e, dg, db = self.energy_and_grad(np.full(p, x[0]), np.full(p, x[1]))
+                return e, np.array([dg.sum(), db.sum()])
+            x0 = np.array([g0[0], b0[0]])
+        else:
+            def fun(x):
+                e, dg, db = self.energy_and_grad(x[:p], x[p:])
+                return e, np.concatenate([dg, db])
+            x0 = np.concatenate([g0, b0])
+        r = scipy.optimize.minimize(fun, x0, jac=True, method="L-BFGS-B",
+                                    options=dict(ftol=1e-6, gtol=1e-10, maxiter=500))
+        if single:
+            return np.full(p, r.x[0]), np.full(p, r.x[1]), float(r.fun), int(r.nfev)
+        return r.x[:p].copy(), r.x[p:].copy(), float(r.fun), int(r.nfev)
+
+    def probability(self, gammas, betas) -> float:
+        _, out, _ = core.evolve(self.cost, self.n, self.m, gammas, betas,
+                                ws=self._workspace("evolve", len(gammas)))
+        return float(out[0].item())
+
+    def min_rounds(self, S: float = 0.5, p_max: int = 64, single: bool = True,
+                   grid=None, seed: int = 0) -> MinRounds:
+        t0 = time.perf_counter()
+        self.evaluations = 0
+        G, B = grid if grid is not None else grid_for(self.n, seed)
+        out, best = core.reduced_sweep(self.hist[None], self.n, G, B, p_max)
+        bi = best[0].long()
+        seed_vals = out[0, bi, torch.arange(p_max, device=out.device)].cpu().numpy()
+        bi = bi.cpu().numpy()
+        res = MinRounds(None, None, None, None, None, grid_prob=seed_vals[:, 0].copy())
+        for k in range(1, p_max + 1):
+            if seed_vals[k - 1, 0] < S / 2:
+                continue
+            a = int(bi[k - 1])
+            g, b, e, _ = self.refine([G[a]] * k, [B[a]] * k, single=True)
+            if not single:
+                g, b, e, _ = self.refine(g, b, single=False)
+            prob = self.probability(g, b)
+            if prob >= S:
+                res.p, res.gammas, res.betas, res.prob, res.energy = k, g, b, prob, e
+                break
+        res.evaluations = self.evaluations
+        res.seconds = time.perf_counter() - t0
+        return res
+
+
+def satisfiable_shapes(count: int, seed: int, n_values, d_lo: float = 2.0, d_hi: float = 4.5):
+    """Section III's satisfiable workload: n uniform over n_values, density
+    uniform on (d_lo, d_hi), m = round(n d), instances drawn until count
+    satisfiable ones are found (h[0] > 0, decided by the cost kernel).
+    Returns [(n, m, instance seed, lits, cost, hist)]."""
+    out = []
+    tries = 0
+    while len(out) < count:
+        batch = instances.uniform_density_shapes(4 * count, seed * 1_000_003 + tries,
+                                                 n_values, d_lo, d_hi)
+        for i, (n, m, _) in enumerate(batch):
+            iseed = (seed * 1_000_003 + tries) * 4096 + i
+            lits = instances.random_3sat(n, m, iseed)
+            cost, hist = core.build_cost(lits, n)
+            if int(hist[0].item()) > 0:
+                out.append((n, m, iseed, lits, cost, hist))
+                if len(out) == count:
+                    break
+        tries += 1
+    return out
