@@ -56,6 +56,14 @@ WORKLOADS = {
     "grad_profile": dict(kind="grad", n=16, m=67, p=4, batch=512, seed=0, lr=0.05,
                          desc="512 random 3-SAT instances n=16 m=67 (d~4.2), p=4 random angles; "
                               "one step = adjoint gradient of P(C=0) for all + one Adam update"),
+    # the paper's angle protocol (Appendix C) on satisfiable instances of
+    # Section III's density range; one step = the protocol for every instance
+    "protocol": dict(kind="protocol", count=32, n_values=list(range(10, 17)), d_lo=2.0, d_hi=4.5,
+                     S=0.5, p_max=64, seed=0,
+                     desc="32 satisfiable random 3-SAT instances, n uniform in 10..16, d uniform "
+                          "in (2, 4.5); pi/180 <H_P> grid (cost-class model), L-BFGS-B with "
+                          "statevector adjoint gradients, fewest single-angle-pair rounds to "
+                          "P >= 50 % on the statevector"),
     # the profiling case: same recipe, state (512 MiB) still far larger than L2
     "profile": dict(n=26, m=109, p=8, shots=100_000, seed=0,
                     desc="random 3-SAT n=26 m=109 (d~4.2) seed 0, p=8 random angles, 1e5 shots"),
@@ -675,6 +683,121 @@ def run_sweep(args, wl):
     return 0
 
 
+def run_protocol(args, wl):
+    """Workload "protocol": the paper's angle protocol for every instance.
+    Metric: instances per second. Also reported: the fewest rounds per
+    instance against the random-guess probability P = h[0] / 2^n and the
+    fitted exponent of p_min ~ (1/P)^x (Section III's evidence for a
+    quadratic speedup: x ~ 0.5), and the cost-class grid kernel's rate."""
+    import torch
+
+    from paper_2402_02585_gb300 import core, instances
+    from paper_2402_02585_gb300.protocol import Protocol, satisfiable_shapes
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    shapes = satisfiable_shapes(wl["count"], wl["seed"] + rank, wl["n_values"], wl["d_lo"],
+                                wl["d_hi"])
+    prots = [(n, m, hist, Protocol(cost, hist, n, m)) for n, m, _, _, cost, hist in shapes]
+
+    def one_pass():
+        res = []
+        for n, m, hist, prot in prots:
+            r = prot.min_rounds(S=wl["S"], p_max=wl["p_max"])
+            if r.p is None:
+                first = r
+                r = prot.min_rounds(S=wl["S"], p_max=4 * wl["p_max"])
+                r.launches += first.launches
+                r.evaluations += first.evaluations
+            res.append(r)
+        return res
+
+    for _ in range(args.warmup):
+        one_pass()
+    # the grid kernel alone, on the full pi/180 grid of the first instance
+    G, B = instances.protocol_grid()
+    n0, _, h0, _ = prots[0]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(5):
+        core.reduced_sweep(h0[None], n0, G, B, wl["p_max"])
+    e1.record()
+    torch.cuda.synchronize()
+    t_grid = e0.elapsed_time(e1) / 5 / 1e3
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        results = one_pass()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    clk = clocks.stop()
+    if world > 1:
+        te = torch.tensor([el], dtype=torch.float64, device="cuda")
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        el = float(te.item())
+    count = len(prots) * world * args.steps
+    pr = np.array([int(h[0].item()) / (1 << n) for n, m, h, _ in prots])
+    pm = np.array([r.p if r.p is not None else np.nan for r in results], dtype=np.float64)
+    ok = np.isfinite(pm)
+    slope = float(np.polyfit(np.log(1 / pr[ok]), np.log(pm[ok]), 1)[0]) if ok.sum() > 2 else None
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    # grid kernel: per item-round a warp issues ~14 FP32 instructions per class
+    # slot and ~125 for its three warp butterflies (derived from the source)
+    J = (int(h0.numel()) + 31) // 32
+    alu_peak = 4 * sms * 2.07e9 / (14 * J + 125)
+    grid_rate = len(G) * wl["p_max"] / t_grid
+    if rank == 0:
+        print(json.dumps({
+            "metric": "protocol instances/s", "value": count / el, "unit": "instances/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64 (grid, statevector) + f64 optimiser",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "instances": len(prots), "S": wl["S"],
+                       "p_max": wl["p_max"]},
+            "roofline": {"bound": "alu", "achieved": grid_rate, "peak": alu_peak,
+                         "unit": "item-rounds/s", "frac": grid_rate / alu_peak,
+                         "kernel": f"reduced_sweep_kernel<{J}>: pi/180 grid ({len(G)} angle "
+                                   f"pairs) x p = {wl['p_max']}, n = {n0}, {t_grid * 1e3:.2f} ms",
+                         "peak_derivation": "4 warp-instr/clk/SM x SMs x 2.07 GHz / "
+                                            f"(14 x {J} + 125) instructions per item-round"},
+            "p_min": [None if r.p is None else int(r.p) for r in results],
+            "P_random": [float(x) for x in pr],
+            "fitted_exponent": slope,
+            "gradient_evaluations_per_instance": float(np.mean([r.evaluations for r in results])),
+            "cpu_baseline": cpu_protocol_baseline(wl, shapes) if world == 1 else None,
+            "gpu_launches": int(sum(r.launches for r in results)) * args.steps, "clocks": clk}),
+              flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def cpu_protocol_baseline(wl, shapes):
+    """The protocol oracle (FP64 cost-class model for the grid and the
+    gradients) on the first two instances, on the host cores."""
+    from oracle import protocol as oprot
+    from paper_2402_02585_gb300 import instances
+    if os.environ.get("GQAOA_BENCH_NO_CPU") == "1":
+        return None
+    G, B = instances.protocol_grid()
+    t0 = time.perf_counter()
+    for n, m, _, _, _, hist in shapes[:2]:
+        oprot.min_rounds(hist.cpu().numpy(), G, B, S=wl["S"], p_max=wl["p_max"])
+    t = time.perf_counter() - t0
+    return {"value": 2 / t, "unit": "instances/s", "cores": 1, "kind": "oracle",
+            "sample": "the first two instances, full protocol (numpy/scipy, FP64 cost-class "
+                      "model for grid, refinement and probability)"}
+
+
 def cpu_sweep_baseline(wl):
     """The FP64 statevector oracle on a bounded sample of the sweep: one
     (instance, grid point) per n in 12..20 for all p rounds with the P trace."""
@@ -736,6 +859,8 @@ def main():
         return run_reference(args, wl)
     if wl.get("kind") == "grad":
         return run_grad(args, wl)
+    if wl.get("kind") == "protocol":
+        return run_protocol(args, wl)
     if wl.get("kind") == "sweep":
         return run_sweep(args, wl)
     return run_ours(args, wl)

@@ -42,6 +42,7 @@ class MinRounds:
     energy: float | None          # <H_P> at the refined angles
     grid_prob: np.ndarray = field(default_factory=lambda: np.zeros(0))  # per depth, at the seed
     evaluations: int = 0          # statevector gradient evaluations
+    launches: int = 0             # kernels launched by the library for this search
     seconds: float = 0.0
 
 
@@ -62,6 +63,8 @@ class Protocol:
         self.cost, self.hist, self.n, self.m = cost, hist, n, m
         self._ws = {}
         self.evaluations = 0
+        self.launches = 0
+        self._small = (1 << n) < 4096  # one CTA per state: phase tables + one or two kernels
 
     def _workspace(self, kind: str, p: int) -> torch.Tensor:
         key = (kind, p)
@@ -75,6 +78,7 @@ class Protocol:
         v, dg, db = core.grad(self.cost, self.n, self.m, gammas, betas, "energy",
                               ws=self._workspace("grad", len(gammas)))
         self.evaluations += 1
+        self.launches += 3 if self._small else 2 * len(gammas) + 3
         return float(v), dg.cpu().numpy(), db.cpu().numpy()
 
     def refine(self, gammas0, betas0, single: bool):
@@ -102,14 +106,17 @@ class Protocol:
     def probability(self, gammas, betas) -> float:
         _, out, _ = core.evolve(self.cost, self.n, self.m, gammas, betas,
                                 ws=self._workspace("evolve", len(gammas)))
+        self.launches += 2 if self._small else len(gammas) + 3
         return float(out[0].item())
 
     def min_rounds(self, S: float = 0.5, p_max: int = 64, single: bool = True,
                    grid=None, seed: int = 0) -> MinRounds:
         t0 = time.perf_counter()
         self.evaluations = 0
+        self.launches = 0
         G, B = grid if grid is not None else grid_for(self.n, seed)
         out, best = core.reduced_sweep(self.hist[None], self.n, G, B, p_max)
+        self.launches += 3  # phase tables, the cost-class evolution, the argmin
         bi = best[0].long()
         seed_vals = out[0, bi, torch.arange(p_max, device=out.device)].cpu().numpy()
         bi = bi.cpu().numpy()
@@ -126,6 +133,7 @@ class Protocol:
                 res.p, res.gammas, res.betas, res.prob, res.energy = k, g, b, prob, e
                 break
         res.evaluations = self.evaluations
+        res.launches = self.launches
         res.seconds = time.perf_counter() - t0
         return res
 
