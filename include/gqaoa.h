@@ -54,10 +54,17 @@ extern "C" {
 
 /* gqaoa_evolve flags */
 #define GQAOA_STATE_IN 1u /* `state` holds the initial state psi_0 on entry */
+/* out[0] becomes the probability of cost value c (0..255) instead of C = 0;
+ * with c the lowest non-empty class it is the Max-SAT probability D of an
+ * unsatisfiable instance (Fig. 1(b)). Not combined with a trace (EINVAL). */
+#define GQAOA_READOUT_CLASS(c) (((unsigned)(c) & 0xFFu) << 8)
 
 /* gqaoa_grad objectives */
 #define GQAOA_OBJ_P0 0     /* P(C=0) = sum_{z: C(z)=0} |psi_p(z)|^2 */
 #define GQAOA_OBJ_ENERGY 1 /* <H_P> = sum_z C(z) |psi_p(z)|^2 (Eq. 4) */
+/* the probability of cost value c (0..255): sum_{z: C(z)=c} |psi_p(z)|^2;
+ * GQAOA_OBJ_CLASS(0) is GQAOA_OBJ_P0 */
+#define GQAOA_OBJ_CLASS(c) (256 + ((int)(c) & 0xFF))
 
 /* Human-readable name of a status code (static storage, never NULL). */
 const char *gqaoa_strerror(int status);
@@ -109,11 +116,13 @@ int gqaoa_evolve_workspace_size(int n, int p, size_t *bytes);
  * p                              number of rounds, 1 <= p <= 2^20.
  * state   device complex64 [2^n] written: psi_p. Read first as psi_0 when
  *                                flags & GQAOA_STATE_IN. 16-byte aligned.
- * out     device double [3]      written: P(C=0), <H_P>, sum |psi_p|^2 of the
- *                                final state; may be NULL.
+ * out     device double [3]      written: P(C=0) (or the probability of the
+ *                                class named by GQAOA_READOUT_CLASS), <H_P>,
+ *                                sum |psi_p|^2 of the final state; may be NULL.
  * trace   device double [p]      written: P(C=0) after each round; may be NULL.
  * ws, ws_bytes  device workspace, at least gqaoa_evolve_workspace_size(n, p).
- * flags                          0 or GQAOA_STATE_IN.
+ * flags                          0, GQAOA_STATE_IN, or-ed with
+ *                                GQAOA_READOUT_CLASS(c) (then trace must be NULL).
  * Precision: complex64 state, phase factors e^{-i gamma c} evaluated in FP64
  * and rounded to FP32; the mixer sum <+|chi> and every readout are FP64.
  * Errors: GQAOA_EINVAL, GQAOA_ERANGE, GQAOA_ENOMEM, GQAOA_ECUDA.
@@ -164,8 +173,11 @@ int gqaoa_grad_workspace_size(int n, int p, size_t *bytes);
 /*
  * Objective and adjoint gradient with respect to every angle of Eq. 3
  * (Appendix C optimises the angles with a gradient method, L-BFGS-B):
- *   objective GQAOA_OBJ_P0:     L = P(C=0)
- *   objective GQAOA_OBJ_ENERGY: L = <H_P>  (Eq. 4)
+ *   objective GQAOA_OBJ_P0:       L = P(C=0)
+ *   objective GQAOA_OBJ_ENERGY:   L = <H_P>  (Eq. 4)
+ *   objective GQAOA_OBJ_CLASS(c): L = probability of cost value c (the
+ *                                 Max-SAT probability D for the lowest
+ *                                 non-empty class; Fig. 1(b))
  * Forward: the rounds of gqaoa_evolve from |+>, storing each round's phased
  * state chi_k = e^{-i gamma_k C} psi_{k-1} in the workspace (checkpoints).
  * Backward, lambda_p = O psi_p and for k = p..1:

@@ -95,8 +95,10 @@ def amplitudes(f, cost):
     return np.asarray(f)[np.asarray(cost, dtype=np.int64)]
 
 
-def grad(hist, gammas, betas, objective: int = OBJ_P0):
-    """(L, dL/dgamma [p], dL/dbeta [p]) by the adjoint recurrence above."""
+def grad(hist, gammas, betas, objective: int = OBJ_P0, target: int = 0):
+    """(L, dL/dgamma [p], dL/dbeta [p]) by the adjoint recurrence above.
+    OBJ_P0 projects on cost value `target` (0: P(C=0); the lowest non-empty
+    class: the Max-SAT probability D)."""
     h = np.asarray(hist, dtype=np.float64)
     N = h.sum()
     c = np.arange(h.shape[0], dtype=np.float64)
@@ -112,7 +114,7 @@ def grad(hist, gammas, betas, objective: int = OBJ_P0):
         gs.append(gk)
         Ss.append(S)
     if objective == OBJ_P0:
-        O = (c == 0).astype(np.float64)
+        O = (c == target).astype(np.float64)
     elif objective == OBJ_ENERGY:
         O = c
     else:
@@ -130,12 +132,14 @@ def grad(hist, gammas, betas, objective: int = OBJ_P0):
     return L, dg, db
 
 
-def objective_value(hist, gammas, betas, objective: int = OBJ_P0) -> float:
-    r = readout(hist, evolve(hist, gammas, betas))
-    return float(r[0] if objective == OBJ_P0 else r[1])
+def objective_value(hist, gammas, betas, objective: int = OBJ_P0, target: int = 0) -> float:
+    f = evolve(hist, gammas, betas)
+    if objective == OBJ_P0:
+        return float(np.asarray(hist, np.float64)[target] * abs(f[target]) ** 2)
+    return float(readout(hist, f)[1])
 
 
-def fd_grad(hist, gammas, betas, objective: int = OBJ_P0, step: float = 1e-4):
+def fd_grad(hist, gammas, betas, objective: int = OBJ_P0, step: float = 1e-4, target: int = 0):
     """Central finite differences of objective_value (FP64)."""
     gammas = np.array(gammas, np.float64)
     betas = np.array(betas, np.float64)
@@ -146,9 +150,9 @@ def fd_grad(hist, gammas, betas, objective: int = OBJ_P0, step: float = 1e-4):
         for arr, out in ((gammas, dg), (betas, db)):
             old = arr[k]
             arr[k] = old + step
-            up = objective_value(hist, gammas, betas, objective)
+            up = objective_value(hist, gammas, betas, objective, target)
             arr[k] = old - step
-            dn = objective_value(hist, gammas, betas, objective)
+            dn = objective_value(hist, gammas, betas, objective, target)
             arr[k] = old
             out[k] = (up - dn) / (2 * step)
     return dg, db

@@ -23,6 +23,17 @@ GQAOA_ENOMEM = -5
 GQAOA_STATE_IN = 1
 GQAOA_OBJ_P0 = 0
 GQAOA_OBJ_ENERGY = 1
+
+
+def GQAOA_OBJ_CLASS(c: int) -> int:
+    """Objective: the probability of cost value c (0..255)."""
+    return 256 + (int(c) & 0xFF)
+
+
+def GQAOA_READOUT_CLASS(c: int) -> int:
+    """gqaoa_evolve flag: out[0] is the probability of cost value c."""
+    return (int(c) & 0xFF) << 8
+
 GQAOA_MAX_N = 34
 GQAOA_MAX_M = 255
 GQAOA_SWEEP_MIN_N = 9

@@ -20,6 +20,16 @@ from . import _capi as C
 OBJECTIVES = {"p0": C.GQAOA_OBJ_P0, "energy": C.GQAOA_OBJ_ENERGY}
 
 
+def objective_code(objective) -> int:
+    """"p0", "energy", ("class", c) (the probability of cost value c; the
+    lowest non-empty class gives the Max-SAT probability D) or a raw code."""
+    if isinstance(objective, tuple) and objective[0] == "class":
+        return C.GQAOA_OBJ_CLASS(objective[1])
+    if isinstance(objective, int):
+        return objective
+    return OBJECTIVES[objective]
+
+
 def _stream() -> int:
     return torch.cuda.current_stream().cuda_stream
 
@@ -60,8 +70,10 @@ def build_cost(lits, n: int, device=None, with_hist: bool = True):
 
 
 def evolve(cost: torch.Tensor, n: int, m: int, gammas, betas, state: torch.Tensor | None = None,
-           state_in: bool = False, trace: bool = False, ws: torch.Tensor | None = None):
-    """psi_p of Eq. 3. Returns (state complex64 [2^n], out float64 [3], trace or None)."""
+           state_in: bool = False, trace: bool = False, ws: torch.Tensor | None = None,
+           readout_class: int = 0):
+    """psi_p of Eq. 3. Returns (state complex64 [2^n], out float64 [3], trace or None);
+    out[0] is the probability of cost value readout_class (default 0: P(C=0))."""
     _require_cuda(cost)
     device = cost.device
     g = _angles(gammas, device)
@@ -76,8 +88,9 @@ def evolve(cost: torch.Tensor, n: int, m: int, gammas, betas, state: torch.Tenso
     need = C.gqaoa_evolve_workspace_size(n, p)
     if ws is None or ws.numel() < need:
         ws = workspace(need, device)
+    flags = (C.GQAOA_STATE_IN if state_in else 0) | C.GQAOA_READOUT_CLASS(readout_class)
     C.gqaoa_evolve(_ptr(cost), n, m, _ptr(g), _ptr(b), p, _ptr(state), _ptr(out), _ptr(tr),
-                   _ptr(ws), ws.numel(), C.GQAOA_STATE_IN if state_in else 0, _stream())
+                   _ptr(ws), ws.numel(), flags, _stream())
     return state, out, tr
 
 
@@ -144,7 +157,7 @@ def grad(cost: torch.Tensor, n: int, m: int, gammas, betas, objective: str = "p0
     need = C.gqaoa_grad_workspace_size(n, p)
     if ws is None or ws.numel() < need:
         ws = workspace(need, device)
-    C.gqaoa_grad(_ptr(cost), n, m, _ptr(g), _ptr(b), p, OBJECTIVES[objective], _ptr(value), _ptr(dg),
+    C.gqaoa_grad(_ptr(cost), n, m, _ptr(g), _ptr(b), p, objective_code(objective), _ptr(value), _ptr(dg),
                  _ptr(db), _ptr(ws), ws.numel(), _stream())
     return value[0], dg, db
 
@@ -164,7 +177,7 @@ def grad_batched(cost: torch.Tensor, n: int, m: int, gammas, betas, objective: s
     if ws is None or ws.numel() < need:
         ws = workspace(need, device)
     stride = 0 if shared_cost else (1 << n)
-    C.gqaoa_grad_batched(_ptr(cost), stride, n, m, B, _ptr(g), _ptr(b), p, OBJECTIVES[objective],
+    C.gqaoa_grad_batched(_ptr(cost), stride, n, m, B, _ptr(g), _ptr(b), p, objective_code(objective),
                          _ptr(value), _ptr(dg), _ptr(db), _ptr(ws), ws.numel(), _stream())
     return value, dg, db
 

@@ -244,6 +244,7 @@ struct PassArgs {
   uint64_t N;
   double inv_n;
   float amp0;               // N^{-1/2}
+  unsigned target;          // the cost class read out (readout) or projected on (lambda init)
 };
 
 // Programmatic dependent launch. A streaming pass is launched while the
@@ -475,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, kFwdPerSm) readout_kernel(const Pass
       const unsigned c_0 = T.c2[j] & 0xFFu, c_1 = T.c2[j] >> 8;
       tn += w0 + w1;
       te += (float)c_0 * w0 + (float)c_1 * w1;
-      tp += (c_0 == 0 ? w0 : 0.f) + (c_1 == 0 ? w1 : 0.f);
+      tp += (c_0 == a.target ? w0 : 0.f) + (c_1 == a.target ? w1 : 0.f);
     }
     if (kPending) {
       const uint64_t vb = vbase(t);
@@ -571,8 +572,8 @@ __global__ void __launch_bounds__(kThreads, kBwdPerSm) lambda_init_kernel(const 
     for (int j = 0; j < kVecPerThread; ++j) {
       const uint16_t c2 = T.c2[j];
       const float4 v = T.v[j];
-      const float o0 = kObj == GQAOA_OBJ_P0 ? ((c2 & 0xFFu) == 0 ? 1.f : 0.f) : (float)(c2 & 0xFFu);
-      const float o1 = kObj == GQAOA_OBJ_P0 ? ((c2 >> 8) == 0 ? 1.f : 0.f) : (float)(c2 >> 8);
+      const float o0 = kObj == GQAOA_OBJ_P0 ? ((c2 & 0xFFu) == a.target ? 1.f : 0.f) : (float)(c2 & 0xFFu);
+      const float o1 = kObj == GQAOA_OBJ_P0 ? ((c2 >> 8) == a.target ? 1.f : 0.f) : (float)(c2 >> 8);
       const float2 p0 = make_float2(v.x + ad.x, v.y + ad.y);
       const float2 p1 = make_float2(v.z + ad.x, v.w + ad.y);
       const float4 l = make_float4(o0 * p0.x, o0 * p0.y, o1 * p1.x, o1 * p1.y);
@@ -723,6 +724,7 @@ struct SmallArgs {
   double *record;        // [B][p][4]
   float2 *ckpt;          // [p][B][N] or null (gradient forward)
   int B;
+  unsigned target;       // the cost class of out[0] and of the projector objective
 };
 
 // One round of the small-state kernel on a thread's amplitudes; writes the
@@ -790,7 +792,7 @@ __global__ void __launch_bounds__(kThreads) evolve_small_kernel(const SmallArgs 
       const double w = (double)s[j].x * s[j].x + (double)s[j].y * s[j].y;
       ln += w;
       le += (double)c[j] * w;
-      if (c[j] == 0) lp += w;
+      if (c[j] == a.target) lp += w;
     }
   }
   const double P = block_sum(lp, s_scr);
@@ -822,7 +824,7 @@ grad_small_kernel(const SmallArgs a, int objective, double *__restrict__ value,
     l[j] = make_float2(0.f, 0.f);
     if (z < N) {
       const float2 ps = make_float2(chip[z].x + ap.x, chip[z].y + ap.y);
-      const float o = objective == GQAOA_OBJ_P0 ? (c[j] == 0 ? 1.f : 0.f) : (float)c[j];
+      const float o = objective == GQAOA_OBJ_P0 ? (c[j] == a.target ? 1.f : 0.f) : (float)c[j];
       l[j] = make_float2(o * ps.x, o * ps.y);
       lv += (double)o * ((double)ps.x * ps.x + (double)ps.y * ps.y);
     }
@@ -1016,7 +1018,9 @@ static int evolve_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m,
   int rc = check_common(n, m, B, p);
   if (rc) return rc;
   if (!cost || !gammas || !betas || !state || !ws) return GQAOA_EINVAL;
-  if (flags & ~GQAOA_STATE_IN) return GQAOA_EINVAL;
+  if (flags & ~(GQAOA_STATE_IN | GQAOA_READOUT_CLASS(255))) return GQAOA_EINVAL;
+  const unsigned target = (flags >> 8) & 0xFFu;  // the class read out as out[0]
+  if (target != 0u && trace) return GQAOA_EINVAL;  // the per-round trace is P(C=0)
   if (!aligned16(state) || !aligned16(cost) || !aligned8(gammas) || !aligned8(betas) ||
       (out && !aligned8(out)) || (trace && !aligned8(trace)) || !aligned16(ws))
     return GQAOA_EINVAL;
@@ -1030,7 +1034,7 @@ static int evolve_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m,
   if (rc) return rc;
   if (g.small) {
     SmallArgs sa = {cost, cost_bstride, n, p, w.phase, w.alpha, static_cast<float2 *>(state),
-                    from_state, out, trace, w.record, nullptr, B};
+                    from_state, out, trace, w.record, nullptr, B, target};
     evolve_small_kernel<<<B, kThreads, 0, st>>>(sa);
     GQ_CHECK_LAUNCH();
     return GQAOA_OK;
@@ -1045,6 +1049,7 @@ static int evolve_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m,
   pa.parts_out = parts_half(w, p);
   pa.src = static_cast<const float4 *>(state);
   pa.dst = static_cast<float4 *>(state);
+  pa.target = target;
   if (launch_pass(g, readout_kernel<true>, st, pa) != cudaSuccess) return GQAOA_ECUDA;
   finalize_readout_kernel<<<B, 32, 0, st>>>(pa.parts_out, g.nparts, p, out, trace);
   GQ_CHECK_LAUNCH();
@@ -1057,7 +1062,14 @@ static int grad_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m, i
   int rc = check_common(n, m, B, p);
   if (rc) return rc;
   if (!cost || !gammas || !betas || !value || !dgamma || !dbeta || !ws) return GQAOA_EINVAL;
-  if (objective != GQAOA_OBJ_P0 && objective != GQAOA_OBJ_ENERGY) return GQAOA_EINVAL;
+  // GQAOA_OBJ_CLASS(c): the projector objective on cost class c (P0 is class 0)
+  unsigned target = 0u;
+  if (objective >= GQAOA_OBJ_CLASS(0) && objective <= GQAOA_OBJ_CLASS(255)) {
+    target = (unsigned)(objective - GQAOA_OBJ_CLASS(0));
+    objective = GQAOA_OBJ_P0;
+  } else if (objective != GQAOA_OBJ_P0 && objective != GQAOA_OBJ_ENERGY) {
+    return GQAOA_EINVAL;
+  }
   if (!aligned16(cost) || !aligned8(gammas) || !aligned8(betas) || !aligned8(value) ||
       !aligned8(dgamma) || !aligned8(dbeta) || !aligned16(ws))
     return GQAOA_EINVAL;
@@ -1072,7 +1084,7 @@ static int grad_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m, i
   if (rc) return rc;
   if (g.small) {
     SmallArgs sa = {cost, cost_bstride, n, p, w.phase, w.alpha, w.lambda, false, nullptr,
-                    nullptr, w.record, w.ckpt, B};
+                    nullptr, w.record, w.ckpt, B, target};
     evolve_small_kernel<<<B, kThreads, 0, st>>>(sa);
     GQ_CHECK_LAUNCH();
     grad_small_kernel<<<B, kThreads, 0, st>>>(sa, objective, value, dgamma, dbeta);
@@ -1088,6 +1100,7 @@ static int grad_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m, i
   pa.value = value;
   pa.dgamma = dgamma;
   pa.dbeta = dbeta;
+  pa.target = target;
   // lambda_p = O psi_p (reads the last forward pass's records)
   pa.nparts_in = g.nparts;
   pa.round = p - 1;

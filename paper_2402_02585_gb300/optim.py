@@ -51,7 +51,7 @@ class AngleOptimizer:
         s = torch.cuda.current_stream().cuda_stream
         C.gqaoa_grad_batched(self.cost.data_ptr(), 1 << self.n, self.n, self.m, self.B,
                              self.theta[0].data_ptr(), self.theta[1].data_ptr(), self.p,
-                             core.OBJECTIVES[self.objective], self.value.data_ptr(),
+                             core.objective_code(self.objective), self.value.data_ptr(),
                              self.grad[0].data_ptr(), self.grad[1].data_ptr(), self.ws.data_ptr(),
                              self.ws.numel(), s)
         return self.value

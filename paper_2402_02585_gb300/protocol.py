@@ -14,6 +14,10 @@ For one instance and a target probability S:
   3. the solution probability P of the refined state on the statevector
      (gqaoa_evolve); the answer is the fewest rounds with P >= S.
 
+For an unsatisfiable instance (Max-SAT, Fig. 1(b)) the target is D, the
+probability of the lowest non-empty cost class (the assignments leaving the
+fewest clauses unsatisfied), read the same way with GQAOA_READOUT_CLASS.
+
 A depth is refined only where its grid seed already reaches S/2 (the
 refinement is local and does not double the probability); the cost-class
 and statevector evaluations agree to complex64 precision (tested), so the
@@ -38,7 +42,7 @@ class MinRounds:
     p: int | None                 # fewest rounds reaching S (None: not within p_max)
     gammas: np.ndarray | None     # refined angles at p
     betas: np.ndarray | None
-    prob: float | None            # P on the statevector at p
+    prob: float | None            # P (or D) on the statevector at p
     energy: float | None          # <H_P> at the refined angles
     grid_prob: np.ndarray = field(default_factory=lambda: np.zeros(0))  # per depth, at the seed
     evaluations: int = 0          # statevector gradient evaluations
@@ -65,6 +69,8 @@ class Protocol:
         self.evaluations = 0
         self.launches = 0
         self._small = (1 << n) < 4096  # one CTA per state: phase tables + one or two kernels
+        h = hist.cpu().numpy()
+        self.min_class = int(np.nonzero(h)[0][0])  # 0 when satisfiable
 
     def _workspace(self, kind: str, p: int) -> torch.Tensor:
         key = (kind, p)
@@ -103,14 +109,16 @@ class Protocol:
             return np.full(p, r.x[0]), np.full(p, r.x[1]), float(r.fun), int(r.nfev)
         return r.x[:p].copy(), r.x[p:].copy(), float(r.fun), int(r.nfev)
 
-    def probability(self, gammas, betas) -> float:
+    def probability(self, gammas, betas, cls: int = 0) -> float:
+        """Probability of cost value cls in the evolved state (statevector)."""
         _, out, _ = core.evolve(self.cost, self.n, self.m, gammas, betas,
-                                ws=self._workspace("evolve", len(gammas)))
+                                ws=self._workspace("evolve", len(gammas)), readout_class=cls)
         self.launches += 2 if self._small else len(gammas) + 3
         return float(out[0].item())
 
     def min_rounds(self, S: float = 0.5, p_max: int = 64, single: bool = True,
-                   grid=None, seed: int = 0) -> MinRounds:
+                   grid=None, seed: int = 0, target: str = "P") -> MinRounds:
+        """target "P": probability of a solution; "D": of a Max-SAT assignment."""
         t0 = time.perf_counter()
         self.evaluations = 0
         self.launches = 0
@@ -120,15 +128,17 @@ class Protocol:
         bi = best[0].long()
         seed_vals = out[0, bi, torch.arange(p_max, device=out.device)].cpu().numpy()
         bi = bi.cpu().numpy()
-        res = MinRounds(None, None, None, None, None, grid_prob=seed_vals[:, 0].copy())
+        col = 0 if target == "P" else 2
+        cls = 0 if target == "P" else self.min_class
+        res = MinRounds(None, None, None, None, None, grid_prob=seed_vals[:, col].copy())
         for k in range(1, p_max + 1):
-            if seed_vals[k - 1, 0] < S / 2:
+            if seed_vals[k - 1, col] < S / 2:
                 continue
             a = int(bi[k - 1])
             g, b, e, _ = self.refine([G[a]] * k, [B[a]] * k, single=True)
             if not single:
                 g, b, e, _ = self.refine(g, b, single=False)
-            prob = self.probability(g, b)
+            prob = self.probability(g, b, cls)
             if prob >= S:
                 res.p, res.gammas, res.betas, res.prob, res.energy = k, g, b, prob, e
                 break

@@ -285,6 +285,31 @@ def test_reduced_readouts_trace_satisfiable_and_gamma_zero():
     assert np.max(np.abs(tr0[:, 0] - hist[0] / 2 ** n)) < 1e-15
 
 
+def test_reduced_class_gradient_matches_statevector_fd_unsat():
+    # the Max-SAT objective D (probability of the lowest non-empty class) of an
+    # unsatisfiable instance: adjoint against central differences of the
+    # statevector oracle's class weight
+    n, m, p = 7, 63, 4
+    lits = instances.random_3sat(n, m, 21)
+    cost, hist = sv.cost_table(lits, n)
+    cs = reduced.min_class(hist)
+    assert cs > 0
+    g, b = instances.random_angles(p, 23)
+    L, dg, db = reduced.grad(hist, g, b, reduced.OBJ_P0, target=cs)
+    psi = sv.evolve(cost, n, g, b)
+    assert abs(L - np.sum(np.abs(psi[cost == cs]) ** 2)) < 1e-14
+    h = 1e-4
+    for k in range(p):
+        for arr, ref in ((g, dg), (b, db)):
+            a0 = arr[k]
+            arr[k] = a0 + h
+            up = np.sum(np.abs(sv.evolve(cost, n, g, b)[cost == cs]) ** 2)
+            arr[k] = a0 - h
+            dn = np.sum(np.abs(sv.evolve(cost, n, g, b)[cost == cs]) ** 2)
+            arr[k] = a0
+            assert abs((up - dn) / (2 * h) - ref[k]) < 1e-7
+
+
 def test_single_angle_gradient_is_sum_over_rounds():
     n, m, p = 9, 38, 7
     lits = instances.random_3sat(n, m, 13)
