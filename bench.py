@@ -64,6 +64,15 @@ WORKLOADS = {
                           "in (2, 4.5); pi/180 <H_P> grid (cost-class model), L-BFGS-B with "
                           "statevector adjoint gradients, fewest single-angle-pair rounds to "
                           "P >= 50 % on the statevector"),
+    # the same protocol for Max-SAT on unsatisfiable instances of the (4.6, 8)
+    # range, target D = probability of the lowest non-empty cost class
+    "protocol_maxsat": dict(kind="protocol", count=32, n_values=list(range(10, 17)), d_lo=4.6,
+                            d_hi=8.0, S=0.5, p_max=64, seed=1, target="D",
+                            desc="32 unsatisfiable random 3-SAT instances, n uniform in 10..16, d "
+                                 "uniform in (4.6, 8); pi/180 <H_P> grid (cost-class model), "
+                                 "L-BFGS-B with statevector adjoint gradients, fewest "
+                                 "single-angle-pair rounds to a Max-SAT probability D >= 50 % on "
+                                 "the statevector"),
     # the profiling case: same recipe, state (512 MiB) still far larger than L2
     "profile": dict(n=26, m=109, p=8, shots=100_000, seed=0,
                     desc="random 3-SAT n=26 m=109 (d~4.2) seed 0, p=8 random angles, 1e5 shots"),
@@ -684,10 +693,11 @@ def run_sweep(args, wl):
 
 
 def run_protocol(args, wl):
-    """Workload "protocol": the paper's angle protocol for every instance.
-    Metric: instances per second. Also reported: the fewest rounds per
-    instance against the random-guess probability P = h[0] / 2^n and the
-    fitted exponent of p_min ~ (1/P)^x (Section III's evidence for a
+    """Workloads "protocol" and "protocol_maxsat": the paper's angle protocol
+    for every instance (target P, or D for unsatisfiable instances). Metric:
+    instances per second. Also reported: the fewest rounds per instance
+    against the target's random-guess probability (h[0] / 2^n, or h[c*] / 2^n)
+    and the fitted exponent of p_min ~ (1/P)^x (Section III's evidence for a
     quadratic speedup: x ~ 0.5), and the cost-class grid kernel's rate."""
     import torch
 
@@ -699,17 +709,18 @@ def run_protocol(args, wl):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    target = wl.get("target", "P")
     shapes = satisfiable_shapes(wl["count"], wl["seed"] + rank, wl["n_values"], wl["d_lo"],
-                                wl["d_hi"])
+                                wl["d_hi"], satisfiable=target == "P")
     prots = [(n, m, hist, Protocol(cost, hist, n, m)) for n, m, _, _, cost, hist in shapes]
 
     def one_pass():
         res = []
         for n, m, hist, prot in prots:
-            r = prot.min_rounds(S=wl["S"], p_max=wl["p_max"])
+            r = prot.min_rounds(S=wl["S"], p_max=wl["p_max"], target=target)
             if r.p is None:
                 first = r
-                r = prot.min_rounds(S=wl["S"], p_max=4 * wl["p_max"])
+                r = prot.min_rounds(S=wl["S"], p_max=4 * wl["p_max"], target=target)
                 r.launches += first.launches
                 r.evaluations += first.evaluations
             res.append(r)
@@ -744,7 +755,8 @@ def run_protocol(args, wl):
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
         el = float(te.item())
     count = len(prots) * world * args.steps
-    pr = np.array([int(h[0].item()) / (1 << n) for n, m, h, _ in prots])
+    # the random-guess probability of the target: h[c*] / 2^n (c* = 0 when satisfiable)
+    pr = np.array([int(h[prot.min_class].item()) / (1 << n) for n, m, h, prot in prots])
     pm = np.array([r.p if r.p is not None else np.nan for r in results], dtype=np.float64)
     ok = np.isfinite(pm)
     slope = float(np.polyfit(np.log(1 / pr[ok]), np.log(pm[ok]), 1)[0]) if ok.sum() > 2 else None
@@ -770,7 +782,8 @@ def run_protocol(args, wl):
                          "peak_derivation": "4 warp-instr/clk/SM x SMs x 2.07 GHz / "
                                             f"(14 x {J} + 125) instructions per item-round"},
             "p_min": [None if r.p is None else int(r.p) for r in results],
-            "P_random": [float(x) for x in pr],
+            "target": target,
+            "random_guess_probability": [float(x) for x in pr],
             "fitted_exponent": slope,
             "gradient_evaluations_per_instance": float(np.mean([r.evaluations for r in results])),
             "cpu_baseline": cpu_protocol_baseline(wl, shapes) if world == 1 else None,
@@ -791,7 +804,8 @@ def cpu_protocol_baseline(wl, shapes):
     G, B = instances.protocol_grid()
     t0 = time.perf_counter()
     for n, m, _, _, _, hist in shapes[:2]:
-        oprot.min_rounds(hist.cpu().numpy(), G, B, S=wl["S"], p_max=wl["p_max"])
+        oprot.min_rounds(hist.cpu().numpy(), G, B, S=wl["S"], p_max=wl["p_max"],
+                         target=wl.get("target", "P"))
     t = time.perf_counter() - t0
     return {"value": 2 / t, "unit": "instances/s", "cores": 1, "kind": "oracle",
             "sample": "the first two instances, full protocol (numpy/scipy, FP64 cost-class "

@@ -148,11 +148,13 @@ class Protocol:
         return res
 
 
-def satisfiable_shapes(count: int, seed: int, n_values, d_lo: float = 2.0, d_hi: float = 4.5):
-    """Section III's satisfiable workload: n uniform over n_values, density
-    uniform on (d_lo, d_hi), m = round(n d), instances drawn until count
-    satisfiable ones are found (h[0] > 0, decided by the cost kernel).
-    Returns [(n, m, instance seed, lits, cost, hist)]."""
+def satisfiable_shapes(count: int, seed: int, n_values, d_lo: float = 2.0, d_hi: float = 4.5,
+                       satisfiable: bool = True):
+    """Section III's workloads: n uniform over n_values, density uniform on
+    (d_lo, d_hi), m = round(n d), instances drawn until count of the wanted
+    kind are found (satisfiable: h[0] > 0, the (2, 4.5) range; unsatisfiable:
+    h[0] = 0, the (4.6, 8) range of the Max-SAT study), decided by the cost
+    kernel. Returns [(n, m, instance seed, lits, cost, hist)]."""
     out = []
     tries = 0
     while len(out) < count:
@@ -162,7 +164,7 @@ def satisfiable_shapes(count: int, seed: int, n_values, d_lo: float = 2.0, d_hi:
             iseed = (seed * 1_000_003 + tries) * 4096 + i
             lits = instances.random_3sat(n, m, iseed)
             cost, hist = core.build_cost(lits, n)
-            if int(hist[0].item()) > 0:
+            if (int(hist[0].item()) > 0) == satisfiable:
                 out.append((n, m, iseed, lits, cost, hist))
                 if len(out) == count:
                     break
