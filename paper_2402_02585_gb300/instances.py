@@ -29,6 +29,7 @@ _STREAM_CLAUSES = 0
 _STREAM_ANGLES = 1
 _STREAM_SHAPE = 2
 _STREAM_PROTOCOL = 5
+_STREAM_SHOTS = 6
 
 
 def _raw(seed: int, stream: int) -> np.random.PCG64:
@@ -118,6 +119,21 @@ def protocol_random_angles(count: int, seed: int) -> tuple[np.ndarray, np.ndarra
     alternative to the grid above n = 20)."""
     u = _unit(_raw(seed, _STREAM_PROTOCOL), 2 * count)
     return np.pi * u[:count], 2 * np.pi * u[count:]
+
+
+def synthetic_shots(n: int, count: int, seed: int, hot=None, hot_fraction: float = 0.0):
+    """count measurement outcomes z in [0, 2^n) (uint64): uniform, except that
+    a hot_fraction of them is drawn uniformly from the `hot` assignments
+    (e.g. the solutions), so shot streams with many solution hits are cheap."""
+    bg = _raw(seed, _STREAM_SHOTS)
+    z = _below(bg, np.full(count, 1 << n)).astype(np.uint64)
+    if hot is not None and hot_fraction > 0:
+        hot = np.asarray(hot, dtype=np.uint64)
+        u = _unit(bg, count)
+        pick = _below(bg, np.full(count, hot.size))
+        sel = u < hot_fraction
+        z[sel] = hot[pick[sel]]
+    return z
 
 
 def sweep_shapes(count: int, seed: int, n_values=range(12, 21),
