@@ -301,6 +301,46 @@ int gqaoa_reduced_sweep(const uint64_t *hist, int hist_stride, int n, int batch,
                         const double *gammas, const double *betas, int angles, int p,
                         double *out, int32_t *best, void *ws, size_t ws_bytes, void *stream);
 
+/*
+ * Fair-sampling metrics of Section IV (Table I): how evenly the shots of
+ * gqaoa_sample cover the solutions (or any target cost class, e.g. the
+ * lowest non-empty class for Max-SAT). For each of `runs` independent runs
+ * (run r takes the shots r, r + runs, r + 2 runs, ... in that order, so
+ * `shots` holds runs * shots_per_run outcomes from one sampler call):
+ *   to_all[r]    = 1-based index (within the run) of the shot that completes
+ *                  the set of target assignments, 0 if the run never does;
+ *   to_reject[r] = the number of target draws d at which a chi-square test
+ *                  of uniform sampling over the M target assignments first
+ *                  rejects, 0 if it never does. The test runs after every
+ *                  draw with d >= min_draws and rejects when
+ *                  double(M sum_j O_j^2 - d^2) > chi2_crit * double(d), i.e.
+ *                  Pearson's X^2 = sum_j (O_j - d/M)^2 / (d/M) > chi2_crit
+ *                  with the exact integer numerator (O_j: draws of target j;
+ *                  chi2_crit: the caller's (1 - alpha) quantile of the
+ *                  chi-square law with M - 1 degrees of freedom).
+ * The paper reports the mean of to_all over runs and the median of
+ * to_reject over trials.
+ * shots   device uint64 [shots_per_run][runs] (8-byte aligned); outcomes
+ *         >= 2^n count as non-target.
+ * cost    device uint8 [2^n] (gqaoa_build_cost).
+ * target  the cost class counted (0 = solutions); targets: its size M, i.e.
+ *         h[target] of gqaoa_build_cost. If the table has a different
+ *         number of assignments of that cost, every output is -1.
+ * to_all, to_reject  device int64 [runs], written.
+ * ws      gqaoa_fairness_workspace_size(n, runs, targets) bytes (16-byte
+ *         aligned, caller-owned): labels of the 2^n assignments and
+ *         runs * M counters.
+ * Errors: GQAOA_ERANGE for n outside 1..30, runs outside 1..2^32, target
+ * outside 0..255, targets outside 1..2^n, min_draws < 1, or
+ * targets * shots_per_run^2 beyond 4e18; GQAOA_EINVAL for NULL or
+ * misaligned pointers; GQAOA_ENOMEM for a short workspace.
+ */
+int gqaoa_fairness_workspace_size(int n, int64_t runs, int targets, size_t *bytes);
+int gqaoa_fairness(const uint64_t *shots, int64_t runs, int64_t shots_per_run,
+                   const uint8_t *cost, int n, int target, int targets, double chi2_crit,
+                   int64_t min_draws, int64_t *to_all, int64_t *to_reject, void *ws,
+                   size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * Learned angle proposer (K9). The paper observes that optimal angles
  * cluster with the instance size and clause count (Section III.B, Fig. 2;

@@ -13,7 +13,10 @@ the set; in (ii) the draws are the solution hits of the same shot sequence,
 the test is applied after every draw once the expected count per solution
 reaches 5 (draws >= 5 M), and it rejects when the Pearson statistic
 X^2 = sum_j (O_j - d/M)^2 / (d/M) exceeds the (1 - alpha) quantile of the
-chi-square law with M - 1 degrees of freedom.
+chi-square law with M - 1 degrees of freedom. With integer counts
+X^2 = (M sum_j O_j^2 - d^2) / d, so the decision is taken on the exact
+integer numerator: reject when double(M sum O^2 - d^2) > crit * double(d)
+(the same IEEE-double comparison as the GPU kernel).
 
 `target` generalises "solution" to any cost class (the lowest non-empty
 class for Max-SAT).
@@ -52,9 +55,8 @@ def run_metrics(shots, cost, target: int, runs: int, chi2_crit: float, min_draws
             if seen == M and to_all[r] == 0:
                 to_all[r] = t + 1
             if d >= min_draws and to_rej[r] == 0:
-                e = d / M
-                x2 = float(np.sum((counts - e) ** 2) / e)
-                if x2 > chi2_crit:
+                num = M * int(np.sum(counts * counts)) - d * d   # d X^2, exact
+                if float(num) > chi2_crit * float(d):
                     to_rej[r] = d
             if to_all[r] and to_rej[r]:
                 break

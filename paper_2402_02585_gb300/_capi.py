@@ -79,6 +79,8 @@ SIGNATURES = {
     "gqaoa_evolve_noalloc": [_P, _I, _I, _P, _P, _I, _P, _P, _P, _U, _P],
     "gqaoa_sweep_workspace_size": [_I, _I, _I, _SZP],
     "gqaoa_reduced_sweep_workspace_size": [_I, _SZP],
+    "gqaoa_fairness_workspace_size": [_I, _I64, _I, _SZP],
+    "gqaoa_fairness": [_P, _I64, _I64, _P, _I, _I, _I, _D, _I64, _P, _P, _P, _SZ, _P],
     "gqaoa_reduced_sweep": [_P, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P, _SZ, _P],
     "gqaoa_sweep": [_P, _I, _I, _I, _P, _P, _I, _I, _P, _I, _I, _P, _P, _SZ, _P],
     "gqaoa_mlp_param_count": [_I, _I, _I, _SZP],
@@ -213,6 +215,16 @@ def gqaoa_reduced_sweep(hist, hist_stride, n, batch, gammas, betas, angles, p, o
                         ws_bytes, stream):
     _call("gqaoa_reduced_sweep", hist, hist_stride, n, batch, gammas, betas, angles, p, out, best,
           ws, ws_bytes, stream)
+
+
+def gqaoa_fairness_workspace_size(n, runs, targets) -> int:
+    return _size("gqaoa_fairness_workspace_size", n, runs, targets)
+
+
+def gqaoa_fairness(shots, runs, shots_per_run, cost, n, target, targets, chi2_crit, min_draws,
+                   to_all, to_reject, ws, ws_bytes, stream):
+    _call("gqaoa_fairness", shots, runs, shots_per_run, cost, n, target, targets, chi2_crit,
+          min_draws, to_all, to_reject, ws, ws_bytes, stream)
 
 
 def gqaoa_mlp_param_count(d_in, d_h, d_out) -> int:

@@ -205,6 +205,24 @@ def reduced_sweep(hist: torch.Tensor, n: int, gammas, betas, p: int, best: bool 
     return out, bst
 
 
+def fairness(shots: torch.Tensor, runs: int, cost: torch.Tensor, n: int, target: int,
+             targets: int, chi2_crit: float, min_draws: int, ws: torch.Tensor | None = None):
+    """Section IV's fair-sampling metrics per run (gqaoa_fairness): shots
+    [runs * shots_per_run] (run r = shots r, r + runs, ...), the target cost
+    class and its size. Returns (to_all [runs], to_reject [runs]) int64."""
+    _require_cuda(shots, cost)
+    device = shots.device
+    per_run = shots.numel() // runs
+    to_all = torch.empty(runs, dtype=torch.int64, device=device)
+    to_rej = torch.empty(runs, dtype=torch.int64, device=device)
+    need = C.gqaoa_fairness_workspace_size(n, runs, targets)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, device)
+    C.gqaoa_fairness(_ptr(shots), runs, per_run, _ptr(cost), n, target, targets, float(chi2_crit),
+                     int(min_draws), _ptr(to_all), _ptr(to_rej), _ptr(ws), ws.numel(), _stream())
+    return to_all, to_rej
+
+
 class GQAOAObjective(torch.autograd.Function):
     """L(gamma, beta) = P(C=0) or <H_P> of Eq. 3, differentiable in the angles.
 
