@@ -73,6 +73,16 @@ WORKLOADS = {
                                  "L-BFGS-B with statevector adjoint gradients, fewest "
                                  "single-angle-pair rounds to a Max-SAT probability D >= 50 % on "
                                  "the statevector"),
+    # Section IV's fair-sampling metrics on a satisfiable instance at the
+    # protocol's fewest-rounds angles: one step = sample runs x shots_per_run
+    # shots and compute both metrics for every run
+    "fairness": dict(kind="fairness", n=14, d_lo=3.8, d_hi=4.2, runs=100_000, shots_per_run=2048,
+                     alpha=0.05, seed=3,
+                     desc="one satisfiable random 3-SAT instance n=14, d in (3.8, 4.2), at the "
+                          "protocol's fewest single-angle-pair rounds to P >= 50 %; 100000 runs "
+                          "of 2048 shots from gqaoa_sample; shots to see every solution and "
+                          "chi-square draws (alpha 0.05, from 5 M draws) to reject uniform "
+                          "solution sampling, per run"),
     # the profiling case: same recipe, state (512 MiB) still far larger than L2
     "profile": dict(n=26, m=109, p=8, shots=100_000, seed=0,
                     desc="random 3-SAT n=26 m=109 (d~4.2) seed 0, p=8 random angles, 1e5 shots"),
@@ -794,6 +804,121 @@ def run_protocol(args, wl):
     return 0
 
 
+def run_fairness(args, wl):
+    """Workload "fairness": Section IV's metrics. Metric: shots per second
+    through sampling and both metrics (whole step)."""
+    import scipy.stats
+    import torch
+
+    from paper_2402_02585_gb300 import core
+    from paper_2402_02585_gb300.protocol import Protocol, satisfiable_shapes
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    n, m, iseed, lits, cost, hist = satisfiable_shapes(1, wl["seed"] + rank, [wl["n"]], wl["d_lo"],
+                                                       wl["d_hi"])[0]
+    res = Protocol(cost, hist, n, m).min_rounds(S=0.5, p_max=64)
+    state, out, _ = core.evolve(cost, n, m, res.gammas, res.betas)
+    M = int(hist[0].item())
+    runs, per_run = wl["runs"], wl["shots_per_run"]
+    shots_n = runs * per_run
+    crit = float(scipy.stats.chi2.ppf(1 - wl["alpha"], max(M - 1, 1)))
+    shots = torch.empty(shots_n, dtype=torch.int64, device="cuda")
+    ws_s = core.workspace(C_size_sample(n, shots_n), "cuda")
+    ws_f = core.workspace(C_size_fair(n, runs, M), "cuda")
+
+    def step(i, ev=None):
+        core.sample(state, n, 1000 + i, shots_n, ws=ws_s, out=shots)
+        if ev is not None:
+            ev.record()
+        return core.fairness(shots, runs, cost, n, 0, M, crit, 5 * M, ws=ws_f)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    for i in range(args.steps):
+        evs[i][0].record()
+        ta, tr = step(args.warmup + i, evs[i][1])
+        evs[i][2].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_samp = sum(a.elapsed_time(b) for a, b, c in evs) / 1e3
+    t_fair = sum(b.elapsed_time(c) for a, b, c in evs) / 1e3
+    el = evs[0][0].elapsed_time(evs[-1][2]) / 1e3
+    ta = ta.cpu().numpy()
+    tr = tr.cpu().numpy()
+    done = ta[ta > 0].astype(np.float64)
+    # the sampler is issue-bound: per shot Philox4x32-10 (~110 instructions), the
+    # tile search (~15), the chunk search in shared memory (~40) and the walk
+    # over 16 weights (~80), ~255 thread-instructions (derived from the source)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = 4 * 32 * sms * 2.07e9 / 255
+    samp_rate = shots_n * args.steps / t_samp
+    if rank == 0:
+        print(json.dumps({
+            "metric": "fair-sampling shots/s", "value": shots_n * args.steps / el, "unit": "shots/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64 state, f64 CDF, int64 metrics", "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": n, "m": m, "solutions": M, "p": res.p,
+                       "P": float(out[0].item()), "runs": runs, "shots_per_run": per_run},
+            "roofline": {"bound": "alu", "achieved": samp_rate, "peak": alu_peak,
+                         "unit": "shots/s", "frac": samp_rate / alu_peak,
+                         "kernel": f"gqaoa_sample, resident-tile path ({100 * t_samp / el:.0f} % "
+                                   "of the step)",
+                         "peak_derivation": "4 warp-instr/clk/SM x 32 x SMs x 2.07 GHz / 255 "
+                                            "instructions per shot"},
+            "metrics_kernel_shots_per_s": shots_n * args.steps / t_fair,
+            "shots_to_all_solutions": {"mean": float(done.mean()),
+                                       "ci95": float(1.96 * done.std() / math.sqrt(done.size)),
+                                       "completed_runs": int(done.size)},
+            "shots_to_reject_fairness": {"median": float(np.median(tr[tr > 0]))
+                                         if (tr > 0).any() else None,
+                                         "rejected_runs": int((tr > 0).sum())},
+            "cpu_baseline": cpu_fairness_baseline(wl, n, lits, res, runs) if world == 1 else None,
+            # sampler: tile sums, tile scan, shot tiles, count scan, scatter, resolve;
+            # metrics: labels, runs
+            "gpu_launches": 8 * args.steps, "clocks": clk}), flush=True)
+    return 0
+
+
+def C_size_sample(n, shots):
+    from paper_2402_02585_gb300 import _capi as C
+    return C.gqaoa_sample_workspace_size(n, shots)
+
+
+def C_size_fair(n, runs, M):
+    from paper_2402_02585_gb300 import _capi as C
+    return C.gqaoa_fairness_workspace_size(n, runs, M)
+
+
+def cpu_fairness_baseline(wl, n, lits, res, runs):
+    """The oracle on a bounded sample: statevector, its sampler and both
+    metrics for 200 runs of the stream."""
+    import scipy.stats
+
+    from oracle import fairness as ofair
+    from oracle import statevector as sv
+    if os.environ.get("GQAOA_BENCH_NO_CPU") == "1":
+        return None
+    cost, hist = sv.cost_table(lits, n)
+    M = int(hist[0])
+    k = 200
+    t0 = time.perf_counter()
+    psi = sv.evolve(cost, n, res.gammas, res.betas)
+    shots = sv.sample(psi, n, 1000, k * wl["shots_per_run"])
+    crit = float(scipy.stats.chi2.ppf(1 - wl["alpha"], max(M - 1, 1)))
+    ofair.run_metrics(shots, cost, 0, k, crit, 5 * M)
+    t = time.perf_counter() - t0
+    return {"value": k * wl["shots_per_run"] / t, "unit": "shots/s", "cores": _oracle_threads(),
+            "kind": "oracle", "sample": f"{k} runs of {wl['shots_per_run']} shots: statevector, "
+                                        "sampler and both metrics (plain Python loop)"}
+
+
 def cpu_protocol_baseline(wl, shapes):
     """The protocol oracle (FP64 cost-class model for the grid and the
     gradients) on the first two instances, on the host cores."""
@@ -875,6 +1000,8 @@ def main():
         return run_grad(args, wl)
     if wl.get("kind") == "protocol":
         return run_protocol(args, wl)
+    if wl.get("kind") == "fairness":
+        return run_fairness(args, wl)
     if wl.get("kind") == "sweep":
         return run_sweep(args, wl)
     return run_ours(args, wl)

@@ -17,7 +17,9 @@
 // finds its tile by binary search, shots are bucketed by tile with a
 // counting sort, and pass 2 re-reads only the tiles that received shots,
 // rebuilds the same chunk sums and scan, and resolves each shot by a binary
-// search over chunks and a walk over 16 amplitudes. Both passes compute the
+// search over chunks and a walk over 16 amplitudes. With at most eight tiles
+// (n <= 15) every CTA keeps all tile scans in shared memory and resolves its
+// shots directly instead (same arithmetic, no bucketing). Both passes compute the
 // tile totals with the same instructions in the same order, so the levels
 // agree exactly; a target that rounding puts past the end of a chunk or tile
 // goes to its last amplitude of nonzero weight.
@@ -259,7 +261,65 @@ resolve_kernel(const float4 *__restrict__ st, uint64_t ntiles, const double *__r
   }
 }
 
-// Small states (N <= 2048): one CTA, exact FP64 CDF in shared memory.
+// Few tiles (N <= kResidentTiles x 4096): shots far outnumber tiles, and the
+// counting sort would serialise on a handful of counters. Every CTA instead
+// rebuilds the chunk scans of all tiles in shared memory (the instructions of
+// pass 2) and resolves a grid-stride range of shots directly, with the same
+// tile search and chunk walk, so the shots are the ones pass 2 would give.
+constexpr int kResidentTiles = 8;
+struct TileScan {
+  float w[kWarps * 32 * kPad];
+  double incl[kChunksPerTile];
+  float chunk[kChunksPerTile];
+};
+
+__global__ void __launch_bounds__(kThreads)
+resolve_resident_kernel(const float4 *__restrict__ st, uint64_t ntiles,
+                        const double *__restrict__ prefix, uint64_t seed, int64_t shots,
+                        uint64_t *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  TileScan *ts = reinterpret_cast<TileScan *>(s_dyn);  // [ntiles]
+  __shared__ double s_wtot[kWarps];
+  for (uint64_t t = 0; t < ntiles; ++t) {
+    float c;
+    tile_chunk_scan(st, t, ts[t].w, ts[t].incl, s_wtot, &c);
+    ts[t].chunk[threadIdx.x] = c;
+    __syncthreads();
+  }
+  const double total = prefix[ntiles];
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < shots;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const double u = shot_uniform(seed, (uint64_t)s);
+    const uint32_t t = find_tile(prefix, ntiles, u * total);
+    const TileScan &T = ts[t];
+    const double r = u * total - prefix[t];
+    int lo = 0, hi = kChunksPerTile;  // chunk: smallest i with incl[i] > r
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (T.incl[mid] > r) hi = mid; else lo = mid + 1;
+    }
+    if (lo >= kChunksPerTile) {  // rounding past the tile end
+      lo = kChunksPerTile - 1;
+      while (lo > 0 && !(T.chunk[lo] > 0.f)) --lo;
+    }
+    const double rl = r - (lo > 0 ? T.incl[lo - 1] : 0.0);
+    const int warp_of = lo >> 5, lane_of = lo & 31;
+    const float *row = T.w + warp_of * 32 * kPad + lane_of * kPad;
+    float cum = 0.f;
+    int pick = -1, last_nz = 0;
+    for (int i = 0; i < kChunk; ++i) {
+      const float wi = row[i];
+      cum += wi;
+      if (wi > 0.f) last_nz = i;
+      if (pick < 0 && (double)cum > rl) pick = i;
+    }
+    if (pick < 0) pick = last_nz;
+    out[s] = t * kSampTile + (uint64_t)warp_of * 512 + (uint64_t)lane_of * kChunk + pick;
+  }
+}
+
+// Small states (N <= 2048): exact FP64 CDF in shared memory, built by every
+// CTA, shots in a grid-stride range.
 __global__ void __launch_bounds__(kThreads)
 sample_small_kernel(const float2 *__restrict__ st, int n, uint64_t seed, int64_t shots,
                     uint64_t *__restrict__ out) {
@@ -279,7 +339,8 @@ sample_small_kernel(const float2 *__restrict__ st, int n, uint64_t seed, int64_t
   }
   __syncthreads();
   const double total = s_cdf[N - 1];
-  for (int64_t s = threadIdx.x; s < shots; s += blockDim.x) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < shots;
+       s += (int64_t)gridDim.x * blockDim.x) {
     const double t = shot_uniform(seed, (uint64_t)s) * total;
     int lo = 0, hi = N - 1;
     while (lo < hi) {
@@ -348,9 +409,16 @@ extern "C" int gqaoa_sample(const void *state, int n, uint64_t seed, int64_t sho
   if (shots == 0) return GQAOA_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint64_t N = 1ull << n;
+  const int sms0 = sm_count() > 0 ? sm_count() : 152;
+  // CTAs for a grid-stride pass over the shots (each builds its own tables)
+  const auto shot_ctas = [&](int per_sm) {
+    const int64_t need = (shots + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)sms0 * per_sm;
+    return (unsigned)(need < cap ? need : cap);
+  };
   if (N < (uint64_t)kSampTile) {
-    sample_small_kernel<<<1, kThreads, 0, st>>>(static_cast<const float2 *>(state), n, seed, shots,
-                                                out_idx);
+    sample_small_kernel<<<shot_ctas(8), kThreads, 0, st>>>(static_cast<const float2 *>(state), n,
+                                                           seed, shots, out_idx);
     GQ_CHECK_LAUNCH();
     return GQAOA_OK;
   }
@@ -360,12 +428,26 @@ extern "C" int gqaoa_sample(const void *state, int n, uint64_t seed, int64_t sho
   SampleWs w;
   sample_ws_layout(ntiles, shots, static_cast<char *>(ws), &w);
   const float4 *s4 = static_cast<const float4 *>(state);
-  const int sms = sm_count() > 0 ? sm_count() : 152;
+  const int sms = sms0;
   const unsigned tgrid = (unsigned)(ntiles < (uint64_t)sms * 8 ? ntiles : (uint64_t)sms * 8);
   tile_sum_kernel<<<tgrid, kThreads, 0, st>>>(s4, ntiles, w.tsum);
   GQ_CHECK_LAUNCH();
   scan_tiles_kernel<<<1, 1024, 0, st>>>(w.tsum, ntiles, w.prefix);
   GQ_CHECK_LAUNCH();
+  if (ntiles <= (uint64_t)kResidentTiles) {
+    const size_t dyn = sizeof(TileScan) * ntiles;
+    if (cudaFuncSetAttribute(resolve_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dyn) != cudaSuccess)
+      return GQAOA_ECUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resolve_resident_kernel, kThreads,
+                                                      dyn) != cudaSuccess || per_sm < 1)
+      return GQAOA_ECUDA;
+    resolve_resident_kernel<<<shot_ctas(per_sm), kThreads, dyn, st>>>(s4, ntiles, w.prefix, seed,
+                                                                       shots, out_idx);
+    GQ_CHECK_LAUNCH();
+    return GQAOA_OK;
+  }
   GQ_CUDA(cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * ntiles * 2, st));
   const unsigned sgrid =
       (unsigned)((shots + kThreads - 1) / kThreads < (int64_t)sms * 16 ? (shots + kThreads - 1) / kThreads
