@@ -853,10 +853,10 @@ def run_fairness(args, wl):
     tr = tr.cpu().numpy()
     done = ta[ta > 0].astype(np.float64)
     # the sampler is issue-bound: per shot Philox4x32-10, the tile search, the
-    # chunk search in shared memory and the walk over 16 weights execute ~486
+    # chunk search and the search of the chunk's running sums execute ~326
     # thread-instructions (ncu, profiles/sampler_and_fairness.md)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_peak = 4 * 32 * sms * 2.07e9 / 486
+    alu_peak = 4 * 32 * sms * 2.07e9 / 326
     samp_rate = shots_n * args.steps / t_samp
     if rank == 0:
         print(json.dumps({
@@ -870,7 +870,7 @@ def run_fairness(args, wl):
                          "unit": "shots/s", "frac": samp_rate / alu_peak,
                          "kernel": f"gqaoa_sample, resident-tile path ({100 * t_samp / el:.0f} % "
                                    "of the step)",
-                         "peak_derivation": "4 warp-instr/clk/SM x 32 x SMs x 2.07 GHz / 486 "
+                         "peak_derivation": "4 warp-instr/clk/SM x 32 x SMs x 2.07 GHz / 326 "
                                             "instructions per shot (measured count)"},
             "metrics_kernel_shots_per_s": shots_n * args.steps / t_fair,
             "shots_to_all_solutions": {"mean": float(done.mean()),

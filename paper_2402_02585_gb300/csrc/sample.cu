@@ -265,13 +265,45 @@ resolve_kernel(const float4 *__restrict__ st, uint64_t ntiles, const double *__r
 // counting sort would serialise on a handful of counters. Every CTA instead
 // rebuilds the chunk scans of all tiles in shared memory (the instructions of
 // pass 2) and resolves a grid-stride range of shots directly, with the same
-// tile search and chunk walk, so the shots are the ones pass 2 would give.
+// tile search. The walk over a chunk's 16 weights is replaced by a binary
+// search over their FP32 running sums, computed once in the walk's order:
+// the sums never decrease, so the first sum above the target is the index
+// the walk would stop at, and the shots are the ones pass 2 would give.
 constexpr int kResidentTiles = 8;
 struct TileScan {
-  float w[kWarps * 32 * kPad];
+  float cum[kWarps * 32 * kPad];  // per chunk (row of kPad): running sums of its 16 weights
   double incl[kChunksPerTile];
   float chunk[kChunksPerTile];
+  uint8_t last_nz[kChunksPerTile];  // last weight > 0 in the chunk (0 if none)
 };
+
+__device__ __forceinline__ uint64_t resolve_shot(const TileScan *ts, const double *s_prefix,
+                                                 uint64_t ntiles, double total, uint64_t seed,
+                                                 uint64_t s) {
+  const double u = shot_uniform(seed, s);
+  const uint32_t t = find_tile(s_prefix, ntiles, u * total);
+  const TileScan &T = ts[t];
+  const double r = u * total - s_prefix[t];
+  int lo = 0, hi = kChunksPerTile;  // chunk: smallest i with incl[i] > r
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (T.incl[mid] > r) hi = mid; else lo = mid + 1;
+  }
+  if (lo >= kChunksPerTile) {  // rounding past the tile end
+    lo = kChunksPerTile - 1;
+    while (lo > 0 && !(T.chunk[lo] > 0.f)) --lo;
+  }
+  const double rl = r - (lo > 0 ? T.incl[lo - 1] : 0.0);
+  const int warp_of = lo >> 5, lane_of = lo & 31;
+  const float *row = T.cum + warp_of * 32 * kPad + lane_of * kPad;
+  int a = 0, b = kChunk;  // first running sum above rl
+  while (a < b) {
+    const int mid = (a + b) >> 1;
+    if ((double)row[mid] > rl) b = mid; else a = mid + 1;
+  }
+  const int pick = a < kChunk ? a : (int)T.last_nz[lo];
+  return t * kSampTile + (uint64_t)warp_of * 512 + (uint64_t)lane_of * kChunk + pick;
+}
 
 __global__ void __launch_bounds__(kThreads)
 resolve_resident_kernel(const float4 *__restrict__ st, uint64_t ntiles,
@@ -280,41 +312,35 @@ resolve_resident_kernel(const float4 *__restrict__ st, uint64_t ntiles,
   extern __shared__ __align__(16) unsigned char s_dyn[];
   TileScan *ts = reinterpret_cast<TileScan *>(s_dyn);  // [ntiles]
   __shared__ double s_wtot[kWarps];
+  __shared__ double s_prefix[kResidentTiles + 1];
+  if (threadIdx.x <= ntiles) s_prefix[threadIdx.x] = prefix[threadIdx.x];
   for (uint64_t t = 0; t < ntiles; ++t) {
     float c;
-    tile_chunk_scan(st, t, ts[t].w, ts[t].incl, s_wtot, &c);
+    tile_chunk_scan(st, t, ts[t].cum, ts[t].incl, s_wtot, &c);
     ts[t].chunk[threadIdx.x] = c;
-    __syncthreads();
-  }
-  const double total = prefix[ntiles];
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < shots;
-       s += (int64_t)gridDim.x * blockDim.x) {
-    const double u = shot_uniform(seed, (uint64_t)s);
-    const uint32_t t = find_tile(prefix, ntiles, u * total);
-    const TileScan &T = ts[t];
-    const double r = u * total - prefix[t];
-    int lo = 0, hi = kChunksPerTile;  // chunk: smallest i with incl[i] > r
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (T.incl[mid] > r) hi = mid; else lo = mid + 1;
-    }
-    if (lo >= kChunksPerTile) {  // rounding past the tile end
-      lo = kChunksPerTile - 1;
-      while (lo > 0 && !(T.chunk[lo] > 0.f)) --lo;
-    }
-    const double rl = r - (lo > 0 ? T.incl[lo - 1] : 0.0);
-    const int warp_of = lo >> 5, lane_of = lo & 31;
-    const float *row = T.w + warp_of * 32 * kPad + lane_of * kPad;
-    float cum = 0.f;
-    int pick = -1, last_nz = 0;
+    // this thread's chunk: weights -> running sums (the walk's FP32 order)
+    float *row = ts[t].cum + (threadIdx.x >> 5) * 32 * kPad + (threadIdx.x & 31) * kPad;
+    float run = 0.f;
+    int last = 0;
     for (int i = 0; i < kChunk; ++i) {
       const float wi = row[i];
-      cum += wi;
-      if (wi > 0.f) last_nz = i;
-      if (pick < 0 && (double)cum > rl) pick = i;
+      run += wi;
+      if (wi > 0.f) last = i;
+      row[i] = run;
     }
-    if (pick < 0) pick = last_nz;
-    out[s] = t * kSampTile + (uint64_t)warp_of * 512 + (uint64_t)lane_of * kChunk + pick;
+    ts[t].last_nz[threadIdx.x] = (uint8_t)last;
+    __syncthreads();
+  }
+  const double total = s_prefix[ntiles];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // two shots per thread in flight: independent chains of shared-memory loads
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < shots; s += 2 * stride) {
+    const int64_t s2 = s + stride;
+    const uint64_t z = resolve_shot(ts, s_prefix, ntiles, total, seed, (uint64_t)s);
+    uint64_t z2 = 0;
+    if (s2 < shots) z2 = resolve_shot(ts, s_prefix, ntiles, total, seed, (uint64_t)s2);
+    out[s] = z;
+    if (s2 < shots) out[s2] = z2;
   }
 }
 
