@@ -109,11 +109,25 @@ class SweepPlan:
         return sum(st[3].shape[0] * self.A * self.p * (1 << st[1]) for st in self.steps
                    if st[0] == kind)
 
-    def run(self, kinds=("onchip", "l2", "stream")):
+    @staticmethod
+    def lane(step) -> str:
+        """"big" for the persistent launches on 16-CTA clusters (one per GPC:
+        the cluster-resident path and the on-chip path at its largest n),
+        "small" for the other persistent launches, "stream" otherwise."""
+        kind, n = step[0], step[1]
+        if kind == "l2":
+            return "big"
+        if kind == "onchip":
+            apt = step[5][1] or (16 if n <= 18 else 32)
+            return "big" if (1 << n) // apt >= 16 * 1024 else "small"
+        return "stream"
+
+    def run(self, kinds=("onchip", "l2", "stream"), lanes=("big", "small", "stream")):
         s = torch.cuda.current_stream().cuda_stream
-        for kind, n, m, cost, out, extra in self.steps:
+        for step in self.steps:
+            kind, n, m, cost, out, extra = step
             B = cost.shape[0]
-            if kind not in kinds:
+            if kind not in kinds or self.lane(step) not in lanes:
                 continue
             if kind in ("onchip", "l2"):
                 ws, apt = extra
@@ -134,7 +148,8 @@ class SweepPlan:
 
     def capture(self):
         """Record the persistent gqaoa_sweep launches into one CUDA graph per
-        path ("onchip", "l2"), after one eager warm-up run of everything."""
+        path ("onchip", "l2") and one per lane ("big", "small"), after one
+        eager warm-up run of everything."""
         self.run()
         torch.cuda.synchronize()
         self.graphs = {}
@@ -144,11 +159,43 @@ class SweepPlan:
                 with torch.cuda.graph(g):
                     self.run(kinds=(kind,))
                 self.graphs[kind] = g
+        self.lane_graphs = {}
+        for lane in ("big", "small"):
+            if any(self.lane(st) == lane for st in self.steps):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    self.run(lanes=(lane,))
+                self.lane_graphs[lane] = g
+        # the 16-CTA-cluster lane on a high-priority stream: when SMs free up,
+        # the scheduler places its pending clusters before the smaller CTAs
+        lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") \
+            else (0, -1)
+        self._big = torch.cuda.Stream(self.device, priority=hi)
+        self._side = torch.cuda.Stream(self.device, priority=lo)
         return self.graphs
 
     def replay(self):
+        """One path after the other (each path's launches alone on the GPU)."""
         for g in self.graphs.values():
             g.replay()
+        self.run(kinds=("stream",))
+        return self.out
+
+    def replay_concurrent(self):
+        """The 16-CTA-cluster launches first, on a high-priority stream, and
+        the other persistent launches on a low-priority one: a 16-CTA
+        cluster occupies a whole GPC and only seven are resident on GB300, so
+        the smaller items fill the SMs those clusters leave idle. Items are
+        independent; the outputs are those of replay()."""
+        main = torch.cuda.current_stream(self.device)
+        fork = torch.cuda.Event()
+        fork.record(main)
+        for lane, stream in (("big", self._big), ("small", self._side)):
+            if lane in self.lane_graphs:
+                stream.wait_event(fork)
+                with torch.cuda.stream(stream):
+                    self.lane_graphs[lane].replay()
+                main.wait_stream(stream)
         self.run(kinds=("stream",))
         return self.out
 

@@ -178,3 +178,30 @@ def test_sweep_plan_mixed_buckets_and_graph_replay():
     torch.cuda.synchronize()
     for n in eager:
         assert torch.equal(plan.out[n], eager[n])
+
+
+def test_sweep_plan_concurrent_replay_matches_sequential():
+    # a 16-CTA-cluster bucket (n = 20, cluster-resident) beside smaller
+    # on-chip buckets: the two-stream replay must give the same bits
+    from paper_2402_02585_gb300.sweep import SweepPlan
+    p, rounds = 6, [1, 6]
+    buckets = {}
+    for n, B in ((11, 2), (15, 1), (20, 1)):
+        m = int(math.floor(4.2 * n + 0.5))
+        cs = [core.build_cost(instances.random_3sat(n, m, 1500 + 10 * n + i), n)[0]
+              for i in range(B)]
+        buckets[n] = (torch.stack(cs), m)
+    rng = np.random.default_rng(5)
+    G = rng.uniform(0, np.pi, 9)
+    Bt = rng.uniform(0, np.pi, 9)
+    table = {11: {"path": "onchip"}, 15: {"path": "onchip", "apt": 32}, 20: {"path": "l2"}}
+    plan = SweepPlan(buckets, G, Bt, p, rounds, table=table)
+    assert [plan.lane(st) for st in plan.steps] == ["small", "small", "big"]
+    eager = {n: o.clone() for n, o in plan.run().items()}
+    plan.capture()
+    for o in plan.out.values():
+        o.fill_(-1.0)
+    plan.replay_concurrent()
+    torch.cuda.synchronize()
+    for n in eager:
+        assert torch.equal(plan.out[n], eager[n])
