@@ -148,6 +148,34 @@ class Protocol:
         return res
 
 
+def min_rounds_many(protocols, workers: int = 8, retry_p_max: int | None = None,
+                    **kwargs) -> list:
+    """Protocol.min_rounds for many instances at once: each search is a
+    sequence of small GPU calls and host optimiser steps, so `workers` host
+    threads, each on its own CUDA stream, keep the GPU busy while the others
+    wait on the host. Instances are independent, so the results are those of
+    calling min_rounds one instance after another. An instance that does not
+    reach S within p_max is searched again up to retry_p_max (if given)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    device = protocols[0].cost.device if protocols else None
+    streams = [torch.cuda.Stream(device) for _ in range(max(1, workers))]
+
+    def one(i):
+        with torch.cuda.stream(streams[i % len(streams)]):
+            r = protocols[i].min_rounds(**kwargs)
+            if r.p is None and retry_p_max:
+                first = r
+                r = protocols[i].min_rounds(**dict(kwargs, p_max=retry_p_max))
+                r.launches += first.launches
+                r.evaluations += first.evaluations
+            torch.cuda.current_stream().synchronize()
+            return r
+
+    with ThreadPoolExecutor(max_workers=len(streams)) as pool:
+        return list(pool.map(one, range(len(protocols))))
+
+
 def satisfiable_shapes(count: int, seed: int, n_values, d_lo: float = 2.0, d_hi: float = 4.5,
                        satisfiable: bool = True):
     """Section III's workloads: n uniform over n_values, density uniform on

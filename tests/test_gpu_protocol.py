@@ -74,3 +74,17 @@ def test_protocol_full_angles_not_worse_than_single():
     assert single.p is not None and full.p is not None
     assert full.p <= single.p
     assert full.prob >= 0.5
+
+
+def test_protocol_many_instances_on_threads_matches_one_by_one():
+    from paper_2402_02585_gb300.protocol import min_rounds_many
+    G, B = instances.protocol_grid(3)
+    prots = []
+    for n, m, seed in ((8, 30, 11), (9, 36, 3), (10, 40, 2), (8, 30, 11)):
+        cost, hist = core.build_cost(instances.random_3sat(n, m, seed), n)
+        prots.append(Protocol(cost, hist, n, m))
+    one = [p.min_rounds(S=0.5, p_max=24, grid=(G, B)) for p in prots]
+    many = min_rounds_many(prots, workers=3, S=0.5, p_max=24, grid=(G, B))
+    for a, b in zip(one, many):
+        assert a.p == b.p and a.prob == b.prob and a.energy == b.energy
+        assert np.array_equal(a.gammas, b.gammas) and np.array_equal(a.betas, b.betas)
