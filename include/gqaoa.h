@@ -159,7 +159,8 @@ int gqaoa_sample_workspace_size(int n, int64_t shots, size_t *bytes);
  *            (out1 << 32 | out0) scaled by 2^-53.
  * state   device complex64 [2^n]; must have nonzero norm.
  * seed    the Philox key.
- * shots   0 <= shots <= 2^32.
+ * shots   0 <= shots < 2^32 (shot numbers and per-tile shot offsets are
+ *         32-bit).
  * out_idx device uint64 [shots] written: z of each shot, in shot order.
  * ws      device workspace of gqaoa_sample_workspace_size(n, shots) bytes.
  */

@@ -420,7 +420,7 @@ using namespace gq;
 
 extern "C" int gqaoa_sample_workspace_size(int n, int64_t shots, size_t *bytes) {
   if (!bytes) return GQAOA_EINVAL;
-  if (n < 1 || n > GQAOA_MAX_N || shots < 0 || shots > (1ll << 32)) return GQAOA_ERANGE;
+  if (n < 1 || n > GQAOA_MAX_N || shots < 0 || shots >= (1ll << 32)) return GQAOA_ERANGE;
   const uint64_t N = 1ull << n;
   *bytes = N < (uint64_t)kSampTile ? 256 : sample_ws_layout(N / kSampTile, shots, nullptr, nullptr);
   return GQAOA_OK;
@@ -429,7 +429,7 @@ extern "C" int gqaoa_sample_workspace_size(int n, int64_t shots, size_t *bytes) 
 extern "C" int gqaoa_sample(const void *state, int n, uint64_t seed, int64_t shots,
                             uint64_t *out_idx, void *ws, size_t ws_bytes, void *stream) {
   gq::NvtxRange nvtx_range("gqaoa_sample");
-  if (n < 1 || n > GQAOA_MAX_N || shots < 0 || shots > (1ll << 32)) return GQAOA_ERANGE;
+  if (n < 1 || n > GQAOA_MAX_N || shots < 0 || shots >= (1ll << 32)) return GQAOA_ERANGE;
   if (!state || (shots > 0 && !out_idx)) return GQAOA_EINVAL;
   if (!aligned16(state) || (out_idx && !aligned8(out_idx))) return GQAOA_EINVAL;
   if (shots == 0) return GQAOA_OK;

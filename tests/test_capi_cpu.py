@@ -109,6 +109,14 @@ def test_sample_and_grad_reject_bad_arguments_before_launch():
     with pytest.raises(C.GQAOAError) as e:
         C.gqaoa_sample(fake, 20, 1, 100, fake, fake, 16, None)
     assert e.value.status == C.GQAOA_ENOMEM
+    # shot numbers and per-tile offsets are 32-bit: 2^32 shots is out of range
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_sample(fake, 20, 1, 1 << 32, fake, fake, 1 << 40, None)
+    assert e.value.status == C.GQAOA_ERANGE
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_sample_workspace_size(20, 1 << 32)
+    assert e.value.status == C.GQAOA_ERANGE
+    assert C.gqaoa_sample_workspace_size(20, (1 << 32) - 1) > 0
     with pytest.raises(C.GQAOAError) as e:
         C.gqaoa_grad(fake, 16, 60, fake, fake, 4, 7, fake, fake, fake, fake, 1 << 40, None)
     assert e.value.status == C.GQAOA_EINVAL

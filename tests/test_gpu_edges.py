@@ -1,8 +1,10 @@
 """Edge and extreme cases of the CUDA path against the oracle (GPU).
 
 Degenerate instances (no clauses, tiny n), a single round, a zero state,
-single-amplitude sampling, and the largest case a test can afford: n = 30
-(8 GiB complex64 state, 1 GiB cost table checked whole and bit-exact).
+single-amplitude sampling, n = 30 (8 GiB complex64 state, 1 GiB cost table
+checked whole and bit-exact), and the largest n the library accepts
+(GQAOA_MAX_N = 34: 128 GiB state) on an instance whose histogram has a
+closed form.
 """
 
 import math
@@ -12,6 +14,7 @@ import pytest
 import torch
 
 from oracle import reduced, statevector as sv
+from paper_2402_02585_gb300 import _capi as C
 from paper_2402_02585_gb300 import core, instances
 
 pytestmark = pytest.mark.gpu
@@ -82,6 +85,58 @@ def test_largest_case_n30():
     z = torch.as_tensor(rng.integers(0, 1 << n, 1 << 20), device="cuda")
     got = state[z].cpu().numpy()
     want = f[ref_cost[z.cpu().numpy()]]
-    assert np.max(np.abs(got - want)) < 1e-5
+    # amplitudes are ~2^(-n/2): the bound is relative to the largest one
+    assert np.max(np.abs(got - want)) < 1e-5 * np.max(np.abs(f))
     assert abs(out[0].item() - reduced.readout(ref_hist, f)[0]) < 1e-6
     assert abs(out[2].item() - 1.0) < 1e-5
+
+
+def test_largest_n_closed_form_histogram():
+    # n = GQAOA_MAX_N: 2^34 amplitudes (128 GiB complex64 state, 16 GiB cost
+    # table), so every index above 2^32 is exercised. With variable-disjoint
+    # clauses C(z) is a sum of m independent indicators, each 1 on one of the
+    # 8 assignments of its three variables (Eq. 1), hence exactly
+    #   h[c] = binom(m, c) 7^(m - c) 2^(n - 3m),
+    # and the cost-class model on that histogram gives every amplitude.
+    n = C.GQAOA_MAX_N
+    if torch.cuda.get_device_properties(0).total_memory < (200 << 30):
+        pytest.skip("needs about 150 GiB of device memory")
+    m = n // 3
+    rng = np.random.default_rng(34)
+    # distinct variables, the lowest and the highest among them
+    rest = rng.permutation(np.setdiff1d(np.arange(n), [0, n - 1, n // 2]))
+    var = np.concatenate([[0, n - 1, n // 2], rest])[: 3 * m]
+    sign = rng.choice([-1, 1], size=3 * m)
+    lits = ((var + 1) * sign).reshape(m, 3).astype(np.int32)
+    want_hist = np.array([math.comb(m, c) * 7 ** (m - c) * 2 ** (n - 3 * m) for c in range(m + 1)],
+                         dtype=np.uint64)
+    assert int(want_hist.sum()) == 1 << n
+    cost, hist = core.build_cost(lits, n)
+    assert np.array_equal(hist.cpu().numpy().astype(np.uint64), want_hist)
+
+    z = rng.integers(0, 1 << n, 4096, dtype=np.int64)
+    z[:4] = [0, (1 << n) - 1, 1 << (n - 1), (1 << (n - 1)) - 1]
+    zd = torch.as_tensor(z, device="cuda")
+    ref_cost = np.array([sv.cost_at(lits, int(v)) for v in z])
+    assert np.array_equal(cost[zd].cpu().numpy(), ref_cost)
+
+    g, b = instances.random_angles(2, 34)
+    state, out, _ = core.evolve(cost, n, m, g, b)
+    f = reduced.evolve(want_hist, g, b)
+    got = state[zd].cpu().numpy()
+    assert np.max(np.abs(got - f[ref_cost])) < 1e-5 * np.max(np.abs(f))
+    o = out.cpu().numpy()
+    assert abs(o[0] - reduced.readout(want_hist, f)[0]) < 1e-6
+    assert abs(o[2] - 1.0) < 1e-5
+
+    # shots: cost-class frequencies against the class weights h[c] |f(c)|^2
+    shots = 100000
+    zs = core.sample(state, n, seed=34, shots=shots)
+    assert int(zs.min()) >= 0 and int(zs.max()) < (1 << n)
+    cls = np.bincount(cost[zs].cpu().numpy(), minlength=m + 1)
+    w = want_hist.astype(np.float64) * np.abs(f) ** 2
+    w /= w.sum()
+    exp = shots * w
+    assert np.all(np.abs(cls - exp) <= 5 * np.sqrt(exp * (1 - w)) + 1), (cls, exp)
+    del state, cost, zs, zd
+    torch.cuda.empty_cache()

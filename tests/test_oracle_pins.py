@@ -68,6 +68,18 @@ def test_cost_single_clause_counts():
             assert hist.tolist() == [(1 << n) - (1 << (n - 3)), 1 << (n - 3)]
 
 
+@pytest.mark.parametrize("n", [6, 10, 13, 17])
+def test_disjoint_clauses_binomial_histogram(n):
+    # Clauses on disjoint variable triples violate independently, each on 1 of
+    # its 8 assignments: h[c] = binom(m, c) 7^(m - c) 2^(n - 3m).
+    m = n // 3
+    rng = np.random.default_rng(n)
+    var = rng.permutation(n)[: 3 * m]
+    lits = ((var + 1) * rng.choice([-1, 1], size=3 * m)).reshape(m, 3).astype(np.int32)
+    want = [math.comb(m, c) * 7 ** (m - c) * 2 ** (n - 3 * m) for c in range(m + 1)]
+    assert sv.histogram(lits, n).tolist() == want
+
+
 def test_cost_at_matches_table():
     lits = instances.random_3sat(11, 46, 5)
     cost, _ = sv.cost_table(lits, 11)
