@@ -720,6 +720,7 @@ def run_protocol(args, wl):
     quadratic speedup: x ~ 0.5), and the cost-class grid kernel's rate."""
     import torch
 
+    from paper_2402_02585_gb300 import _capi as C
     from paper_2402_02585_gb300 import core, instances
     from paper_2402_02585_gb300.protocol import Protocol, min_rounds_many, satisfiable_shapes
 
@@ -743,14 +744,29 @@ def run_protocol(args, wl):
 
     for _ in range(args.warmup):
         one_pass()
-    # the grid kernel alone, on the full pi/180 grid of the first instance
+    # the grid call alone (phase tables + cost-class kernel, no argmin), on
+    # the full pi/180 grid of the first instance, buffers resident
     G, B = instances.protocol_grid()
     n0, _, h0, _ = prots[0]
+    dev = torch.device("cuda", local)
+    h0d = h0.reshape(1, -1).contiguous()
+    Gd = torch.as_tensor(G, dtype=torch.float64, device=dev)
+    Bd = torch.as_tensor(B, dtype=torch.float64, device=dev)
+    grid_out = torch.empty((1, len(G), wl["p_max"], 3), dtype=torch.float64, device=dev)
+    grid_ws = core.workspace(C.gqaoa_reduced_sweep_workspace_size(len(G)), dev)
+    st = torch.cuda.current_stream().cuda_stream
+
+    def grid_call():
+        C.gqaoa_reduced_sweep(h0d.data_ptr(), h0d.shape[1], n0, 1, Gd.data_ptr(), Bd.data_ptr(),
+                              len(G), wl["p_max"], grid_out.data_ptr(), None, grid_ws.data_ptr(),
+                              grid_ws.numel(), st)
+
+    grid_call()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
     for _ in range(5):
-        core.reduced_sweep(h0[None], n0, G, B, wl["p_max"])
+        grid_call()
     e1.record()
     torch.cuda.synchronize()
     t_grid = e0.elapsed_time(e1) / 5 / 1e3
@@ -776,10 +792,12 @@ def run_protocol(args, wl):
     ok = np.isfinite(pm)
     slope = float(np.polyfit(np.log(1 / pr[ok]), np.log(pm[ok]), 1)[0]) if ok.sum() > 2 else None
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    # grid kernel: per item-round a warp issues ~14 FP32 instructions per class
-    # slot and ~125 for its three warp butterflies (derived from the source)
-    J = (int(h0.numel()) + 31) // 32
-    alu_peak = 4 * sms * 2.07e9 / (14 * J + 125)
+    # grid call: the cost-class arithmetic is 14 FP32 instructions per class
+    # and round (phase and mixer 8, readout 6); the ceiling issues them at
+    # 4 warp-instructions (128 lanes) per clock per SM, so an item-round of
+    # m + 1 classes costs 14 (m + 1) / 32 warp-instructions
+    classes = int(h0.numel())
+    alu_peak = 4 * sms * 2.07e9 / (14 * classes / 32)
     grid_rate = len(G) * wl["p_max"] / t_grid
     if rank == 0:
         print(json.dumps({
@@ -792,10 +810,12 @@ def run_protocol(args, wl):
                        "p_max": wl["p_max"], "host_threads": workers},
             "roofline": {"bound": "alu", "achieved": grid_rate, "peak": alu_peak,
                          "unit": "item-rounds/s", "frac": grid_rate / alu_peak,
-                         "kernel": f"reduced_sweep_kernel<{J}>: pi/180 grid ({len(G)} angle "
-                                   f"pairs) x p = {wl['p_max']}, n = {n0}, {t_grid * 1e3:.2f} ms",
-                         "peak_derivation": "4 warp-instr/clk/SM x SMs x 2.07 GHz / "
-                                            f"(14 x {J} + 125) instructions per item-round"},
+                         "kernel": f"gqaoa_reduced_sweep (phase tables + reduced_sweep_kernel): "
+                                   f"pi/180 grid ({len(G)} angle pairs) x p = {wl['p_max']}, "
+                                   f"n = {n0}, {classes} classes, {t_grid * 1e3:.3f} ms",
+                         "peak_derivation": "4 warp-instr/clk/SM x SMs x 2.07 GHz / (14 FP32 "
+                                            f"instructions x {classes} classes / 32 lanes) per "
+                                            "item-round"},
             "p_min": [None if r.p is None else int(r.p) for r in results],
             "target": target,
             "random_guess_probability": [float(x) for x in pr],

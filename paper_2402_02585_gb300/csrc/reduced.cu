@@ -11,12 +11,12 @@
 // the paper's protocol (Appendix C: a pi/180 grid, or 4000 random points
 // above n = 20), while the statevector kernels remain the evolution itself.
 //
-// One warp per (instance, angle point) item; lane l holds the classes
-// c = l + 32 j. Amplitudes are scaled by sqrt(N) (u = sqrt(N) f, u_0 = 1) and
+// One group of 1..16 lanes per (instance, angle point) item, each lane
+// holding 12 or 16 classes. Amplitudes are scaled by sqrt(N) (u = sqrt(N) f, u_0 = 1) and
 // the weights are w[c] = h[c] / N, so S / N = sum_c w[c] g(c) and
 // P = w[0] |u(0)|^2 do not depend on N. Complex64 amplitudes with FP64 phase
 // tables rounded to complex64 (as the statevector path); the sums over
-// classes are FP32 per lane and double-float across the warp.
+// classes are FP32 per lane and double-float across the lane group.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -43,9 +43,12 @@ struct ReducedArgs {
   int p;
 };
 
-__device__ __forceinline__ void df_warp32(float &hi, float &lo) {
+// Double-float butterfly over the kG lanes of an aligned lane group (every
+// lane of the group ends with the same sum, in the same order for all groups).
+template <int kG>
+__device__ __forceinline__ void df_group(float &hi, float &lo) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = kG / 2; o > 0; o >>= 1) {
     const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
     const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
     float s, e;
@@ -55,13 +58,24 @@ __device__ __forceinline__ void df_warp32(float &hi, float &lo) {
   }
 }
 
-template <int kJ>
+// One item = (instance, angle point) per group of kG lanes (a power of two up
+// to 16; 32 / kG items per warp); lane l of a group holds the classes
+// c = l + kG j, j < kJ, so kG kJ >= hist_stride. Small groups keep the
+// per-round butterflies short: a round costs kJ classes of arithmetic per
+// lane and log2(kG) butterfly steps for each of its three sums.
+template <int kG, int kJ>
 __global__ void __launch_bounds__(256) reduced_sweep_kernel(const __grid_constant__ ReducedArgs a) {
-  const int lane = threadIdx.x & 31;
+  constexpr int kPerWarp = 32 / kG;
+  const int lane = threadIdx.x & 31, gl = lane % kG, g0 = lane - gl;
   const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
   const double inv_n = ldexp(1.0, -a.n);
-  for (uint64_t item = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-       item < a.nitems; item += nwarps) {
+  for (uint64_t base = ((uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * kPerWarp;
+       base < a.nitems; base += nwarps * kPerWarp) {
+    // a group past the last item repeats it (the shuffles need every lane)
+    // and writes nothing
+    const uint64_t want = base + (uint64_t)(lane / kG);
+    const bool valid = want < a.nitems;
+    const uint64_t item = valid ? want : a.nitems - 1;
     const uint64_t b = item / (uint64_t)a.A;
     const int ai = (int)(item % (uint64_t)a.A);
     const uint64_t *h = a.hist + b * (uint64_t)a.stride;
@@ -70,18 +84,24 @@ __global__ void __launch_bounds__(256) reduced_sweep_kernel(const __grid_constan
     int cs = 256;  // lowest non-empty class
 #pragma unroll
     for (int j = 0; j < kJ; ++j) {
-      const int c = lane + 32 * j;
+      const int c = gl + kG * j;
       const uint64_t hc = c < a.stride ? h[c] : 0ull;
       w[j] = (float)((double)hc * inv_n);
       T[j] = a.phase[(size_t)ai * 256 + c];
       u[j] = make_float2(1.f, 0.f);
-      const unsigned bal = __ballot_sync(0xffffffffu, hc != 0ull);
-      if (bal != 0u && cs == 256) cs = 32 * j + __ffs(bal) - 1;
+      if (hc != 0ull && c < cs) cs = c;
     }
+#pragma unroll
+    for (int o = kG / 2; o > 0; o >>= 1) cs = min(cs, __shfl_xor_sync(0xffffffffu, cs, o));
+    const int cs_lane = g0 + (cs & (kG - 1));
     const double2 al = a.alpha[ai];
     const float alr = (float)al.x, ali = (float)al.y;
     float2 ad = make_float2(0.f, 0.f);  // pending mixer add
     double *o = a.out + item * (uint64_t)a.p * 3;
+    // round k's readouts are group-uniform; lane k mod kG of the group keeps
+    // them and the group converts them to FP64 and stores them every kG
+    // rounds, so every lane of a warp does the (slow) FP64 conversions at once
+    float kp = 0.f, ke = 0.f, kel = 0.f, kd = 0.f;
     for (int k = 0; k < a.p; ++k) {
       // phase (with the previous round's mixer add), then S / N
       float sr = 0.f, si = 0.f;
@@ -93,15 +113,15 @@ __global__ void __launch_bounds__(256) reduced_sweep_kernel(const __grid_constan
         si = fmaf(w[j], x.y, si);
       }
       float lr = 0.f, li = 0.f;
-      df_warp32(sr, lr);
-      df_warp32(si, li);
+      df_group<kG>(sr, lr);
+      df_group<kG>(si, li);
       const float Sr = sr + lr, Si = si + li;
       const float2 am = make_float2(alr * Sr - ali * Si, alr * Si + ali * Sr);
       // readouts of f_k = g_k + a_k
       float e = 0.f, pz = 0.f, dm = 0.f;
 #pragma unroll
       for (int j = 0; j < kJ; ++j) {
-        const int c = lane + 32 * j;
+        const int c = gl + kG * j;
         const float yr = u[j].x + am.x, yi = u[j].y + am.y;
         const float q = w[j] * fmaf(yr, yr, yi * yi);
         e = fmaf((float)c, q, e);
@@ -109,13 +129,18 @@ __global__ void __launch_bounds__(256) reduced_sweep_kernel(const __grid_constan
         if (c == cs) dm = q;
       }
       float el = 0.f;
-      df_warp32(e, el);
-      pz = __shfl_sync(0xffffffffu, pz, 0);
-      dm = __shfl_sync(0xffffffffu, dm, cs & 31);
-      if (lane == 0) {
-        o[3 * k] = (double)pz;
-        o[3 * k + 1] = (double)e + (double)el;
-        o[3 * k + 2] = (double)dm;
+      df_group<kG>(e, el);
+      pz = __shfl_sync(0xffffffffu, pz, g0);
+      dm = __shfl_sync(0xffffffffu, dm, cs_lane);
+      const int kr = k & (kG - 1);
+      if (kr == gl) { kp = pz; ke = e; kel = el; kd = dm; }
+      if (kr == kG - 1 || k + 1 == a.p) {
+        const int kk = k - kr + gl;  // this lane's pending round
+        if (valid && kk <= k) {
+          o[3 * kk] = (double)kp;
+          o[3 * kk + 1] = (double)ke + (double)kel;
+          o[3 * kk + 2] = (double)kd;
+        }
       }
       ad = am;
     }
@@ -123,17 +148,23 @@ __global__ void __launch_bounds__(256) reduced_sweep_kernel(const __grid_constan
 }
 
 // best[b][k] = the angle point with the smallest <H_P> after round k + 1
-// (the smallest index among equal values). One CTA per (b, k).
-__global__ void __launch_bounds__(256) reduced_argmin_kernel(const double *__restrict__ out,
-                                                             int A, int p,
-                                                             int32_t *__restrict__ best) {
-  __shared__ double s_v[8];
-  __shared__ int s_i[8];
+// (the smallest index among equal values). One CTA of kArgThreads per (b, k);
+// the reads of one (b, k) are p * 24 bytes apart, so each thread keeps
+// several in flight.
+constexpr int kArgThreads = 1024;
+
+__global__ void __launch_bounds__(kArgThreads) reduced_argmin_kernel(const double *__restrict__ out,
+                                                                     int A, int p,
+                                                                     int32_t *__restrict__ best) {
+  __shared__ double s_v[kArgThreads / 32];
+  __shared__ int s_i[kArgThreads / 32];
   const int b = blockIdx.x / p, k = blockIdx.x % p;
+  const double *col = out + ((size_t)b * A * p + k) * 3 + 1;
   double bv = INFINITY;
   int bi = 0x7fffffff;
-  for (int ai = threadIdx.x; ai < A; ai += blockDim.x) {
-    const double v = out[(((size_t)b * A + ai) * p + k) * 3 + 1];
+#pragma unroll 8
+  for (int ai = threadIdx.x; ai < A; ai += kArgThreads) {
+    const double v = col[(size_t)ai * p * 3];
     if (v < bv) { bv = v; bi = ai; }  // ascending ai: the first minimum stays
   }
 #pragma unroll
@@ -146,21 +177,22 @@ __global__ void __launch_bounds__(256) reduced_argmin_kernel(const double *__res
   if (lane == 0) { s_v[warp] = bv; s_i[warp] = bi; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+    for (int w = 1; w < kArgThreads / 32; ++w)
       if (s_v[w] < bv || (s_v[w] == bv && s_i[w] < bi)) { bv = s_v[w]; bi = s_i[w]; }
     best[(size_t)b * p + k] = bi == 0x7fffffff ? -1 : bi;
   }
 }
 
-template <int kJ>
+template <int kG, int kJ>
 int launch_reduced(const ReducedArgs &args, cudaStream_t st) {
-  auto kernel = reduced_sweep_kernel<kJ>;
+  auto kernel = reduced_sweep_kernel<kG, kJ>;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess ||
       per_sm < 1)
     return GQAOA_ECUDA;
   uint64_t blocks = (uint64_t)per_sm * (uint64_t)sm_count();
-  const uint64_t need = (args.nitems + 7) / 8;
+  const uint64_t per_block = 8ull * (32 / kG);  // items per CTA pass
+  const uint64_t need = (args.nitems + per_block - 1) / per_block;
   if (need < blocks) blocks = need;
   kernel<<<(unsigned)blocks, 256, 0, st>>>(args);
   GQ_CHECK_LAUNCH();
@@ -218,19 +250,20 @@ extern "C" int gqaoa_reduced_sweep(const uint64_t *hist, int hist_stride, int n,
   args.n = n;
   args.A = angles;
   args.p = p;
-  switch ((hist_stride + 31) / 32) {
-    case 1: rc = launch_reduced<1>(args, st); break;
-    case 2: rc = launch_reduced<2>(args, st); break;
-    case 3: rc = launch_reduced<3>(args, st); break;
-    case 4: rc = launch_reduced<4>(args, st); break;
-    case 5: rc = launch_reduced<5>(args, st); break;
-    case 6: rc = launch_reduced<6>(args, st); break;
-    case 7: rc = launch_reduced<7>(args, st); break;
-    default: rc = launch_reduced<8>(args, st); break;
-  }
+  // lane groups as small as 12 or 16 classes per lane allow: per item-round
+  // a group issues about kG (14 kJ + 30 log2 kG) / 32 warp instructions
+  if (hist_stride <= 16) rc = launch_reduced<1, 16>(args, st);
+  else if (hist_stride <= 32) rc = launch_reduced<2, 16>(args, st);
+  else if (hist_stride <= 48) rc = launch_reduced<4, 12>(args, st);
+  else if (hist_stride <= 64) rc = launch_reduced<4, 16>(args, st);
+  else if (hist_stride <= 96) rc = launch_reduced<8, 12>(args, st);
+  else if (hist_stride <= 128) rc = launch_reduced<8, 16>(args, st);
+  else if (hist_stride <= 192) rc = launch_reduced<16, 12>(args, st);
+  else rc = launch_reduced<16, 16>(args, st);
   if (rc || !best) return rc;
   if ((uint64_t)batch * (uint64_t)p > 0x7fffffffull) return GQAOA_ERANGE;
-  reduced_argmin_kernel<<<(unsigned)((uint64_t)batch * p), 256, 0, st>>>(out, angles, p, best);
+  reduced_argmin_kernel<<<(unsigned)((uint64_t)batch * p), kArgThreads, 0, st>>>(out, angles, p,
+                                                                          best);
   GQ_CHECK_LAUNCH();
   return GQAOA_OK;
 }

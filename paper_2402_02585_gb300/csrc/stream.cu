@@ -184,37 +184,99 @@ static size_t ws_layout(const Geometry &g, int p, bool grad, char *base, Ws *w,
 }
 
 // ---------------------------------------------------------------------------
-// K10: phase tables and mixer coefficients, FP64 sincos rounded to complex64
+// K10: phase tables and mixer coefficients
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) phase_table_kernel(const double *__restrict__ gammas,
-                                                               const double *__restrict__ betas,
-                                                               int64_t bp, float2 *__restrict__ phase,
-                                                               double2 *__restrict__ alpha) {
-  // One table per CTA at a time: 32 FP64 sincos give e^{-i gamma r} and
-  // e^{-i gamma 16 q} (r, q = 0..15), and T[16 q + r] is their FP64 product
-  // rounded to FP32. The product is within a few FP64 ulps of the directly
-  // evaluated exponential, far below the FP32 rounding of the table, and it
-  // costs 8x fewer sincos (FP64 is a small fraction of GB300's FP32 rate).
-  __shared__ double2 s_e[32];  // [0, 16): e^{-i gamma r}; [16, 32): e^{-i gamma 16 q}
-  for (int64_t k = blockIdx.x; k < bp; k += gridDim.x) {
-    if (threadIdx.x < 32) {
-      const int j = threadIdx.x;
-      const double c = j < 16 ? (double)j : 16.0 * (double)(j - 16);
-      double s, co;
-      sincos(gammas[k] * c, &s, &co);
-      s_e[j] = make_double2(co, -s);
-      if (j == 0) {
-        double sb, cb;
-        sincos(betas[k], &sb, &cb);
-        alpha[k] = make_double2(cb - 1.0, -sb);
+// T[c] = e^{-i gamma c} for c < 256, rounded to complex64, and
+// alpha = e^{-i beta} - 1 in FP64. GB300's FP64 rate is a small fraction of
+// its FP32 rate, so FP64 is spent only on three sincos per table (gamma,
+// 16 gamma, beta); the powers e^{-i gamma r} and e^{-i 16 gamma q}
+// (r, q < 16) and the entries T[16 q + r] = e^{-i 16 gamma q} e^{-i gamma r}
+// are formed in double-float arithmetic (FP32 pairs, ~2^-44 relative error
+// after the 15 multiplications of a power chain), whose leading word is the
+// entry rounded to FP32.
+struct DFv {
+  float hi, lo;
+};
+__device__ __forceinline__ DFv dfv_from(double x) {
+  const float h = (float)x;
+  return DFv{h, (float)(x - (double)h)};
+}
+// Renormalise a + b with |a| >= |b| (Dekker's Fast2Sum).
+__device__ __forceinline__ DFv dfv_fast(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return DFv{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DFv dfv_mul(DFv a, DFv b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);  // the rounding error of p, exactly
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return dfv_fast(p, e);
+}
+__device__ __forceinline__ DFv dfv_add(DFv a, DFv b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return dfv_fast(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+struct DFc {
+  DFv x, y;  // x + i y
+};
+__device__ __forceinline__ DFc dfc_mul(const DFc &a, const DFc &b) {
+  const DFv yy = dfv_mul(a.y, b.y);
+  return DFc{dfv_add(dfv_mul(a.x, b.x), DFv{-yy.hi, -yy.lo}),
+             dfv_add(dfv_mul(a.x, b.y), dfv_mul(a.y, b.x))};
+}
+__device__ __forceinline__ DFc dfc_load(float4 v) { return DFc{{v.x, v.y}, {v.z, v.w}}; }
+
+constexpr int kPhaseWarps = 2;  // warps per CTA; each owns 32 tables at a time
+
+// Lane l of a warp takes table t0 + l for the sincos and its power chains,
+// which go to the warp's shared rows ([table][power], padded so the lanes'
+// float4 stores spread over the banks); then the warp writes the 32 tables
+// one after the other, 32 consecutive entries per store.
+__global__ void __launch_bounds__(kPhaseWarps * 32)
+phase_table_kernel(const double *__restrict__ gammas, const double *__restrict__ betas,
+                   int64_t count, float2 *__restrict__ phase, double2 *__restrict__ alpha) {
+  __shared__ float4 s_pow[kPhaseWarps][32][33];  // [r] = e^{-i gamma r}, [16 + q] = e^{-i 16 gamma q}
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4(*P)[33] = s_pow[warp];
+  const int64_t nblk = (count + 31) / 32;
+  for (int64_t blk = (int64_t)blockIdx.x * kPhaseWarps + warp; blk < nblk;
+       blk += (int64_t)gridDim.x * kPhaseWarps) {
+    const int64_t t = blk * 32 + lane;
+    const bool live = t < count;
+    const double g = live ? gammas[t] : 0.0;
+    double s1, c1, s16, c16;
+    sincos(g, &s1, &c1);
+    sincos(16.0 * g, &s16, &c16);  // 16 g is exact
+    if (live) {
+      double sb, cb;
+      sincos(betas[t], &sb, &cb);
+      alpha[t] = make_double2(cb - 1.0, -sb);
+    }
+    const DFc e1 = {dfv_from(c1), dfv_from(-s1)}, e16 = {dfv_from(c16), dfv_from(-s16)};
+    DFc a1 = {{1.f, 0.f}, {0.f, 0.f}}, a16 = a1;
+#pragma unroll 1
+    for (int r = 0; r < 16; ++r) {
+      P[lane][r] = make_float4(a1.x.hi, a1.x.lo, a1.y.hi, a1.y.lo);
+      P[lane][16 + r] = make_float4(a16.x.hi, a16.x.lo, a16.y.hi, a16.y.lo);
+      a1 = dfc_mul(a1, e1);
+      a16 = dfc_mul(a16, e16);
+    }
+    __syncwarp();
+    const int tn = (int)(count - blk * 32 < 32 ? count - blk * 32 : 32);
+#pragma unroll 1
+    for (int tt = 0; tt < tn; ++tt) {
+      const DFc er = dfc_load(P[tt][lane & 15]);
+      float2 *dst = phase + (blk * 32 + tt) * 256;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        // entry c = lane + 32 i = 16 q + r with r = lane & 15, q = (lane >> 4) + 2 i
+        const DFc v = dfc_mul(dfc_load(P[tt][16 + (lane >> 4) + 2 * i]), er);
+        dst[lane + 32 * i] = make_float2(v.x.hi, v.y.hi);
       }
     }
-    __syncthreads();
-    const int c = threadIdx.x;
-    const double2 e1 = s_e[c & 15], e16 = s_e[16 + (c >> 4)];
-    phase[k * 256 + c] = make_float2((float)(e16.x * e1.x - e16.y * e1.y),
-                                     (float)(e16.x * e1.y + e16.y * e1.x));
-    __syncthreads();  // s_e is rewritten for the next table
+    __syncwarp();  // the rows are rewritten for the next block
   }
 }
 
@@ -964,8 +1026,12 @@ static double *parts_half(const Ws &w, int i) { return w.parts + (size_t)(i & 1)
 // `count` angle pairs (also used by the on-chip sweep).
 int phase_tables(const double *gammas, const double *betas, int64_t count, float2 *phase,
                  double2 *alpha, cudaStream_t st) {
-  int64_t grid = count < 4096 ? count : 4096;
-  phase_table_kernel<<<(unsigned)grid, kThreads, 0, st>>>(gammas, betas, count, phase, alpha);
+  const int64_t nblk = (count + 31) / 32;  // blocks of 32 tables, one per warp
+  const int64_t cap = (int64_t)sm_count() * 8;
+  int64_t grid = (nblk + kPhaseWarps - 1) / kPhaseWarps;
+  if (grid > cap) grid = cap;
+  phase_table_kernel<<<(unsigned)grid, kPhaseWarps * 32, 0, st>>>(gammas, betas, count, phase,
+                                                                  alpha);
   GQ_CHECK_LAUNCH();
   return GQAOA_OK;
 }

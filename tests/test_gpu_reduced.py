@@ -6,7 +6,8 @@ with oracle.reduced.readouts_trace (itself pinned against the statevector
 oracle) within the complex64 tolerance used for the statevector path: P and
 D within 1e-6, and <H_P> = sum_c c q_c (q the cost distribution of the state,
 summing to 1) within 1e-6 times the largest cost value m, on satisfiable and unsatisfiable
-instances, class counts that do and do not fill whole warps, and batches of
+instances, class counts for every lane-group shape (1 to 16 lanes per item,
+groups filled or not, warps with idle groups), and batches of
 instances with different clause counts; the statevector sweep (an
 independent kernel family) must give the same P; the per-round argmin must be
 the first minimum of the written <H_P>.
@@ -39,11 +40,16 @@ def _hist_rows(shapes, seed0):
 
 
 @pytest.mark.parametrize("n,ms,A,p", [
-    (6, [10, 40], 7, 12),        # 11 / 41 classes: partial warps
+    (8, [5], 6, 10),             # 6 classes: one lane per item, 6 of a warp's 32 items
+    (9, [12], 5, 10),            # 13 classes: one lane per item
+    (7, [20, 30], 5, 12),        # 31 classes: lane pairs
+    (6, [10, 40], 7, 12),        # 11 / 41 classes: groups of 4 lanes, partly filled
     (10, [42, 60, 90], 5, 20),   # density 9: unsatisfiable, D != P
     (14, [59], 9, 40),
     (20, [84, 100], 4, 16),
     (24, [101], 3, 8),
+    (12, [180], 3, 10),          # 181 classes: groups of 16 lanes, 12 classes each
+    (11, [230], 2, 6),           # 231 classes: groups of 16 lanes, 16 classes each
 ])
 def test_reduced_sweep_matches_oracle(n, ms, A, p):
     H = _hist_rows([(n, m) for m in ms], 3000 + n)
