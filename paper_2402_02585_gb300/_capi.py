@@ -124,7 +124,8 @@ def strerror(status: int) -> str:
 
 
 def _call(name: str, *args) -> None:
-    rc = getattr(load(), name)(*args)
+    lib = _lib if _lib is not None else load()  # no lock once loaded
+    rc = getattr(lib, name)(*args)
     if rc != GQAOA_OK:
         raise GQAOAError(name, rc, strerror(rc))
 

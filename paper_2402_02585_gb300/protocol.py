@@ -58,6 +58,39 @@ def grid_for(n: int, seed: int = 0):
     return instances.protocol_random_angles(4000, seed)
 
 
+class _EnergyGrad:
+    """<H_P> and its adjoint gradient at a fixed depth p with resident
+    buffers: the angles go to the device in one copy from pinned host memory
+    and the value and both gradients come back in one (an L-BFGS-B search
+    makes hundreds of these small calls, so their host cost matters)."""
+
+    def __init__(self, prot: "Protocol", p: int):
+        dev = prot.cost.device
+        self.p = p
+        self.d_ang = torch.empty(2 * p, dtype=torch.float64, device=dev)      # [gammas | betas]
+        self.d_out = torch.empty(1 + 2 * p, dtype=torch.float64, device=dev)  # [value | dg | db]
+        self.h_ang = torch.empty(2 * p, dtype=torch.float64, pin_memory=True)
+        self.h_out = torch.empty(1 + 2 * p, dtype=torch.float64, pin_memory=True)
+        self.a_ang = self.h_ang.numpy()
+        self.a_out = self.h_out.numpy()
+        self.ws = core.workspace(C.gqaoa_grad_workspace_size(prot.n, p), dev)
+        ang, out = self.d_ang.data_ptr(), self.d_out.data_ptr()
+        self.args = (prot.cost.data_ptr(), prot.n, prot.m, ang, ang + 8 * p, p,
+                     core.objective_code("energy"), out, out + 8, out + 8 + 8 * p,
+                     self.ws.data_ptr(), self.ws.numel())
+
+    def __call__(self, gammas, betas):
+        p = self.p
+        self.a_ang[:p] = gammas
+        self.a_ang[p:] = betas
+        st = torch.cuda.current_stream()
+        self.d_ang.copy_(self.h_ang, non_blocking=True)
+        C.gqaoa_grad(*self.args, st.cuda_stream)
+        self.h_out.copy_(self.d_out, non_blocking=True)
+        st.synchronize()  # also frees the pinned buffers for the next call
+        return float(self.a_out[0]), self.a_out[1:1 + p].copy(), self.a_out[1 + p:].copy()
+
+
 class Protocol:
     """The protocol for one instance: cost [2^n] uint8 and hist [m + 1] int64
     on the device (core.build_cost)."""
@@ -66,26 +99,26 @@ class Protocol:
         core._require_cuda(cost, hist)
         self.cost, self.hist, self.n, self.m = cost, hist, n, m
         self._ws = {}
+        self._grad_calls = {}
         self.evaluations = 0
         self.launches = 0
         self._small = (1 << n) < 4096  # one CTA per state: phase tables + one or two kernels
         h = hist.cpu().numpy()
         self.min_class = int(np.nonzero(h)[0][0])  # 0 when satisfiable
 
-    def _workspace(self, kind: str, p: int) -> torch.Tensor:
-        key = (kind, p)
-        if key not in self._ws:
-            size = (C.gqaoa_grad_workspace_size(self.n, p) if kind == "grad"
-                    else C.gqaoa_evolve_workspace_size(self.n, p))
-            self._ws[key] = core.workspace(size, self.cost.device)
-        return self._ws[key]
+    def _evolve_workspace(self, p: int) -> torch.Tensor:
+        if p not in self._ws:
+            self._ws[p] = core.workspace(C.gqaoa_evolve_workspace_size(self.n, p), self.cost.device)
+        return self._ws[p]
 
     def energy_and_grad(self, gammas, betas):
-        v, dg, db = core.grad(self.cost, self.n, self.m, gammas, betas, "energy",
-                              ws=self._workspace("grad", len(gammas)))
+        p = len(gammas)
+        call = self._grad_calls.get(p)
+        if call is None:
+            call = self._grad_calls[p] = _EnergyGrad(self, p)
         self.evaluations += 1
-        self.launches += 3 if self._small else 2 * len(gammas) + 3
-        return float(v), dg.cpu().numpy(), db.cpu().numpy()
+        self.launches += 3 if self._small else 2 * p + 3
+        return call(gammas, betas)
 
     def refine(self, gammas0, betas0, single: bool):
         """L-BFGS-B on <H_P> (relative change 1e-6). Returns (gammas, betas,
@@ -112,7 +145,7 @@ class Protocol:
     def probability(self, gammas, betas, cls: int = 0) -> float:
         """Probability of cost value cls in the evolved state (statevector)."""
         _, out, _ = core.evolve(self.cost, self.n, self.m, gammas, betas,
-                                ws=self._workspace("evolve", len(gammas)), readout_class=cls)
+                                ws=self._evolve_workspace(len(gammas)), readout_class=cls)
         self.launches += 2 if self._small else len(gammas) + 3
         return float(out[0].item())
 
