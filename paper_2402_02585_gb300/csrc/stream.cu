@@ -789,12 +789,54 @@ struct SmallArgs {
   unsigned target;       // the cost class of out[0] and of the projector objective
 };
 
+// Sum of two FP32 values per thread over the CTA, every thread getting the
+// FP64 results: a double-float butterfly per warp, then the warps' partials
+// in warp order, also in double-float. The rounds of the small-state kernels
+// reduce this way so that their per-amplitude work stays on the FP32 pipe
+// (GB300's FP64 rate is a small fraction of it). scr: 2 kWarps float2.
+__device__ __forceinline__ double2 block_sum_df2(float x, float y, float2 *scr) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float xl = 0.f, yl = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float xh2 = __shfl_xor_sync(0xffffffffu, x, o), xl2 = __shfl_xor_sync(0xffffffffu, xl, o);
+    const float yh2 = __shfl_xor_sync(0xffffffffu, y, o), yl2 = __shfl_xor_sync(0xffffffffu, yl, o);
+    float s, e;
+    two_sum(x, xh2, s, e);
+    x = s;
+    xl = __fadd_rn(__fadd_rn(xl, xl2), e);
+    two_sum(y, yh2, s, e);
+    y = s;
+    yl = __fadd_rn(__fadd_rn(yl, yl2), e);
+  }
+  __syncthreads();  // scr is free (its last readers are past this point)
+  if (lane == 0) {
+    scr[warp] = make_float2(x, xl);
+    scr[kWarps + warp] = make_float2(y, yl);
+  }
+  __syncthreads();
+  float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const float2 px = scr[w], py = scr[kWarps + w];
+    float s, e;
+    two_sum(hx, px.x, s, e);
+    hx = s;
+    lx = __fadd_rn(lx, __fadd_rn(e, px.y));
+    two_sum(hy, py.x, s, e);
+    hy = s;
+    ly = __fadd_rn(ly, __fadd_rn(e, py.y));
+  }
+  return make_double2((double)hx + (double)lx, (double)hy + (double)ly);
+}
+
 // One round of the small-state kernel on a thread's amplitudes; writes the
-// round's record (S_k, a_k), the checkpoint chi_k if asked, and *P = P(C=0).
+// round's record (S_k, a_k), the checkpoint chi_k if asked, and, if P is
+// given, *P = P(C=0) of the round's state.
 __device__ __forceinline__ void small_round(float2 (&s)[kSmallPer], const unsigned (&c)[kSmallPer],
                                             const float2 *T, const double2 al, int N, double inv_n,
-                                            double *s_scr, float2 *ck, double *rec, double *P) {
-  double lr = 0.0, li = 0.0;
+                                            float2 *s_scr, float2 *ck, double *rec, double *P) {
+  float lr = 0.f, li = 0.f;
 #pragma unroll
   for (int j = 0; j < kSmallPer; ++j) {
     const int z = threadIdx.x + j * kThreads;
@@ -805,25 +847,26 @@ __device__ __forceinline__ void small_round(float2 (&s)[kSmallPer], const unsign
       li += s[j].y;
     }
   }
-  const double Sre = block_sum(lr, s_scr);
-  const double Sim = block_sum(li, s_scr);
+  const double2 S = block_sum_df2(lr, li, s_scr);
+  const double Sre = S.x, Sim = S.y;
   const double ar = (al.x * Sre - al.y * Sim) * inv_n, ai = (al.x * Sim + al.y * Sre) * inv_n;
   const float2 af = make_float2((float)ar, (float)ai);
-  double lp = 0.0;
+  float lp = 0.f;
 #pragma unroll
   for (int j = 0; j < kSmallPer; ++j) {
     const int z = threadIdx.x + j * kThreads;
     if (z < N) {
       s[j] = make_float2(s[j].x + af.x, s[j].y + af.y);
-      if (c[j] == 0) lp += (double)s[j].x * s[j].x + (double)s[j].y * s[j].y;
+      if (P && c[j] == 0) lp += fmaf(s[j].x, s[j].x, s[j].y * s[j].y);
     }
   }
-  *P = block_sum(lp, s_scr);
+  if (P) *P = block_sum_df2(lp, 0.f, s_scr).x;
   if (threadIdx.x == 0) { rec[0] = Sre; rec[1] = Sim; rec[2] = ar; rec[3] = ai; }
 }
 
 __global__ void __launch_bounds__(kThreads) evolve_small_kernel(const SmallArgs a) {
   __shared__ double s_scr[kWarps];
+  __shared__ float2 s_df[2 * kWarps];
   const int b = blockIdx.x;
   const int N = 1 << a.n;
   const double inv_n = 1.0 / (double)N;
@@ -840,9 +883,10 @@ __global__ void __launch_bounds__(kThreads) evolve_small_kernel(const SmallArgs 
   }
   for (int k = 0; k < a.p; ++k) {
     const size_t bk = (size_t)b * a.p + k;
-    double P;
+    double P = 0.0;
     float2 *ck = a.ckpt ? a.ckpt + ((size_t)k * a.B + b) * N : nullptr;
-    small_round(s, c, a.phase + bk * 256, a.alpha[bk], N, inv_n, s_scr, ck, a.record + 4 * bk, &P);
+    small_round(s, c, a.phase + bk * 256, a.alpha[bk], N, inv_n, s_df, ck, a.record + 4 * bk,
+                a.trace ? &P : nullptr);
     if (a.trace && threadIdx.x == 0) a.trace[bk] = P;
   }
   double lp = 0.0, le = 0.0, ln = 0.0;
@@ -869,6 +913,7 @@ __global__ void __launch_bounds__(kThreads)
 grad_small_kernel(const SmallArgs a, int objective, double *__restrict__ value,
                   double *__restrict__ dgamma, double *__restrict__ dbeta) {
   __shared__ double s_scr[kWarps];
+  __shared__ float2 s_df[2 * kWarps];
   const int b = blockIdx.x;
   const int N = 1 << a.n;
   const double inv_n = 1.0 / (double)N;
@@ -895,31 +940,32 @@ grad_small_kernel(const SmallArgs a, int objective, double *__restrict__ value,
   if (threadIdx.x == 0) value[b] = L;
   for (int k = a.p - 1; k >= 0; --k) {
     const size_t bk = (size_t)b * a.p + k;
-    double lr = 0.0, li = 0.0;
+    float lr = 0.f, li = 0.f;
 #pragma unroll
     for (int j = 0; j < kSmallPer; ++j) {
       const int z = threadIdx.x + j * kThreads;
       if (z < N) { lr += l[j].x; li += l[j].y; }
     }
-    const double Lr = block_sum(lr, s_scr), Li = block_sum(li, s_scr);
+    const double2 Ls = block_sum_df2(lr, li, s_df);
+    const double Lr = Ls.x, Li = Ls.y;
     const double2 al = a.alpha[bk];
     const float2 bv = make_float2((float)((al.x * Lr + al.y * Li) * inv_n),
                                   (float)((al.x * Li - al.y * Lr) * inv_n));
     const float2 *T = a.phase + bk * 256;
     const float2 *chi = a.ckpt + ((size_t)k * a.B + b) * N;
-    double g = 0.0;
+    float g = 0.f;
 #pragma unroll
     for (int j = 0; j < kSmallPer; ++j) {
       const int z = threadIdx.x + j * kThreads;
       if (z < N) {
         const float2 mu = make_float2(l[j].x + bv.x, l[j].y + bv.y);
         const float2 x = chi[z];
-        g += (double)c[j] * ((double)mu.x * x.y - (double)mu.y * x.x);
+        g = fmaf((float)c[j], fmaf(mu.x, x.y, -mu.y * x.x), g);
         const float2 t = T[c[j]];
         l[j] = make_float2(fmaf(t.x, mu.x, t.y * mu.y), fmaf(t.x, mu.y, -t.y * mu.x));
       }
     }
-    const double G = block_sum(g, s_scr);
+    const double G = block_sum_df2(g, 0.f, s_df).x;
     if (threadIdx.x == 0) {
       const double *rec = a.record + 4 * bk;
       const double Sre = rec[0] * inv_n, Sim = rec[1] * inv_n;
