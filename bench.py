@@ -877,11 +877,11 @@ def run_fairness(args, wl):
     ta = ta.cpu().numpy()
     tr = tr.cpu().numpy()
     done = ta[ta > 0].astype(np.float64)
-    # the sampler is issue-bound: per shot Philox4x32-10, the tile search, the
-    # chunk search and the search of the chunk's running sums execute ~326
-    # thread-instructions (ncu, profiles/sampler_and_fairness.md)
+    # the sampler's ceiling is its issue rate: per shot Philox4x32-10, the tile
+    # search, the chunk search and the search of the chunk's running sums
+    # execute ~318 thread-instructions (ncu instruction count of this path)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_peak = 4 * 32 * sms * 2.07e9 / 326
+    alu_peak = 4 * 32 * sms * 2.07e9 / 318
     samp_rate = shots_n * args.steps / t_samp
     if rank == 0:
         print(json.dumps({
@@ -895,7 +895,7 @@ def run_fairness(args, wl):
                          "unit": "shots/s", "frac": samp_rate / alu_peak,
                          "kernel": f"gqaoa_sample, resident-tile path ({100 * t_samp / el:.0f} % "
                                    "of the step)",
-                         "peak_derivation": "4 warp-instr/clk/SM x 32 x SMs x 2.07 GHz / 326 "
+                         "peak_derivation": "4 warp-instr/clk/SM x 32 x SMs x 2.07 GHz / 318 "
                                             "instructions per shot (measured count)"},
             "metrics_kernel_shots_per_s": shots_n * args.steps / t_fair,
             "shots_to_all_solutions": {"mean": float(done.mean()),

@@ -10,8 +10,9 @@
 // into 256 chunks of 16 consecutive amplitudes.
 //   w(z)     = |psi(z)|^2 in FP32 (the state is complex64),
 //   chunk    = FP32 running sum of its 16 w in index order,
-//   in-tile  = FP64 inclusive scan over the chunks (warp shuffles, then warps
-//              in order), tile total = its last value,
+//   in-tile  = inclusive scan over the chunks in double-float arithmetic
+//              (FP32 pairs: warp shuffles, then warps in order), each prefix
+//              rounded to FP64, tile total = the last one,
 //   tiles    = FP64 exclusive scan over tile totals.
 // Pass 1 computes tile totals; a single-CTA pass scans them; each shot then
 // finds its tile by binary search, shots are bucketed by tile with a
@@ -55,11 +56,29 @@ __device__ __forceinline__ double shot_uniform(uint64_t seed, uint64_t s) {
   return (double)(x >> 11) * (1.0 / 9007199254740992.0);
 }
 
-// Per tile: chunk sums (FP32, index order) and their FP64 inclusive scan.
+// a > b for non-negative doubles (CDF values and targets), decided on the
+// integer pipe: IEEE 754 orders non-negative values as their bit patterns
+// read as integers, so this equals the FP64 comparison without using GB300's
+// narrow FP64 pipe, which the shot searches would otherwise saturate.
+__device__ __forceinline__ bool gt_nonneg(double a, double b) {
+  return __double_as_longlong(a) > __double_as_longlong(b);
+}
+
+// (h, l) += (yh, yl) in double-float arithmetic (non-negative terms here).
+__device__ __forceinline__ void df_add(float &h, float &l, float yh, float yl) {
+  float s, e;
+  two_sum(h, yh, s, e);
+  h = s;
+  l = __fadd_rn(__fadd_rn(l, yl), e);
+}
+
+// Per tile: chunk sums (FP32, index order) and their inclusive scan in
+// double-float arithmetic (FP32 pairs, ~48 bits; FP64 would be issue-bound on
+// GB300's FP64 pipe here), stored as FP64.
 // On return s_incl[i] holds the inclusive prefix of chunk i within the tile
 // and s_w the tile's w values (row stride kPad). Called by all 256 threads.
 __device__ __forceinline__ void tile_chunk_scan(const float4 *__restrict__ st, uint64_t tile,
-                                                float *s_w, double *s_incl, double *s_wtot,
+                                                float *s_w, double *s_incl, float2 *s_wtot,
                                                 float *chunk_out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // coalesced loads: warp covers 512 amplitudes, lane holds amplitudes
@@ -78,25 +97,27 @@ __device__ __forceinline__ void tile_chunk_scan(const float4 *__restrict__ st, u
 #pragma unroll
   for (int i = 0; i < kChunk; ++i) c += sw[lane * kPad + i];
   *chunk_out = c;
-  // FP64 inclusive scan over the warp's 32 chunks
-  double x = (double)c;
+  // inclusive scan over the warp's 32 chunks
+  float xh = c, xl = 0.f;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const double y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
+    const float yh = __shfl_up_sync(0xffffffffu, xh, o);
+    const float yl = __shfl_up_sync(0xffffffffu, xl, o);
+    if (lane >= o) df_add(xh, xl, yh, yl);
   }
-  if (lane == 31) s_wtot[warp] = x;
+  if (lane == 31) s_wtot[warp] = make_float2(xh, xl);
   __syncthreads();
-  double base = 0.0;
-  for (int w = 0; w < warp; ++w) base += s_wtot[w];
-  s_incl[threadIdx.x] = base + x;
+  float bh = 0.f, bl = 0.f;  // the warps before this one, in order
+  for (int w = 0; w < warp; ++w) df_add(bh, bl, s_wtot[w].x, s_wtot[w].y);
+  df_add(bh, bl, xh, xl);
+  s_incl[threadIdx.x] = (double)bh + (double)bl;
   __syncthreads();
 }
 
-__device__ __forceinline__ double tile_total(const double *s_wtot) {
-  double t = 0.0;
-  for (int w = 0; w < kWarps; ++w) t += s_wtot[w];
-  return t;
+__device__ __forceinline__ double tile_total(const float2 *s_wtot) {
+  float th = 0.f, tl = 0.f;
+  for (int w = 0; w < kWarps; ++w) df_add(th, tl, s_wtot[w].x, s_wtot[w].y);
+  return (double)th + (double)tl;
 }
 
 // Pass 1: tile totals.
@@ -104,7 +125,7 @@ __global__ void __launch_bounds__(kThreads)
 tile_sum_kernel(const float4 *__restrict__ st, uint64_t ntiles, double *__restrict__ tsum) {
   __shared__ float s_w[kWarps * 32 * kPad];
   __shared__ double s_incl[kChunksPerTile];
-  __shared__ double s_wtot[kWarps];
+  __shared__ float2 s_wtot[kWarps];
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     float c;
     tile_chunk_scan(st, t, s_w, s_incl, s_wtot, &c);
@@ -121,6 +142,7 @@ scan_tiles_kernel(const double *__restrict__ tsum, uint64_t ntiles, double *__re
   const uint64_t lo = threadIdx.x * per;
   const uint64_t hi = lo + per < ntiles ? lo + per : ntiles;
   double acc = 0.0;
+#pragma unroll 8
   for (uint64_t i = lo; i < hi; ++i) acc += tsum[i];
   s_part[threadIdx.x] = acc;
   __syncthreads();
@@ -135,6 +157,7 @@ scan_tiles_kernel(const double *__restrict__ tsum, uint64_t ntiles, double *__re
   }
   __syncthreads();
   double run = s_part[threadIdx.x];
+#pragma unroll 8
   for (uint64_t i = lo; i < hi; ++i) {
     prefix[i] = run;
     run += tsum[i];
@@ -147,7 +170,7 @@ __device__ __forceinline__ uint32_t find_tile(const double *__restrict__ prefix,
   uint64_t lo = 0, hi = ntiles;  // answer in [lo, hi)
   while (lo < hi) {
     const uint64_t mid = lo + (hi - lo) / 2;
-    if (prefix[mid + 1] > t) hi = mid; else lo = mid + 1;
+    if (gt_nonneg(prefix[mid + 1], t)) hi = mid; else lo = mid + 1;
   }
   if (lo >= ntiles) {
     lo = ntiles - 1;
@@ -170,29 +193,42 @@ __global__ void shot_tile_kernel(const double *__restrict__ prefix, uint64_t nti
   }
 }
 
-// Single-CTA exclusive scan of the per-tile counts (uint32, exact).
+// Single-CTA exclusive scan of the per-tile counts (uint32, exact in any
+// order): thread t sums its contiguous range, a shuffle scan over the threads
+// gives its offset, then it writes its range.
 __global__ void __launch_bounds__(1024)
 scan_counts_kernel(const uint32_t *__restrict__ count, uint64_t ntiles,
                    uint32_t *__restrict__ offset) {
-  __shared__ uint32_t s_part[1024];
+  __shared__ uint32_t s_warp[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
   const uint64_t lo = threadIdx.x * per;
   const uint64_t hi = lo + per < ntiles ? lo + per : ntiles;
   uint32_t acc = 0;
+#pragma unroll 8
   for (uint64_t i = lo; i < hi; ++i) acc += count[i];
-  s_part[threadIdx.x] = acc;
+  // exclusive scan of acc over the CTA
+  uint32_t x = acc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int i = 0; i < (int)blockDim.x; ++i) {
-      const uint32_t v = s_part[i];
-      s_part[i] = run;
-      run += v;
+  if (warp == 0) {
+    uint32_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
     }
-    offset[ntiles] = run;
+    s_warp[lane] = w;  // inclusive over warps
   }
   __syncthreads();
-  uint32_t run = s_part[threadIdx.x];
+  uint32_t run = (warp > 0 ? s_warp[warp - 1] : 0u) + x - acc;
+  if (threadIdx.x == blockDim.x - 1) offset[ntiles] = run + acc;
+#pragma unroll 8
   for (uint64_t i = lo; i < hi; ++i) {
     offset[i] = run;
     run += count[i];
@@ -217,7 +253,7 @@ resolve_kernel(const float4 *__restrict__ st, uint64_t ntiles, const double *__r
                uint64_t seed, uint64_t *__restrict__ out) {
   __shared__ float s_w[kWarps * 32 * kPad];
   __shared__ double s_incl[kChunksPerTile];
-  __shared__ double s_wtot[kWarps];
+  __shared__ float2 s_wtot[kWarps];
   __shared__ float s_chunk[kChunksPerTile];
   const double total = prefix[ntiles];
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -235,23 +271,27 @@ resolve_kernel(const float4 *__restrict__ st, uint64_t ntiles, const double *__r
       int lo = 0, hi = kChunksPerTile;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (s_incl[mid] > r) hi = mid; else lo = mid + 1;
+        if (gt_nonneg(s_incl[mid], r)) hi = mid; else lo = mid + 1;
       }
       if (lo >= kChunksPerTile) {  // rounding past the tile end
         lo = kChunksPerTile - 1;
         while (lo > 0 && !(s_chunk[lo] > 0.f)) --lo;
       }
       const double rl = r - (lo > 0 ? s_incl[lo - 1] : 0.0);
+      // for a float f, f > rl exactly when f > rl rounded down to a float, so
+      // the walk compares in FP32 and decides as an FP64 comparison would
+      const float rlf = __double2float_rd(rl);
       // walk the chunk in index order with the same FP32 running sum
       const int warp_of = lo >> 5, lane_of = lo & 31;
       const float *row = s_w + warp_of * 32 * kPad + lane_of * kPad;
       float cum = 0.f;
       int pick = -1, last_nz = 0;
+#pragma unroll
       for (int i = 0; i < kChunk; ++i) {
         const float wi = row[i];
         cum += wi;
         if (wi > 0.f) last_nz = i;
-        if (pick < 0 && (double)cum > rl) pick = i;
+        if (pick < 0 && cum > rlf) pick = i;
       }
       if (pick < 0) pick = last_nz;
       // amplitude index: tile, warp tile of the chunk, position in the warp tile
@@ -287,19 +327,20 @@ __device__ __forceinline__ uint64_t resolve_shot(const TileScan *ts, const doubl
   int lo = 0, hi = kChunksPerTile;  // chunk: smallest i with incl[i] > r
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (T.incl[mid] > r) hi = mid; else lo = mid + 1;
+    if (gt_nonneg(T.incl[mid], r)) hi = mid; else lo = mid + 1;
   }
   if (lo >= kChunksPerTile) {  // rounding past the tile end
     lo = kChunksPerTile - 1;
     while (lo > 0 && !(T.chunk[lo] > 0.f)) --lo;
   }
   const double rl = r - (lo > 0 ? T.incl[lo - 1] : 0.0);
+  const float rlf = __double2float_rd(rl);  // f > rl  <=>  f > rlf for every float f
   const int warp_of = lo >> 5, lane_of = lo & 31;
   const float *row = T.cum + warp_of * 32 * kPad + lane_of * kPad;
   int a = 0, b = kChunk;  // first running sum above rl
   while (a < b) {
     const int mid = (a + b) >> 1;
-    if ((double)row[mid] > rl) b = mid; else a = mid + 1;
+    if (row[mid] > rlf) b = mid; else a = mid + 1;
   }
   const int pick = a < kChunk ? a : (int)T.last_nz[lo];
   return t * kSampTile + (uint64_t)warp_of * 512 + (uint64_t)lane_of * kChunk + pick;
@@ -311,7 +352,7 @@ resolve_resident_kernel(const float4 *__restrict__ st, uint64_t ntiles,
                         uint64_t *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
   TileScan *ts = reinterpret_cast<TileScan *>(s_dyn);  // [ntiles]
-  __shared__ double s_wtot[kWarps];
+  __shared__ float2 s_wtot[kWarps];
   __shared__ double s_prefix[kResidentTiles + 1];
   if (threadIdx.x <= ntiles) s_prefix[threadIdx.x] = prefix[threadIdx.x];
   for (uint64_t t = 0; t < ntiles; ++t) {
@@ -371,7 +412,7 @@ sample_small_kernel(const float2 *__restrict__ st, int n, uint64_t seed, int64_t
     int lo = 0, hi = N - 1;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if (s_cdf[mid] > t) hi = mid; else lo = mid + 1;
+      if (gt_nonneg(s_cdf[mid], t)) hi = mid; else lo = mid + 1;
     }
     out[s] = (uint64_t)lo;
   }
