@@ -152,7 +152,10 @@ int gqaoa_sample_workspace_size(int n, int64_t shots, size_t *bytes);
  * Fair sampling of measurement shots (Section IV, "sample all solutions";
  * Section II.B: the Grover mixer weights every solution equally):
  *   shot s = smallest z with CDF(z) > u_s * CDF(2^n - 1),
- *   CDF(z) = sum_{y <= z} |psi(y)|^2 (FP64),
+ *   CDF(z) = sum_{y <= z} |psi(y)|^2, accumulated as FP32 sums of 16
+ *            consecutive |psi|^2, prefixes of those within a tile of 4096
+ *            amplitudes in double-float (about 2^-44 relative, rounded to
+ *            FP64) and prefixes of the tile totals in FP64,
  *   u_s    = uniform double in [0,1) from Philox4x32-10 (Salmon et al.,
  *            SC 2011) with counter (s mod 2^32, s >> 32, 0, 0) and key
  *            (seed mod 2^32, seed >> 32); the top 53 bits of the 64-bit word
