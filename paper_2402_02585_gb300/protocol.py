@@ -93,7 +93,9 @@ class _EnergyGrad:
 
 class Protocol:
     """The protocol for one instance: cost [2^n] uint8 and hist [m + 1] int64
-    on the device (core.build_cost)."""
+    on the device (core.build_cost). An instance keeps per-depth device and
+    pinned host buffers, so it is used by one thread at a time (different
+    instances may run on different threads, as in min_rounds_many)."""
 
     def __init__(self, cost: torch.Tensor, hist: torch.Tensor, n: int, m: int):
         core._require_cuda(cost, hist)
@@ -177,6 +179,8 @@ class Protocol:
                 break
         res.evaluations = self.evaluations
         res.launches = self.launches
+        torch.cuda.current_stream().synchronize()
+        self._grad_calls.clear()  # each depth's checkpoints: p 2^n 8 bytes
         res.seconds = time.perf_counter() - t0
         return res
 
