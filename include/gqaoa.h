@@ -292,9 +292,9 @@ int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const double *gamm
  *        batch * p must stay below 2^31. NULL skips it.
  * ws     device workspace of gqaoa_reduced_sweep_workspace_size(angles)
  *        bytes (16-byte aligned, caller-owned): the phase tables.
- * Precision: complex64 class amplitudes and FP64 phases rounded to
- * complex64 (as the statevector path); the class sums are FP32 per lane and
- * double-float across a warp.
+ * Precision: complex64 class amplitudes and phases rounded to complex64 (as
+ * the statevector path); the class sums are FP32 per lane and double-float
+ * across the 1..16 lanes that hold one item's classes.
  * Errors: GQAOA_ERANGE for n outside 1..GQAOA_MAX_N, hist_stride outside
  * 1..256, batch < 1, angles outside 1..2^24, p outside 1..2^20;
  * GQAOA_EINVAL for NULL or misaligned pointers; GQAOA_ENOMEM for a short

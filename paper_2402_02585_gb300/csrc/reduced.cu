@@ -12,11 +12,12 @@
 // above n = 20), while the statevector kernels remain the evolution itself.
 //
 // One group of 1..16 lanes per (instance, angle point) item, each lane
-// holding 12 or 16 classes. Amplitudes are scaled by sqrt(N) (u = sqrt(N) f, u_0 = 1) and
-// the weights are w[c] = h[c] / N, so S / N = sum_c w[c] g(c) and
-// P = w[0] |u(0)|^2 do not depend on N. Complex64 amplitudes with FP64 phase
-// tables rounded to complex64 (as the statevector path); the sums over
-// classes are FP32 per lane and double-float across the lane group.
+// holding 12 or 16 classes. Amplitudes are scaled by sqrt(N)
+// (u = sqrt(N) f, u_0 = 1) and the weights are w[c] = h[c] / N, so
+// S / N = sum_c w[c] g(c) and P = w[0] |u(0)|^2 do not depend on N.
+// Complex64 amplitudes with phase tables rounded to complex64 (as the
+// statevector path); the sums over classes are FP32 per lane and
+// double-float across the lane group.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
