@@ -186,3 +186,36 @@ def test_sweep_rejects_bad_arguments_before_launch():
     with pytest.raises(C.GQAOAError) as e:
         C.gqaoa_sweep(fake, 12, 50, 1, fake, fake, 4, 4, r.ctypes.data, 1, 8, fake, fake, 1 << 20, None)
     assert e.value.status == C.GQAOA_EINVAL
+
+
+def test_fairness_workspace_and_bad_arguments_before_launch():
+    fake = 1 << 20
+    runs, targets = 1000, 25
+    need = C.gqaoa_fairness_workspace_size(14, runs, targets)
+    # a label per assignment, a counter, and the per-run counts of every target
+    assert need >= 4 * (1 << 14) + 4 * runs * targets
+    for args in ((0, runs, targets), (31, runs, targets), (14, 0, targets), (14, runs, 0),
+                 (4, runs, 17)):  # more targets than assignments
+        with pytest.raises(C.GQAOAError) as e:
+            C.gqaoa_fairness_workspace_size(*args)
+        assert e.value.status == C.GQAOA_ERANGE, args
+    ok = (fake, runs, 2048, fake, 14, 0, targets, 36.4, 125, fake, fake, fake, need, None)
+
+    def call(**kw):
+        a = list(ok)
+        for k, v in kw.items():
+            a[{"shots": 0, "runs": 1, "per_run": 2, "n": 4, "target": 5, "targets": 6,
+               "min_draws": 8, "to_all": 9, "ws_bytes": 12}[k]] = v
+        with pytest.raises(C.GQAOAError) as e:
+            C.gqaoa_fairness(*a)
+        return e.value.status
+
+    assert call(n=31) == C.GQAOA_ERANGE
+    assert call(target=256) == C.GQAOA_ERANGE
+    assert call(targets=0) == C.GQAOA_ERANGE
+    assert call(min_draws=0) == C.GQAOA_ERANGE
+    assert call(per_run=-1) == C.GQAOA_ERANGE
+    assert call(per_run=1 << 31, targets=1 << 12) == C.GQAOA_ERANGE  # M sum O^2 would overflow
+    assert call(shots=0) == C.GQAOA_EINVAL
+    assert call(to_all=fake + 4) == C.GQAOA_EINVAL  # misaligned output
+    assert call(ws_bytes=need - 1) == C.GQAOA_ENOMEM
