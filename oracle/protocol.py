@@ -82,21 +82,19 @@ def min_rounds(hist, gammas, betas, S: float = 0.5, p_max: int = 64, single: boo
                target: str = "P"):
     """Fewest rounds k <= p_max whose <H_P>-optimised state reaches
     probability S of a solution (target "P") or of a Max-SAT assignment
-    (target "D"). Seeds: the grid point of lowest <H_P> at depth k; a depth
-    is refined only where that seed already reaches S/2 (the refinement is a
-    local one and does not double the probability). Returns
-    (k or None, gammas, betas, probability, <H_P>)."""
-    E, P, D = grid_readouts(hist, gammas, betas, p_max)
-    prob = P if target == "P" else D
+    (target "D"). Every depth k = 1, 2, ... is optimised in turn, as
+    Appendix C does for each instance and depth: the seed is the grid point
+    of lowest <H_P> after k rounds, L-BFGS-B starts from it over the single
+    angle pair (single) or over all 2k per-round angles (not single: the
+    same seed, every angle free), and the depth is accepted when the
+    optimised state reaches S. Returns (k or None, gammas, betas,
+    probability, <H_P>)."""
+    E, _, _ = grid_readouts(hist, gammas, betas, p_max)
     G = np.asarray(gammas, np.float64)
     B = np.asarray(betas, np.float64)
     for k in range(1, p_max + 1):
         a = int(np.argmin(E[:, k - 1]))
-        if prob[a, k - 1] < S / 2:
-            continue
-        g, b, e, _ = refine(hist, [G[a]] * k, [B[a]] * k, single=True)
-        if not single:
-            g, b, e, _ = refine(hist, g, b, single=False)
+        g, b, e, _ = refine(hist, [G[a]] * k, [B[a]] * k, single=single)
         r = reduced.readouts_trace(hist, g, b)[-1]
         val = r[0] if target == "P" else r[2]
         if val >= S:

@@ -18,10 +18,12 @@ For an unsatisfiable instance (Max-SAT, Fig. 1(b)) the target is D, the
 probability of the lowest non-empty cost class (the assignments leaving the
 fewest clauses unsatisfied), read the same way with GQAOA_READOUT_CLASS.
 
-A depth is refined only where its grid seed already reaches S/2 (the
-refinement is local and does not double the probability); the cost-class
-and statevector evaluations agree to complex64 precision (tested), so the
-grid ranks candidates and the statevector decides.
+Every depth k = 1, 2, ... is refined in turn, as Appendix C optimises each
+instance at each depth: L-BFGS-B starts from that depth's grid seed over the
+single angle pair, or, for G-QAOA with per-round angles, from the same seed
+over all 2k angles. The cost-class and statevector evaluations agree to
+complex64 precision (tested), so the grid ranks candidates and the
+statevector decides.
 """
 
 from __future__ import annotations
@@ -167,12 +169,9 @@ class Protocol:
         cls = 0 if target == "P" else self.min_class
         res = MinRounds(None, None, None, None, None, grid_prob=seed_vals[:, col].copy())
         for k in range(1, p_max + 1):
-            if seed_vals[k - 1, col] < S / 2:
-                continue
             a = int(bi[k - 1])
-            g, b, e, _ = self.refine([G[a]] * k, [B[a]] * k, single=True)
-            if not single:
-                g, b, e, _ = self.refine(g, b, single=False)
+            g, b, e, _ = self.refine([G[a]] * k, [B[a]] * k, single=single)
+            self._grad_calls.pop(k, None)  # this depth's checkpoints, k 2^n 8 bytes
             prob = self.probability(g, b, cls)
             if prob >= S:
                 res.p, res.gammas, res.betas, res.prob, res.energy = k, g, b, prob, e
@@ -180,7 +179,6 @@ class Protocol:
         res.evaluations = self.evaluations
         res.launches = self.launches
         torch.cuda.current_stream().synchronize()
-        self._grad_calls.clear()  # each depth's checkpoints: p 2^n 8 bytes
         res.seconds = time.perf_counter() - t0
         return res
 

@@ -63,9 +63,32 @@ def test_protocol_matches_oracle(n, m, seed):
     assert got.prob >= 0.5
 
 
+@pytest.mark.parametrize("n,m,seed", [(9, 32, 1), (10, 35, 21)])
+def test_protocol_all_angles_matches_oracle(n, m, seed):
+    # G-QAOA with per-round angles: L-BFGS-B over all 2k angles from the grid
+    # seed of every depth. On these instances the accepted depth (17) has a
+    # grid seed below S/2 that the refinement lifts above S, so a protocol
+    # refining only promising seeds would answer 18.
+    lits = instances.random_3sat(n, m, seed)
+    _, ohist = sv.cost_table(lits, n)
+    cost, hist = core.build_cost(lits, n)
+    G, B = instances.protocol_grid(2)
+    p_max = 24
+    got = Protocol(cost, hist, n, m).min_rounds(S=0.5, p_max=p_max, single=False, grid=(G, B))
+    k, g, b, val, e = oprot.min_rounds(ohist, G, B, S=0.5, p_max=p_max, single=False)
+    assert k == 17 and got.p == k
+    assert got.grid_prob[k - 1] < 0.25
+    # 34 free angles stop at a 1e-6 relative change of <H_P>; the two
+    # searches end at slightly different points of the same flat optimum
+    assert abs(got.energy - e) < 1e-4 * m
+    assert abs(got.prob - val) < 2e-3
+    assert got.prob >= 0.5
+
+
 def test_protocol_full_angles_not_worse_than_single():
     n, m = 10, 40
     lits = instances.random_3sat(n, m, 2)
+    _, ohist = sv.cost_table(lits, n)
     cost, hist = core.build_cost(lits, n)
     G, B = instances.protocol_grid(3)
     prot = Protocol(cost, hist, n, m)
@@ -74,6 +97,7 @@ def test_protocol_full_angles_not_worse_than_single():
     assert single.p is not None and full.p is not None
     assert full.p <= single.p
     assert full.prob >= 0.5
+    assert full.p == oprot.min_rounds(ohist, G, B, S=0.5, p_max=24, single=False)[0]
 
 
 def test_protocol_many_instances_on_threads_matches_one_by_one():

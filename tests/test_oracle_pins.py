@@ -391,6 +391,24 @@ def test_protocol_min_rounds_two_class_closed_form():
     assert abs(e - (1 - val)) < 1e-9
 
 
+def test_protocol_refines_every_depth():
+    # Appendix C optimises every depth from its grid seed. Here the accepted
+    # depth of the per-round-angle protocol has a seed below S/2, which
+    # L-BFGS-B over the 2k angles lifts above S; the depth before it stays
+    # below S after the same refinement.
+    n, m, seed = 10, 35, 21
+    _, hist = sv.cost_table(instances.random_3sat(n, m, seed), n)
+    G, B = instances.protocol_grid(2)
+    k, g, b, val, e = protocol.min_rounds(hist, G, B, S=0.5, p_max=24, single=False)
+    assert k == 17 and val >= 0.5
+    E, P, _ = protocol.grid_readouts(hist, G, B, k)
+    a = int(np.argmin(E[:, k - 1]))
+    assert P[a, k - 1] < 0.25
+    a = int(np.argmin(E[:, k - 2]))
+    g1, b1, _, _ = protocol.refine(hist, [G[a]] * (k - 1), [B[a]] * (k - 1), single=False)
+    assert reduced.readouts_trace(hist, g1, b1)[-1][0] < 0.5
+
+
 def test_protocol_grid_readouts_match_single_evolutions():
     n, m, p = 8, 34, 9
     _, hist = sv.cost_table(instances.random_3sat(n, m, 31), n)
