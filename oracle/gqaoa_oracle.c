@@ -222,18 +222,29 @@ double oracle_shot_uniform(uint64_t seed, uint64_t shot)
 
 /* Shots z ~ |psi(z)|^2 by inversion of the cumulative distribution in index
  * order: shot s is the smallest z with CDF(z) > u_s * CDF(N-1), CDF(z) the
- * running FP64 sum of |psi|^2 up to and including z. If cdf_out is not NULL
- * it receives the running sums. Returns 0, or -1 if the state has zero norm. */
+ * sum of |psi|^2 up to and including z. The running sum carries the rounding
+ * error of every addition in a second word (Neumaier's compensated
+ * summation), so each CDF(z) is within a few units in the last place of the
+ * exact sum of the FP64 weights however many terms precede it; a plain
+ * running sum would drift by up to N rounding errors over 2^n terms. If
+ * cdf_out is not NULL it receives the CDF. Returns 0, or -1 if the state has
+ * zero norm. */
 int oracle_sample(const double *psi, int n, uint64_t seed, int64_t shots, uint32_t *out,
                   double *cdf_out)
 {
     uint64_t N = (uint64_t)1 << n;
     double *cdf = cdf_out ? cdf_out : (double *)malloc(sizeof(double) * N);
     if (!cdf) return -1;
-    double run = 0.0;
+    double run = 0.0, carry = 0.0;
     for (uint64_t z = 0; z < N; ++z) {
-        run += psi[2 * z] * psi[2 * z] + psi[2 * z + 1] * psi[2 * z + 1];
-        cdf[z] = run;
+        double w = psi[2 * z] * psi[2 * z] + psi[2 * z + 1] * psi[2 * z + 1];
+        double t = run + w;
+        if (fabs(run) >= fabs(w))
+            carry += (run - t) + w;  /* the low part of run + w lost in t */
+        else
+            carry += (w - t) + run;
+        run = t;
+        cdf[z] = run + carry;
     }
     double total = cdf[N - 1];
     int status = 0;

@@ -6,24 +6,36 @@
 // double in [0,1) from Philox4x32-10 (Salmon et al., SC 2011) with counter
 // (s, s >> 32, 0, 0) and key (seed, seed >> 32).
 //
-// Two-level CDF. The state is cut into tiles of 4096 amplitudes and a tile
-// into 256 chunks of 16 consecutive amplitudes.
-//   w(z)     = |psi(z)|^2 in FP32 (the state is complex64),
-//   chunk    = FP32 running sum of its 16 w in index order,
+// CDF arithmetic. The weights of a complex64 state are formed without
+// rounding loss that matters: w(z) = re^2 + im^2 as a double-float pair (FP32
+// hi + lo; each square is split exactly into its product and the product's
+// error by an FMA, the two products are added with TwoSum), about 2^-46
+// relative. The state is cut into tiles of 4096 amplitudes and a tile into
+// 256 chunks of 16 consecutive amplitudes:
+//   chunk    = double-float sum of its 16 weights in index order,
 //   in-tile  = inclusive scan over the chunks in double-float arithmetic
-//              (FP32 pairs: warp shuffles, then warps in order), each prefix
-//              rounded to FP64, tile total = the last one,
-//   tiles    = FP64 exclusive scan over tile totals.
-// Pass 1 computes tile totals; a single-CTA pass scans them; each shot then
-// finds its tile by binary search, shots are bucketed by tile with a
-// counting sort, and pass 2 re-reads only the tiles that received shots,
-// rebuilds the same chunk sums and scan, and resolves each shot by a binary
-// search over chunks and a walk over 16 amplitudes. With at most eight tiles
-// (n <= 15) every CTA keeps all tile scans in shared memory and resolves its
-// shots directly instead (same arithmetic, no bucketing). Both passes compute the
-// tile totals with the same instructions in the same order, so the levels
-// agree exactly; a target that rounding puts past the end of a chunk or tile
-// goes to its last amplitude of nonzero weight.
+//              (warp shuffles, then warps in order), each prefix rounded to
+//              FP64, tile total = the last one,
+//   tiles    = exclusive scan over the tile totals in FP64 pairs (TwoSum
+//              carries each addition's rounding error), rounded to FP64, by
+//              many CTAs in two launches,
+//   in-chunk = double-float running sums of the chunk's weights, compared as
+//              FP64.
+// Every CDF value is therefore within a few FP64 rounding units of the exact
+// prefix sum of the state's weights, at any n: equal-magnitude amplitudes
+// (a whole cost class has one magnitude) cannot make rounding errors pile up
+// the way FP32 sums would.
+//
+// Pass 1 computes tile totals; two launches scan them; each shot then finds
+// its tile by binary search, shots are bucketed by tile with a counting sort
+// (its counts scanned the same way), and pass 2 re-reads only the tiles that
+// received shots, rebuilds the same chunk sums and scan, and resolves each
+// shot by a binary search over chunks and a walk over its chunk's 16
+// weights. With at most eight tiles (n <= 15) every CTA keeps all tile scans
+// in shared memory and resolves its shots directly instead (no bucketing).
+// Both passes compute the tile totals with the same instructions in the same
+// order, so the levels agree exactly; a target that rounding puts past the
+// end of a chunk or tile goes to its last amplitude of nonzero weight.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,7 +46,8 @@ namespace gq {
 constexpr int kSampTile = 4096;
 constexpr int kChunk = 16;
 constexpr int kChunksPerTile = kSampTile / kChunk;  // 256 = one per thread
-constexpr int kPad = kChunk + 1;                    // shared row stride (bank spread)
+constexpr int kRowVec = kChunk / 2 + 1;  // float4 (2 amplitudes) per shared chunk row, 1 pad
+constexpr int kPad = kChunk + 1;         // floats per row of the resident running sums
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10: ten rounds of two 32x32 multiplies, key bumped by the Weyl
@@ -72,33 +85,86 @@ __device__ __forceinline__ void df_add(float &h, float &l, float yh, float yl) {
   l = __fadd_rn(__fadd_rn(l, yl), e);
 }
 
-// Per tile: chunk sums (FP32, index order) and their inclusive scan in
-// double-float arithmetic (FP32 pairs, ~48 bits; FP64 would be issue-bound on
-// GB300's FP64 pipe here), stored as FP64.
-// On return s_incl[i] holds the inclusive prefix of chunk i within the tile
-// and s_w the tile's w values (row stride kPad). Called by all 256 threads.
-__device__ __forceinline__ void tile_chunk_scan(const float4 *__restrict__ st, uint64_t tile,
-                                                float *s_w, double *s_incl, float2 *s_wtot,
-                                                float *chunk_out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // coalesced loads: warp covers 512 amplitudes, lane holds amplitudes
-  // 64j + 2 lane and 64j + 2 lane + 1 of its warp tile
-  const uint64_t vbase = tile * (kSampTile / 2) + (uint64_t)warp * 256 + lane;
-  float *sw = s_w + warp * 32 * kPad;
+// Renormalise (h, l) so that h is the FP32 rounding of h + l (Fast2Sum,
+// |h| >= |l|).
+__device__ __forceinline__ void df_norm(float &h, float &l) {
+  const float s = __fadd_rn(h, l);
+  l = __fsub_rn(l, __fsub_rn(s, h));
+  h = s;
+}
+
+// |re + i im|^2 as a normalised double-float (h, l): re^2 = p1 + e1 and
+// im^2 = p2 + e2 exactly (e = fma(x, x, -p)), p1 + p2 = s + e exactly
+// (TwoSum), and the three small words are added in FP32, which leaves a
+// relative error below 2^-46.
+__device__ __forceinline__ void weight_df(float re, float im, float &h, float &l) {
+  const float p1 = __fmul_rn(re, re), e1 = fmaf(re, re, -p1);
+  const float p2 = __fmul_rn(im, im), e2 = fmaf(im, im, -p2);
+  float s, e;
+  two_sum(p1, p2, s, e);
+  h = s;
+  l = __fadd_rn(e, __fadd_rn(e1, e2));
+  df_norm(h, l);
+}
+
+// The first of a chunk's 16 amplitudes (row: 8 float4 in shared or global
+// memory) whose running weight sum exceeds rl: the sums are formed in
+// double-float in index order (the order of the chunk sum) and compared as
+// FP64. A target that rounding puts past the chunk's sum goes to its last
+// amplitude of nonzero weight.
+__device__ __forceinline__ int chunk_pick(const float4 *row, double rl) {
+  float h = 0.f, l = 0.f;
+  int pick = -1, last_nz = 0;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const float4 v = st[vbase + 32 * j];
-    const int a = 64 * j + 2 * lane;  // amplitude index within the warp tile
-    sw[(a / kChunk) * kPad + (a % kChunk)] = fmaf(v.x, v.x, v.y * v.y);
-    sw[((a + 1) / kChunk) * kPad + ((a + 1) % kChunk)] = fmaf(v.z, v.z, v.w * v.w);
+  for (int i = 0; i < kChunk / 2; ++i) {
+    const float4 v = row[i];
+    float wh, wl;
+    weight_df(v.x, v.y, wh, wl);
+    df_add(h, l, wh, wl);
+    if (wh > 0.f) last_nz = 2 * i;
+    if (pick < 0 && gt_nonneg((double)h + (double)l, rl)) pick = 2 * i;
+    weight_df(v.z, v.w, wh, wl);
+    df_add(h, l, wh, wl);
+    if (wh > 0.f) last_nz = 2 * i + 1;
+    if (pick < 0 && gt_nonneg((double)h + (double)l, rl)) pick = 2 * i + 1;
   }
-  __syncwarp();
-  float c = 0.f;
+  return pick >= 0 ? pick : last_nz;
+}
+
+// Per tile: the tile's amplitudes into shared memory, one row of 16 per
+// chunk (row stride kRowVec float4; chunk i = row i, amplitudes 16 i ..
+// 16 i + 15 of the tile), every thread's chunk sum in double-float, and the
+// inclusive in-tile scan of the chunk sums in double-float, rounded to FP64
+// into s_incl. (ch, cl) receives this thread's chunk sum, normalised.
+// Called by all 256 threads.
+__device__ __forceinline__ void tile_chunk_scan(const float4 *__restrict__ st, uint64_t tile,
+                                                float4 *s_amp, double *s_incl, float2 *s_wtot,
+                                                float &ch, float &cl) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // coalesced loads: a warp covers 512 amplitudes; load j of lane l is
+  // amplitudes 64 j + 2 l and 64 j + 2 l + 1 of the warp's 512, i.e. slot
+  // l mod 8 of row 4 j + l / 8
+  const uint64_t vbase = tile * (kSampTile / 2) + (uint64_t)warp * 256 + lane;
+  float4 *sa = s_amp + warp * 32 * kRowVec;
 #pragma unroll
-  for (int i = 0; i < kChunk; ++i) c += sw[lane * kPad + i];
-  *chunk_out = c;
+  for (int j = 0; j < 8; ++j) sa[(4 * j + (lane >> 3)) * kRowVec + (lane & 7)] = st[vbase + 32 * j];
+  __syncwarp();
+  const float4 *row = sa + lane * kRowVec;
+  float h = 0.f, l = 0.f;
+#pragma unroll
+  for (int i = 0; i < kChunk / 2; ++i) {
+    const float4 v = row[i];
+    float wh, wl;
+    weight_df(v.x, v.y, wh, wl);
+    df_add(h, l, wh, wl);
+    weight_df(v.z, v.w, wh, wl);
+    df_add(h, l, wh, wl);
+  }
+  df_norm(h, l);
+  ch = h;
+  cl = l;
   // inclusive scan over the warp's 32 chunks
-  float xh = c, xl = 0.f;
+  float xh = h, xl = l;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const float yh = __shfl_up_sync(0xffffffffu, xh, o);
@@ -123,45 +189,125 @@ __device__ __forceinline__ double tile_total(const float2 *s_wtot) {
 // Pass 1: tile totals.
 __global__ void __launch_bounds__(kThreads)
 tile_sum_kernel(const float4 *__restrict__ st, uint64_t ntiles, double *__restrict__ tsum) {
-  __shared__ float s_w[kWarps * 32 * kPad];
+  __shared__ float4 s_amp[kWarps * 32 * kRowVec];
   __shared__ double s_incl[kChunksPerTile];
   __shared__ float2 s_wtot[kWarps];
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    float c;
-    tile_chunk_scan(st, t, s_w, s_incl, s_wtot, &c);
+    float ch, cl;
+    tile_chunk_scan(st, t, s_amp, s_incl, s_wtot, ch, cl);
     if (threadIdx.x == 0) tsum[t] = tile_total(s_wtot);
     __syncthreads();
   }
 }
 
-// Single-CTA exclusive FP64 scan of tile totals: prefix[0..ntiles].
-__global__ void __launch_bounds__(1024)
-scan_tiles_kernel(const double *__restrict__ tsum, uint64_t ntiles, double *__restrict__ prefix) {
-  __shared__ double s_part[1024];
-  const uint64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
-  const uint64_t lo = threadIdx.x * per;
-  const uint64_t hi = lo + per < ntiles ? lo + per : ntiles;
-  double acc = 0.0;
-#pragma unroll 8
-  for (uint64_t i = lo; i < hi; ++i) acc += tsum[i];
-  s_part[threadIdx.x] = acc;
+// ---------------------------------------------------------------------------
+// Exclusive scans over per-tile values (tile totals, shot counts) by many
+// CTAs in two launches: CTA g scans its 1024 values and their total; then
+// CTA g adds the total of the CTAs before it, summed in a fixed order, so the
+// result does not depend on scheduling. Tile totals are added in FP64 pairs
+// (the rounding error of each addition kept in the second word, TwoSum), so
+// a prefix over 2^22 tiles stays within a rounding unit of the exact sum;
+// counts are exact integers.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+
+struct DD {
+  double hi, lo;
+};
+__device__ __forceinline__ DD dd_add(DD a, DD b) {
+  const double s = __dadd_rn(a.hi, b.hi);
+  const double bb = __dsub_rn(s, a.hi);
+  const double e = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(s, bb)), __dsub_rn(b.hi, bb));
+  const double t = __dadd_rn(e, __dadd_rn(a.lo, b.lo));
+  const double h = __dadd_rn(s, t);
+  return DD{h, __dsub_rn(t, __dsub_rn(h, s))};
+}
+
+struct SumDD {  // tile totals -> FP64 prefixes
+  using In = double;
+  using Acc = DD;
+  using Out = double;
+  static __device__ __forceinline__ Acc zero() { return DD{0.0, 0.0}; }
+  static __device__ __forceinline__ Acc from(In v) { return DD{v, 0.0}; }
+  static __device__ __forceinline__ Acc add(Acc a, Acc b) { return dd_add(a, b); }
+  static __device__ __forceinline__ Acc shfl_up(Acc a, int o) {
+    return DD{__shfl_up_sync(0xffffffffu, a.hi, o), __shfl_up_sync(0xffffffffu, a.lo, o)};
+  }
+  static __device__ __forceinline__ Acc shfl_xor(Acc a, int o) {
+    return DD{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+  }
+  static __device__ __forceinline__ Out out(Acc a) { return __dadd_rn(a.hi, a.lo); }
+};
+
+struct SumU32 {  // shot counts -> offsets
+  using In = uint32_t;
+  using Acc = uint32_t;
+  using Out = uint32_t;
+  static __device__ __forceinline__ Acc zero() { return 0u; }
+  static __device__ __forceinline__ Acc from(In v) { return v; }
+  static __device__ __forceinline__ Acc add(Acc a, Acc b) { return a + b; }
+  static __device__ __forceinline__ Acc shfl_up(Acc a, int o) {
+    return __shfl_up_sync(0xffffffffu, a, o);
+  }
+  static __device__ __forceinline__ Acc shfl_xor(Acc a, int o) {
+    return __shfl_xor_sync(0xffffffffu, a, o);
+  }
+  static __device__ __forceinline__ Out out(Acc a) { return a; }
+};
+
+template <class A>
+__global__ void __launch_bounds__(kScanThreads)
+scan_local_kernel(const typename A::In *__restrict__ in, uint64_t count,
+                  typename A::Acc *__restrict__ loc, typename A::Acc *__restrict__ gtot) {
+  using Acc = typename A::Acc;
+  __shared__ Acc s_warp[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t i = (uint64_t)blockIdx.x * kScanThreads + threadIdx.x;
+  Acc inc = i < count ? A::from(in[i]) : A::zero();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const Acc y = A::shfl_up(inc, o);
+    if (lane >= o) inc = A::add(y, inc);
+  }
+  if (lane == 31) s_warp[warp] = inc;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double run = 0.0;
-    for (int i = 0; i < (int)blockDim.x; ++i) {
-      const double v = s_part[i];
-      s_part[i] = run;
-      run += v;
+  if (warp == 0) {
+    Acc w = s_warp[lane];  // kScanThreads / 32 == 32 warps
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const Acc y = A::shfl_up(w, o);
+      if (lane >= o) w = A::add(y, w);
     }
-    prefix[ntiles] = run;
+    s_warp[lane] = w;  // inclusive over warps
   }
   __syncthreads();
-  double run = s_part[threadIdx.x];
-#pragma unroll 8
-  for (uint64_t i = lo; i < hi; ++i) {
-    prefix[i] = run;
-    run += tsum[i];
-  }
+  Acc ex = A::shfl_up(inc, 1);
+  if (lane == 0) ex = A::zero();
+  if (warp > 0) ex = A::add(s_warp[warp - 1], ex);
+  if (i < count) loc[i] = ex;
+  if (threadIdx.x == 0) gtot[blockIdx.x] = s_warp[31];
+}
+
+template <class A>
+__global__ void __launch_bounds__(kScanThreads)
+scan_finish_kernel(const typename A::Acc *__restrict__ loc, uint64_t count,
+                   const typename A::Acc *__restrict__ gtot, typename A::Out *__restrict__ out) {
+  using Acc = typename A::Acc;
+  __shared__ Acc s_warp[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // total of the CTAs before this one: strided partial sums, then a fixed tree
+  Acc acc = A::zero();
+  for (uint32_t g = threadIdx.x; g < blockIdx.x; g += kScanThreads) acc = A::add(acc, gtot[g]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc = A::add(acc, A::shfl_xor(acc, o));
+  if (lane == 0) s_warp[warp] = acc;
+  __syncthreads();
+  Acc base = A::zero();
+  for (int w = 0; w < kScanThreads / 32; ++w) base = A::add(base, s_warp[w]);
+  const uint64_t i = (uint64_t)blockIdx.x * kScanThreads + threadIdx.x;
+  if (i < count) out[i] = A::out(A::add(base, loc[i]));
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+    out[count] = A::out(A::add(base, gtot[blockIdx.x]));
 }
 
 // Smallest tile i with prefix[i+1] > t; past the end -> last tile of nonzero weight.
@@ -193,48 +339,6 @@ __global__ void shot_tile_kernel(const double *__restrict__ prefix, uint64_t nti
   }
 }
 
-// Single-CTA exclusive scan of the per-tile counts (uint32, exact in any
-// order): thread t sums its contiguous range, a shuffle scan over the threads
-// gives its offset, then it writes its range.
-__global__ void __launch_bounds__(1024)
-scan_counts_kernel(const uint32_t *__restrict__ count, uint64_t ntiles,
-                   uint32_t *__restrict__ offset) {
-  __shared__ uint32_t s_warp[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
-  const uint64_t lo = threadIdx.x * per;
-  const uint64_t hi = lo + per < ntiles ? lo + per : ntiles;
-  uint32_t acc = 0;
-#pragma unroll 8
-  for (uint64_t i = lo; i < hi; ++i) acc += count[i];
-  // exclusive scan of acc over the CTA
-  uint32_t x = acc;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_warp[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    s_warp[lane] = w;  // inclusive over warps
-  }
-  __syncthreads();
-  uint32_t run = (warp > 0 ? s_warp[warp - 1] : 0u) + x - acc;
-  if (threadIdx.x == blockDim.x - 1) offset[ntiles] = run + acc;
-#pragma unroll 8
-  for (uint64_t i = lo; i < hi; ++i) {
-    offset[i] = run;
-    run += count[i];
-  }
-}
-
 __global__ void scatter_kernel(const uint32_t *__restrict__ shot_tile, int64_t shots,
                                const uint32_t *__restrict__ offset, uint32_t *__restrict__ cursor,
                                uint32_t *__restrict__ bucket) {
@@ -246,12 +350,27 @@ __global__ void scatter_kernel(const uint32_t *__restrict__ shot_tile, int64_t s
   }
 }
 
+// Chunk of the tile: smallest i with incl[i] > r; a target that rounding puts
+// past the tile's end goes to its last chunk of nonzero weight.
+__device__ __forceinline__ int find_chunk(const double *incl, const float *chunk, double r) {
+  int lo = 0, hi = kChunksPerTile;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (gt_nonneg(incl[mid], r)) hi = mid; else lo = mid + 1;
+  }
+  if (lo >= kChunksPerTile) {
+    lo = kChunksPerTile - 1;
+    while (lo > 0 && !(chunk[lo] > 0.f)) --lo;
+  }
+  return lo;
+}
+
 // Pass 2: resolve the shots of every tile that received any.
 __global__ void __launch_bounds__(kThreads)
 resolve_kernel(const float4 *__restrict__ st, uint64_t ntiles, const double *__restrict__ prefix,
                const uint32_t *__restrict__ offset, const uint32_t *__restrict__ bucket,
                uint64_t seed, uint64_t *__restrict__ out) {
-  __shared__ float s_w[kWarps * 32 * kPad];
+  __shared__ float4 s_amp[kWarps * 32 * kRowVec];
   __shared__ double s_incl[kChunksPerTile];
   __shared__ float2 s_wtot[kWarps];
   __shared__ float s_chunk[kChunksPerTile];
@@ -259,43 +378,18 @@ resolve_kernel(const float4 *__restrict__ st, uint64_t ntiles, const double *__r
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint32_t b0 = offset[t], b1 = offset[t + 1];
     if (b0 == b1) continue;  // uniform across the CTA
-    float c;
-    tile_chunk_scan(st, t, s_w, s_incl, s_wtot, &c);
-    s_chunk[threadIdx.x] = c;
+    float ch, cl;
+    tile_chunk_scan(st, t, s_amp, s_incl, s_wtot, ch, cl);
+    s_chunk[threadIdx.x] = ch;
     __syncthreads();
     const double tbase = prefix[t];
     for (uint32_t q = b0 + threadIdx.x; q < b1; q += blockDim.x) {
       const uint32_t s = bucket[q];
       const double r = shot_uniform(seed, s) * total - tbase;
-      // chunk: smallest i with s_incl[i] > r
-      int lo = 0, hi = kChunksPerTile;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (gt_nonneg(s_incl[mid], r)) hi = mid; else lo = mid + 1;
-      }
-      if (lo >= kChunksPerTile) {  // rounding past the tile end
-        lo = kChunksPerTile - 1;
-        while (lo > 0 && !(s_chunk[lo] > 0.f)) --lo;
-      }
-      const double rl = r - (lo > 0 ? s_incl[lo - 1] : 0.0);
-      // for a float f, f > rl exactly when f > rl rounded down to a float, so
-      // the walk compares in FP32 and decides as an FP64 comparison would
-      const float rlf = __double2float_rd(rl);
-      // walk the chunk in index order with the same FP32 running sum
-      const int warp_of = lo >> 5, lane_of = lo & 31;
-      const float *row = s_w + warp_of * 32 * kPad + lane_of * kPad;
-      float cum = 0.f;
-      int pick = -1, last_nz = 0;
-#pragma unroll
-      for (int i = 0; i < kChunk; ++i) {
-        const float wi = row[i];
-        cum += wi;
-        if (wi > 0.f) last_nz = i;
-        if (pick < 0 && cum > rlf) pick = i;
-      }
-      if (pick < 0) pick = last_nz;
-      // amplitude index: tile, warp tile of the chunk, position in the warp tile
-      out[s] = t * kSampTile + (uint64_t)warp_of * 512 + (uint64_t)lane_of * kChunk + pick;
+      const int c = find_chunk(s_incl, s_chunk, r);
+      const double rl = r - (c > 0 ? s_incl[c - 1] : 0.0);
+      const int pick = chunk_pick(s_amp + c * kRowVec, rl);
+      out[s] = t * kSampTile + (uint64_t)c * kChunk + pick;
     }
     __syncthreads();
   }
@@ -305,45 +399,40 @@ resolve_kernel(const float4 *__restrict__ st, uint64_t ntiles, const double *__r
 // counting sort would serialise on a handful of counters. Every CTA instead
 // rebuilds the chunk scans of all tiles in shared memory (the instructions of
 // pass 2) and resolves a grid-stride range of shots directly, with the same
-// tile search. The walk over a chunk's 16 weights is replaced by a binary
-// search over their FP32 running sums, computed once in the walk's order:
-// the sums never decrease, so the first sum above the target is the index
-// the walk would stop at, and the shots are the ones pass 2 would give.
+// tile and chunk searches. Inside a chunk it first searches FP32 running sums
+// of the weights' leading words, which lie within 2^-19 of the chunk's sum of
+// the exact running sums; only a target within 2^-17 of the chunk's sum of
+// one of them (about one shot in 10^4) is decided by chunk_pick on the
+// chunk's amplitudes reloaded from global memory (L2-resident at these
+// sizes), so every shot is the one pass 2 would give.
 constexpr int kResidentTiles = 8;
 struct TileScan {
-  float cum[kWarps * 32 * kPad];  // per chunk (row of kPad): running sums of its 16 weights
+  float cum[kChunksPerTile * kPad];  // per chunk (row of kPad): FP32 running sums
   double incl[kChunksPerTile];
-  float chunk[kChunksPerTile];
-  uint8_t last_nz[kChunksPerTile];  // last weight > 0 in the chunk (0 if none)
+  float chunk[kChunksPerTile];       // leading word of each chunk's sum
 };
 
-__device__ __forceinline__ uint64_t resolve_shot(const TileScan *ts, const double *s_prefix,
-                                                 uint64_t ntiles, double total, uint64_t seed,
-                                                 uint64_t s) {
+__device__ __forceinline__ uint64_t resolve_shot(const float4 *__restrict__ st, const TileScan *ts,
+                                                 const double *s_prefix, uint64_t ntiles,
+                                                 double total, uint64_t seed, uint64_t s) {
   const double u = shot_uniform(seed, s);
   const uint32_t t = find_tile(s_prefix, ntiles, u * total);
   const TileScan &T = ts[t];
   const double r = u * total - s_prefix[t];
-  int lo = 0, hi = kChunksPerTile;  // chunk: smallest i with incl[i] > r
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (gt_nonneg(T.incl[mid], r)) hi = mid; else lo = mid + 1;
-  }
-  if (lo >= kChunksPerTile) {  // rounding past the tile end
-    lo = kChunksPerTile - 1;
-    while (lo > 0 && !(T.chunk[lo] > 0.f)) --lo;
-  }
-  const double rl = r - (lo > 0 ? T.incl[lo - 1] : 0.0);
-  const float rlf = __double2float_rd(rl);  // f > rl  <=>  f > rlf for every float f
-  const int warp_of = lo >> 5, lane_of = lo & 31;
-  const float *row = T.cum + warp_of * 32 * kPad + lane_of * kPad;
-  int a = 0, b = kChunk;  // first running sum above rl
+  const int c = find_chunk(T.incl, T.chunk, r);
+  const double rl = r - (c > 0 ? T.incl[c - 1] : 0.0);
+  const float rlf = (float)rl;
+  const float *row = T.cum + c * kPad;
+  int a = 0, b = kChunk;  // first FP32 running sum above rl
   while (a < b) {
     const int mid = (a + b) >> 1;
     if (row[mid] > rlf) b = mid; else a = mid + 1;
   }
-  const int pick = a < kChunk ? a : (int)T.last_nz[lo];
-  return t * kSampTile + (uint64_t)warp_of * 512 + (uint64_t)lane_of * kChunk + pick;
+  const float tol = T.chunk[c] * 0x1p-17f;
+  const bool clear = a < kChunk && row[a] > rlf + tol && (a == 0 || row[a - 1] < rlf - tol);
+  const uint64_t base = (uint64_t)t * kSampTile + (uint64_t)c * kChunk;
+  const int pick = clear ? a : chunk_pick(st + base / 2, rl);
+  return base + pick;
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -351,41 +440,47 @@ resolve_resident_kernel(const float4 *__restrict__ st, uint64_t ntiles,
                         const double *__restrict__ prefix, uint64_t seed, int64_t shots,
                         uint64_t *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
-  TileScan *ts = reinterpret_cast<TileScan *>(s_dyn);  // [ntiles]
+  TileScan *ts = reinterpret_cast<TileScan *>(s_dyn);                      // [ntiles]
+  float4 *s_amp = reinterpret_cast<float4 *>(s_dyn + sizeof(TileScan) * ntiles);  // one tile
   __shared__ float2 s_wtot[kWarps];
   __shared__ double s_prefix[kResidentTiles + 1];
   if (threadIdx.x <= ntiles) s_prefix[threadIdx.x] = prefix[threadIdx.x];
   for (uint64_t t = 0; t < ntiles; ++t) {
-    float c;
-    tile_chunk_scan(st, t, ts[t].cum, ts[t].incl, s_wtot, &c);
-    ts[t].chunk[threadIdx.x] = c;
-    // this thread's chunk: weights -> running sums (the walk's FP32 order)
-    float *row = ts[t].cum + (threadIdx.x >> 5) * 32 * kPad + (threadIdx.x & 31) * kPad;
+    float ch, cl;
+    tile_chunk_scan(st, t, s_amp, ts[t].incl, s_wtot, ch, cl);
+    ts[t].chunk[threadIdx.x] = ch;
+    // this thread's chunk: FP32 running sums of its weights' leading words
+    const float4 *arow = s_amp + threadIdx.x * kRowVec;
+    float *crow = ts[t].cum + threadIdx.x * kPad;
     float run = 0.f;
-    int last = 0;
-    for (int i = 0; i < kChunk; ++i) {
-      const float wi = row[i];
-      run += wi;
-      if (wi > 0.f) last = i;
-      row[i] = run;
+#pragma unroll
+    for (int i = 0; i < kChunk / 2; ++i) {
+      const float4 v = arow[i];
+      float wh, wl;
+      weight_df(v.x, v.y, wh, wl);
+      run += wh;
+      crow[2 * i] = run;
+      weight_df(v.z, v.w, wh, wl);
+      run += wh;
+      crow[2 * i + 1] = run;
     }
-    ts[t].last_nz[threadIdx.x] = (uint8_t)last;
-    __syncthreads();
+    __syncthreads();  // s_amp is rewritten for the next tile
   }
   const double total = s_prefix[ntiles];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // two shots per thread in flight: independent chains of shared-memory loads
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < shots; s += 2 * stride) {
     const int64_t s2 = s + stride;
-    const uint64_t z = resolve_shot(ts, s_prefix, ntiles, total, seed, (uint64_t)s);
+    const uint64_t z = resolve_shot(st, ts, s_prefix, ntiles, total, seed, (uint64_t)s);
     uint64_t z2 = 0;
-    if (s2 < shots) z2 = resolve_shot(ts, s_prefix, ntiles, total, seed, (uint64_t)s2);
+    if (s2 < shots) z2 = resolve_shot(st, ts, s_prefix, ntiles, total, seed, (uint64_t)s2);
     out[s] = z;
     if (s2 < shots) out[s2] = z2;
   }
 }
 
-// Small states (N <= 2048): exact FP64 CDF in shared memory, built by every
+// Small states (N <= 2048): FP64 CDF in shared memory (exact squares of the
+// complex64 parts, running sum with Neumaier's compensation), built by every
 // CTA, shots in a grid-stride range.
 __global__ void __launch_bounds__(kThreads)
 sample_small_kernel(const float2 *__restrict__ st, int n, uint64_t seed, int64_t shots,
@@ -398,10 +493,13 @@ sample_small_kernel(const float2 *__restrict__ st, int n, uint64_t seed, int64_t
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double run = 0.0;
+    double run = 0.0, carry = 0.0;
     for (int z = 0; z < N; ++z) {
-      run += s_cdf[z];
-      s_cdf[z] = run;
+      const double w = s_cdf[z];
+      const double t = run + w;
+      carry += fabs(run) >= fabs(w) ? (run - t) + w : (w - t) + run;
+      run = t;
+      s_cdf[z] = run + carry;
     }
   }
   __syncthreads();
@@ -421,9 +519,13 @@ sample_small_kernel(const float2 *__restrict__ st, int n, uint64_t seed, int64_t
 struct SampleWs {
   double *tsum;        // [ntiles]
   double *prefix;      // [ntiles + 1]
+  DD *scan_loc;        // [ntiles]   in-CTA prefixes of the tile-total scan
+  DD *scan_tot;        // [groups]   CTA totals of the tile-total scan
   uint32_t *count;     // [ntiles]
   uint32_t *cursor;    // [ntiles]
   uint32_t *offset;    // [ntiles + 1]
+  uint32_t *cnt_loc;   // [ntiles]   the same for the shot counts
+  uint32_t *cnt_tot;   // [groups]
   uint32_t *shot_tile; // [shots]
   uint32_t *bucket;    // [shots]
 };
@@ -435,20 +537,29 @@ static size_t sample_ws_layout(uint64_t ntiles, int64_t shots, char *base, Sampl
     off = round_up(off + bytes, 256);
     return o;
   };
+  const uint64_t groups = (ntiles + kScanThreads - 1) / kScanThreads;
   size_t o1 = take(sizeof(double) * ntiles);
   size_t o2 = take(sizeof(double) * (ntiles + 1));
-  size_t o3 = take(sizeof(uint32_t) * ntiles * 2);  // count and cursor, adjacent
-  size_t o5 = take(sizeof(uint32_t) * (ntiles + 1));
-  size_t o6 = take(sizeof(uint32_t) * (size_t)shots);
-  size_t o7 = take(sizeof(uint32_t) * (size_t)shots);
+  size_t o3 = take(sizeof(DD) * ntiles);
+  size_t o4 = take(sizeof(DD) * groups);
+  size_t o5 = take(sizeof(uint32_t) * ntiles * 2);  // count and cursor, adjacent
+  size_t o6 = take(sizeof(uint32_t) * (ntiles + 1));
+  size_t o7 = take(sizeof(uint32_t) * ntiles);
+  size_t o8 = take(sizeof(uint32_t) * groups);
+  size_t o9 = take(sizeof(uint32_t) * (size_t)shots);
+  size_t o10 = take(sizeof(uint32_t) * (size_t)shots);
   if (w) {
     w->tsum = reinterpret_cast<double *>(base + o1);
     w->prefix = reinterpret_cast<double *>(base + o2);
-    w->count = reinterpret_cast<uint32_t *>(base + o3);
+    w->scan_loc = reinterpret_cast<DD *>(base + o3);
+    w->scan_tot = reinterpret_cast<DD *>(base + o4);
+    w->count = reinterpret_cast<uint32_t *>(base + o5);
     w->cursor = w->count + ntiles;
-    w->offset = reinterpret_cast<uint32_t *>(base + o5);
-    w->shot_tile = reinterpret_cast<uint32_t *>(base + o6);
-    w->bucket = reinterpret_cast<uint32_t *>(base + o7);
+    w->offset = reinterpret_cast<uint32_t *>(base + o6);
+    w->cnt_loc = reinterpret_cast<uint32_t *>(base + o7);
+    w->cnt_tot = reinterpret_cast<uint32_t *>(base + o8);
+    w->shot_tile = reinterpret_cast<uint32_t *>(base + o9);
+    w->bucket = reinterpret_cast<uint32_t *>(base + o10);
   }
   return off;
 }
@@ -497,12 +608,17 @@ extern "C" int gqaoa_sample(const void *state, int n, uint64_t seed, int64_t sho
   const float4 *s4 = static_cast<const float4 *>(state);
   const int sms = sms0;
   const unsigned tgrid = (unsigned)(ntiles < (uint64_t)sms * 8 ? ntiles : (uint64_t)sms * 8);
+  const unsigned groups = (unsigned)((ntiles + kScanThreads - 1) / kScanThreads);
   tile_sum_kernel<<<tgrid, kThreads, 0, st>>>(s4, ntiles, w.tsum);
   GQ_CHECK_LAUNCH();
-  scan_tiles_kernel<<<1, 1024, 0, st>>>(w.tsum, ntiles, w.prefix);
+  scan_local_kernel<SumDD><<<groups, kScanThreads, 0, st>>>(w.tsum, ntiles, w.scan_loc,
+                                                            w.scan_tot);
+  GQ_CHECK_LAUNCH();
+  scan_finish_kernel<SumDD><<<groups, kScanThreads, 0, st>>>(w.scan_loc, ntiles, w.scan_tot,
+                                                             w.prefix);
   GQ_CHECK_LAUNCH();
   if (ntiles <= (uint64_t)kResidentTiles) {
-    const size_t dyn = sizeof(TileScan) * ntiles;
+    const size_t dyn = sizeof(TileScan) * ntiles + sizeof(float4) * kWarps * 32 * kRowVec;
     if (cudaFuncSetAttribute(resolve_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)dyn) != cudaSuccess)
       return GQAOA_ECUDA;
@@ -521,7 +637,11 @@ extern "C" int gqaoa_sample(const void *state, int n, uint64_t seed, int64_t sho
                                                                       : (int64_t)sms * 16);
   shot_tile_kernel<<<sgrid, kThreads, 0, st>>>(w.prefix, ntiles, seed, shots, w.shot_tile, w.count);
   GQ_CHECK_LAUNCH();
-  scan_counts_kernel<<<1, 1024, 0, st>>>(w.count, ntiles, w.offset);
+  scan_local_kernel<SumU32><<<groups, kScanThreads, 0, st>>>(w.count, ntiles, w.cnt_loc,
+                                                             w.cnt_tot);
+  GQ_CHECK_LAUNCH();
+  scan_finish_kernel<SumU32><<<groups, kScanThreads, 0, st>>>(w.cnt_loc, ntiles, w.cnt_tot,
+                                                              w.offset);
   GQ_CHECK_LAUNCH();
   scatter_kernel<<<sgrid, kThreads, 0, st>>>(w.shot_tile, shots, w.offset, w.cursor, w.bucket);
   GQ_CHECK_LAUNCH();

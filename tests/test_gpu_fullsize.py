@@ -16,6 +16,7 @@ import torch
 from oracle import reduced, statevector as sv
 from paper_2402_02585_gb300 import _capi as C
 from paper_2402_02585_gb300 import core, instances
+from tests.shot_compare import compare_same_state
 
 pytestmark = pytest.mark.gpu
 
@@ -70,13 +71,21 @@ def test_every_amplitude_matches_cost_class_model(run):
 
 
 def test_readout_and_trace(run):
+    # P(C=0) is about 7e-8 here, so an absolute 1e-6 would accept P = 0: the
+    # solution probability and its per-round trace are bounded relative to
+    # their own size (complex64 rounding over 100 rounds moves P by ~1e-6 of
+    # itself; 1e-4 leaves that margin and still catches a wrong amplitude)
     h = run["ref_hist"]
     _, tr = reduced.evolve(h, run["g"], run["b"], trace=True)
     r = reduced.readout(h, run["f"])
-    assert abs(run["out"][0] - r[0]) < 1e-6
+    rel = abs(run["out"][0] - r[0]) / r[0]
+    rel_tr = np.max(np.abs(run["trace"] - tr) / (tr + 1e-300))
+    print(f"P(C=0) = {run['out'][0]:.6e} (oracle {r[0]:.6e}), relative error {rel:.2e}; "
+          f"largest relative error of the per-round trace {rel_tr:.2e}")
+    assert r[0] > 0 and abs(run["out"][0] - r[0]) <= 1e-4 * r[0] + 1e-12
+    assert np.all(np.abs(run["trace"] - tr) <= 1e-4 * tr + 1e-12)
     assert abs(run["out"][1] - r[1]) < 1e-4 * M_CLAUSES / 8
     assert abs(run["out"][2] - 1.0) < 1e-5
-    assert np.max(np.abs(run["trace"] - tr)) < 1e-6
 
 
 def test_shots_valid_against_exact_cdf(run):
@@ -99,6 +108,16 @@ def test_shots_valid_against_exact_cdf(run):
     tol = 1e-5 * total
     miss = np.maximum(np.maximum(lo - t, t - hi), 0.0)
     assert np.max(miss) <= tol, np.max(miss) / total
+
+
+def test_shots_match_oracle_on_the_same_state(run):
+    # the oracle samples the GPU's own complex64 state (upcast to FP64): the
+    # shots are index work and must be identical except where a target lies
+    # within the CDFs' rounding (a few FP64 units of the norm) of a boundary
+    psi = run["state"].cpu().numpy().astype(np.complex128)
+    ref, cdf = sv.sample(psi, N_VARS, seed=12345, shots=SHOTS, return_cdf=True)
+    del psi
+    compare_same_state(run["shots"], ref, cdf, 12345, eps=1e-14 * cdf[-1], label="n=28")
 
 
 def test_shot_classes_follow_cost_class_weights(run):

@@ -462,6 +462,25 @@ def test_sample_is_inverse_cdf():
     assert np.array_equal(shots, ref.astype(np.uint32))
 
 
+def test_sample_cdf_is_exact_sum_of_weights():
+    # Every assignment of one cost class has the same weight, so a plain FP64
+    # running sum rounds the same way again and again and drifts; the CDF must
+    # instead stay within a few units in the last place of the exact prefix
+    # sum (checked in rational arithmetic) over 2^20 terms.
+    from fractions import Fraction
+    n = 20
+    a = float(np.float32(0.3))  # a complex64 amplitude: a^2 is exact in FP64
+    psi = np.full(1 << n, a, dtype=np.complex128)
+    _, cdf = sv.sample(psi, n, seed=1, shots=1, return_cdf=True)
+    w = Fraction(a * a)
+    assert a * a == float(w)
+    for z in (0, 1, 1000, 123457, (1 << 19) + 3, (1 << n) - 1):
+        exact = (z + 1) * w
+        assert abs(Fraction(cdf[z]) - exact) <= 4 * np.spacing(cdf[z]), z
+    run = np.cumsum(np.full(1 << n, a * a))  # the plain running sum drifts here
+    assert abs(Fraction(run[-1]) - (1 << n) * w) > 100 * np.spacing(run[-1])
+
+
 def test_sample_distribution_chi_square():
     import scipy.stats
     n, m, p = 6, 24, 4
