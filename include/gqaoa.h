@@ -31,6 +31,11 @@
  *  - Complex state: complex64, interleaved (float re, float im), 8 bytes per
  *    amplitude, index z. Alignment: 16 bytes.
  *  - Sizes: 1 <= n <= GQAOA_MAX_N, 0 <= m <= GQAOA_MAX_M, 1 <= p.
+ *  - Per-device state: the library caches, per device ordinal, the SM count,
+ *    the occupancy of its clustered passes and (gqaoa_evolve_noalloc) the
+ *    device address of its static scratch. cudaDeviceReset destroys the
+ *    context those belong to, so a process must not call the library on a
+ *    device after resetting it.
  */
 #ifndef GQAOA_H
 #define GQAOA_H
@@ -231,6 +236,18 @@ int gqaoa_grad_batched(const uint8_t *cost, int64_t cost_stride, int n, int m, i
                        void *stream);
 
 /*
+ * Launch geometry of the streaming passes of gqaoa_evolve_batched and
+ * gqaoa_grad_batched (adjoint = 0: forward rounds; 1: adjoint rounds) for
+ * `batch` instances of 2^n amplitudes on the current device: the CTAs that
+ * share one instance and the per-round reduction records each instance's
+ * mixer sum <+|chi_k> (Eq. 2) is combined from. batch = 1 is the geometry
+ * of gqaoa_evolve and gqaoa_grad. A query only: nothing is launched.
+ * Errors: GQAOA_EINVAL (NULL outputs), GQAOA_ERANGE (n, batch).
+ */
+int gqaoa_batched_geometry(int n, int batch, int adjoint, int *ctas_per_instance,
+                           int *records_per_instance);
+
+/*
  * Single-angle-pair sweep (Eq. 5; Appendix C's grid scan): `batch` instances
  * of equal n times `angles` angle points, each evolved p rounds from |+> with
  * gamma_k = gammas[a], beta_k = betas[a], and P(C=0) read out after each
@@ -405,10 +422,12 @@ int gqaoa_adam_f64(double *params, const double *grads, double *m, double *v, in
  * every GPU loading the library holds until the process exits. p is limited
  * to 1..GQAOA_NOALLOC_MAX_P (GQAOA_ERANGE beyond). The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make it before any stream capture. All calls on a
- * device share the array: calls whose GPU work overlaps race and must be
- * serialised by the caller. No scratch word needs to start at zero; the
- * contents left by a previous call are overwritten before use.
+ * that device current; make it before any stream capture. The address is
+ * kept for the life of the process, so the entry point must not be called on
+ * a device after cudaDeviceReset. All calls on a device share the array:
+ * calls whose GPU work overlaps race and must be serialised by the caller. No
+ * scratch word needs to start at zero; the contents left by a previous call
+ * are overwritten before use.
  */
 #define GQAOA_NOALLOC_MAX_P 256
 #define GQAOA_NOALLOC_SCRATCH_BYTES (1u << 20) /* 1 MiB */

@@ -41,6 +41,8 @@ GQAOA_SWEEP_MAX_N = 19
 GQAOA_SWEEP_L2 = 1
 GQAOA_SWEEP_L2_MIN_N = 20
 GQAOA_SWEEP_L2_MAX_N = 24
+GQAOA_NOALLOC_MAX_P = 256
+GQAOA_NOALLOC_SCRATCH_BYTES = 1 << 20
 
 
 class GQAOAError(RuntimeError):
@@ -76,6 +78,7 @@ SIGNATURES = {
     "gqaoa_grad": [_P, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P],
     "gqaoa_grad_batched_workspace_size": [_I, _I, _I, _SZP],
     "gqaoa_grad_batched": [_P, _I64, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P],
+    "gqaoa_batched_geometry": [_I, _I, _I, _P, _P],
     "gqaoa_evolve_noalloc": [_P, _I, _I, _P, _P, _I, _P, _P, _P, _U, _P],
     "gqaoa_sweep_workspace_size": [_I, _I, _I, _SZP],
     "gqaoa_reduced_sweep_workspace_size": [_I, _SZP],
@@ -264,3 +267,13 @@ def gqaoa_evolve_noalloc(cost, n, m, gammas, betas, p, state, out, trace, flags,
     """gqaoa_evolve with the library's fixed static scratch instead of a
     caller workspace (for callers that cannot allocate device memory)."""
     _call("gqaoa_evolve_noalloc", cost, n, m, gammas, betas, p, state, out, trace, flags, stream)
+
+
+def gqaoa_batched_geometry(n, batch, adjoint) -> tuple[int, int]:
+    """(CTAs per instance, reduction records per instance) of the batched
+    streaming passes (adjoint: the gradient's backward rounds)."""
+    cpi = ctypes.c_int(0)
+    rec = ctypes.c_int(0)
+    _call("gqaoa_batched_geometry", n, batch, int(bool(adjoint)), ctypes.byref(cpi),
+          ctypes.byref(rec))
+    return int(cpi.value), int(rec.value)

@@ -1282,6 +1282,17 @@ extern "C" int gqaoa_evolve_batched(const uint8_t *cost, int64_t cost_stride, in
                      ws, ws_bytes, flags, static_cast<cudaStream_t>(stream));
 }
 
+extern "C" int gqaoa_batched_geometry(int n, int batch, int adjoint, int *ctas_per_instance,
+                                      int *records_per_instance) {
+  if (!ctas_per_instance || !records_per_instance) return GQAOA_EINVAL;
+  int rc = check_common(n, 0, batch, 1);
+  if (rc) return rc;
+  const Geometry g = make_geometry(n, batch, adjoint ? kBwdPerSm : kFwdPerSm);
+  *ctas_per_instance = g.cpi;
+  *records_per_instance = g.nparts;
+  return GQAOA_OK;
+}
+
 extern "C" int gqaoa_grad_workspace_size(int n, int p, size_t *bytes) {
   return gqaoa_grad_batched_workspace_size(n, 1, p, bytes);
 }

@@ -56,6 +56,24 @@ def test_workspace_sizes_monotone():
     assert C.gqaoa_prob_workspace_size(28) > 0
 
 
+def test_batched_geometry_query():
+    # below one 4096-amplitude tile an instance is one CTA; at n = 16 a batch
+    # spreads each instance over several CTAs and reduction records, never
+    # more CTAs than tiles. (Without a device the library assumes 152 SMs.)
+    assert C.gqaoa_batched_geometry(11, 64, 0) == (1, 1)
+    for B in (8, 64, 1024):
+        for adjoint in (0, 1):
+            cpi, rec = C.gqaoa_batched_geometry(16, B, adjoint)
+            assert 1 <= rec <= cpi <= 16
+    cpi, rec = C.gqaoa_batched_geometry(16, 64, 1)
+    assert cpi >= 2 and rec == cpi  # a batch runs without clusters
+    cpi, rec = C.gqaoa_batched_geometry(24, 1, 0)
+    assert cpi > rec >= 1  # one instance: clusters of CTAs, one record per cluster
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_batched_geometry(16, 0, 0)
+    assert e.value.status == C.GQAOA_ERANGE
+
+
 @pytest.mark.parametrize("args,code", [
     ((0, 10), C.GQAOA_ERANGE),
     ((35, 10), C.GQAOA_ERANGE),
