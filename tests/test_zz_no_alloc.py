@@ -3,8 +3,10 @@ allocate device memory (no workspace argument; the library's fixed static
 scratch is used instead). It must give the same results as gqaoa_evolve with
 a caller workspace, on consecutive calls that share that scratch.
 
-This file is collected last on purpose, so that a run stopping at the first
-failure has already run every other test.
+The file name sorts last, so a run that stops at its first failure has run
+every other test before this one. The test does not rely on that order: it
+waits for all earlier GPU work before its first call, so it passes alone in
+a fresh process as well as after the other tests.
 """
 
 import numpy as np
@@ -17,15 +19,19 @@ from paper_2402_02585_gb300 import core, instances
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n,m,p", [(10, 42, 8), (16, 67, 12), (20, 84, 5)])
+# (22, 92, 256): the streaming path on clustered CTAs at the largest round
+# count the static scratch takes, i.e. its largest workspace layout
+@pytest.mark.parametrize("n,m,p", [(10, 42, 8), (16, 67, 12), (20, 84, 5), (22, 92, 256)])
 def test_noalloc_matches_workspace_evolve_twice(n, m, p):
     lits = instances.random_3sat(n, m, 5)
     g, b = instances.random_angles(p, 5)
     cost, _ = core.build_cost(lits, n)
     ref_state, ref_out, ref_tr = core.evolve(cost, n, m, g, b, trace=True)
+    assert C.gqaoa_evolve_workspace_size(n, p) <= C.GQAOA_NOALLOC_SCRATCH_BYTES
     gd = torch.as_tensor(g, device="cuda")
     bd = torch.as_tensor(b, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()  # nothing else in flight may still use the shared scratch
     for _ in range(2):  # the second call reuses the scratch the first one left behind
         state = torch.full((1 << n,), 7.0 + 7.0j, dtype=torch.complex64, device="cuda")
         out = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
