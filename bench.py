@@ -73,6 +73,17 @@ WORKLOADS = {
                                  "L-BFGS-B with statevector adjoint gradients, fewest "
                                  "single-angle-pair rounds to a Max-SAT probability D >= 50 % on "
                                  "the statevector"),
+    # the same protocol over the paper's sizes (Section III: up to 26 qubits;
+    # the pi/180 grid up to n = 20, 4000 sampled angle pairs above), for the
+    # fitted exponent of the fewest rounds against 1/P over that range; a
+    # warm-up pass runs the first warm_count instances only
+    "protocol_scaling": dict(kind="protocol", count=45, n_values=list(range(10, 25)), d_lo=2.0,
+                             d_hi=4.5, S=0.5, p_max=64, retry_p_max=256, seed=2, warm_count=4,
+                             desc="45 satisfiable random 3-SAT instances, n uniform in 10..24, d "
+                                  "uniform in (2, 4.5); <H_P> on the pi/180 grid (n <= 20) or 4000 "
+                                  "sampled angle pairs (n > 20) by the cost-class model, L-BFGS-B "
+                                  "with statevector adjoint gradients at every depth, fewest "
+                                  "single-angle-pair rounds to P >= 50 % on the statevector"),
     # Section IV's fair-sampling metrics on a satisfiable instance at the
     # protocol's fewest-rounds angles: one step = sample runs x shots_per_run
     # shots and compute both metrics for every run
@@ -83,6 +94,18 @@ WORKLOADS = {
                           "of 2048 shots from gqaoa_sample; shots to see every solution and "
                           "chi-square draws (alpha 0.05, from 5 M draws) to reject uniform "
                           "solution sampling, per run"),
+    # the learned angle proposer (config 5): labels from the batched gradient
+    # optimizer on 20000 training instances, the MLP trained on them, and the
+    # wall time to 95 % of the plain optimizer's P(C=0) on 2000 held-out n = 20
+    # instances; one step = the whole study (a warm-up step is the same study
+    # at 1/100 of the instance counts)
+    "study": dict(kind="study", train=20000, train_n=list(range(10, 19)), test=2000, test_n=[20],
+                  d_lo=3.0, d_hi=5.0, p=16, seed=0,
+                  desc="learned angle proposer: MLP 130-256-256-32 (GELU) trained on 20000 "
+                       "satisfiable random 3-SAT instances, n uniform in 10..18, d uniform in "
+                       "[3, 5], labels from Adam over all 2p angles (p = 16) after a 16x16 "
+                       "single-angle-pair grid; evaluated on 2000 satisfiable n = 20 instances: "
+                       "wall time to 95 % of the plain optimizer's final P(C=0)"),
     # the profiling case: same recipe, state (512 MiB) still far larger than L2
     "profile": dict(n=26, m=109, p=8, shots=100_000, seed=0,
                     desc="random 3-SAT n=26 m=109 (d~4.2) seed 0, p=8 random angles, 1e5 shots"),
@@ -736,14 +759,16 @@ def run_protocol(args, wl):
 
     workers = int(os.environ.get("GQAOA_PROTOCOL_WORKERS", "8"))
 
-    def one_pass():
+    retry = wl.get("retry_p_max", 4 * wl["p_max"])
+
+    def one_pass(count=None):
         # several instances in flight (host threads, one CUDA stream each)
-        return min_rounds_many([pr for _, _, _, pr in prots], workers=workers,
-                               retry_p_max=4 * wl["p_max"], S=wl["S"], p_max=wl["p_max"],
-                               target=target)
+        sel = prots if count is None else prots[:count]
+        return min_rounds_many([pr for _, _, _, pr in sel], workers=workers, retry_p_max=retry,
+                               S=wl["S"], p_max=wl["p_max"], target=target)
 
     for _ in range(args.warmup):
-        one_pass()
+        one_pass(wl.get("warm_count"))
     # the grid call alone (phase tables + cost-class kernel, no argmin), on
     # the full pi/180 grid of the first instance, buffers resident
     G, B = instances.protocol_grid()
@@ -791,6 +816,9 @@ def run_protocol(args, wl):
     pm = np.array([r.p if r.p is not None else np.nan for r in results], dtype=np.float64)
     ok = np.isfinite(pm)
     slope = float(np.polyfit(np.log(1 / pr[ok]), np.log(pm[ok]), 1)[0]) if ok.sum() > 2 else None
+    big = ok & (pr < 1e-3)  # the large-1/P regime of Section III's asymptotic claim
+    slope_big = (float(np.polyfit(np.log(1 / pr[big]), np.log(pm[big]), 1)[0])
+                 if big.sum() > 2 else None)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     # grid call: the cost-class arithmetic is 14 FP32 instructions per class
     # and round (phase and mixer 8, readout 6); the ceiling issues them at
@@ -807,7 +835,9 @@ def run_protocol(args, wl):
             "vs_baseline": None, "dtype": "c64 (grid, statevector) + f64 optimiser",
             "data": "synthetic",
             "config": {"workload": wl["desc"], "instances": len(prots), "S": wl["S"],
-                       "p_max": wl["p_max"], "host_threads": workers},
+                       "p_max": wl["p_max"], "retry_p_max": retry, "host_threads": workers,
+                       "warmup_pass": "all instances" if wl.get("warm_count") is None
+                       else f"the first {wl['warm_count']} instances"},
             "roofline": {"bound": "alu", "achieved": grid_rate, "peak": alu_peak,
                          "unit": "item-rounds/s", "frac": grid_rate / alu_peak,
                          "kernel": f"gqaoa_reduced_sweep (phase tables + reduced_sweep_kernel): "
@@ -817,9 +847,13 @@ def run_protocol(args, wl):
                                             f"instructions x {classes} classes / 32 lanes) per "
                                             "item-round"},
             "p_min": [None if r.p is None else int(r.p) for r in results],
+            "n": [int(n) for n, _, _, _ in prots],
+            "seconds_per_instance": [round(float(r.seconds), 4) for r in results],
             "target": target,
             "random_guess_probability": [float(x) for x in pr],
             "fitted_exponent": slope,
+            "fitted_exponent_one_over_P_above_1e3": slope_big,
+            "median_p_sqrt_P": float(np.median(pm[ok] * np.sqrt(pr[ok]))) if ok.any() else None,
             "gradient_evaluations_per_instance": float(np.mean([r.evaluations for r in results])),
             "cpu_baseline": cpu_protocol_baseline(wl, shapes) if world == 1 else None,
             "gpu_launches": int(sum(r.launches for r in results)) * args.steps, "clocks": clk}),
@@ -911,6 +945,73 @@ def run_fairness(args, wl):
     return 0
 
 
+def run_study(args, wl):
+    """Workload "study": the learned-initialisation study of the proposer
+    (study.run). Value: the median wall time for the optimizer started from the
+    proposal to reach 95 % of the plain optimizer's final P(C=0) (Adam from
+    angles uniform in [0, pi), 200 steps), fallbacks charged both runs; the
+    plain optimizer's own median, the grid-protocol baseline, hit and
+    fallback rates and each phase's time beside it."""
+    import torch
+
+    from paper_2402_02585_gb300 import study
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    quiet = lambda *a, **k: None  # noqa: E731
+    for i in range(args.warmup):
+        study.run(train_count=max(1, wl["train"] // 100), train_n=wl["train_n"],
+                  test_count=max(1, wl["test"] // 100), test_n=wl["test_n"], d_lo=wl["d_lo"],
+                  d_hi=wl["d_hi"], p=wl["p"], epochs=5, seed=wl["seed"] + 100 + i, log=quiet)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    results = []
+    for i in range(args.steps):
+        results.append(study.run(train_count=wl["train"], train_n=wl["train_n"],
+                                 test_count=wl["test"], test_n=wl["test_n"], d_lo=wl["d_lo"],
+                                 d_hi=wl["d_hi"], p=wl["p"], seed=wl["seed"] + i, log=quiet))
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    clk = clocks.stop()
+    r = results[-1]
+    # the dominant kernels are the batched adjoint passes of the label phase:
+    # per Adam step and instance 9 + 17 (p - 1) + 17 + 25 p bytes per amplitude
+    # (forward rounds with checkpoints, lambda init, backward rounds)
+    p = wl["p"]
+    label_bytes = r["label_amplitudes_x_steps"] * (9 + 17 * (p - 1) + 17 + 25 * p)
+    achieved = label_bytes / r["timings"]["labels_s"] / 1e9
+    peak, peak_kind = hbm_peak()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "learned-init angle optimisation: median wall-s to 95 % of plain P(C=0)",
+            "value": r["median_wall_proposer"], "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 state + f64 angles (optimizer), f32 MLP", "data": "synthetic",
+            "config": {"workload": wl["desc"], "train_instances": r["train_instances"],
+                       "test_instances": r["test_instances"], "p": p,
+                       "warmup_step": "the same study at 1/100 of the instance counts"},
+            "plain": {"median_wall_s": r["median_wall_plain"],
+                      "median_steps": r["median_steps_plain"], "mean_P": r["mean_P_plain"]},
+            "proposer": {"median_wall_s": r["median_wall_proposer"],
+                         "median_steps": r["median_steps_proposer"], "hit_rate": r["hit_rate"],
+                         "fallback_rate": r["fallback_rate"],
+                         "mean_P_final": r["mean_P_proposer_final"],
+                         "inference_s_total": r["proposer_inference_s"]},
+            "grid_protocol_baseline": r["grid"],
+            "timings_s": r["timings"], "loss": [r["loss_first"], r["loss_last"]],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "label phase: batched adjoint gradient + Adam (algorithmic "
+                                   "bytes of the forward and backward passes over the phase's "
+                                   "wall time, host work included)"},
+            "cpu_baseline": None,
+            "gpu_launches": r["gpu_launches"], "clocks": clk}), flush=True)
+    return 0
+
+
 def C_size_sample(n, shots):
     from paper_2402_02585_gb300 import _capi as C
     return C.gqaoa_sample_workspace_size(n, shots)
@@ -951,15 +1052,16 @@ def cpu_protocol_baseline(wl, shapes):
     from paper_2402_02585_gb300 import instances
     if os.environ.get("GQAOA_BENCH_NO_CPU") == "1":
         return None
-    G, B = instances.protocol_grid()
+    from paper_2402_02585_gb300.protocol import grid_for
     t0 = time.perf_counter()
     for n, m, _, _, _, hist in shapes[:2]:
+        G, B = grid_for(n)
         oprot.min_rounds(hist.cpu().numpy(), G, B, S=wl["S"], p_max=wl["p_max"],
                          target=wl.get("target", "P"))
     t = time.perf_counter() - t0
     return {"value": 2 / t, "unit": "instances/s", "cores": 1, "kind": "oracle",
-            "sample": "the first two instances, full protocol (numpy/scipy, FP64 cost-class "
-                      "model for grid, refinement and probability)"}
+            "sample": "the first two instances, full protocol up to p_max (numpy/scipy, FP64 "
+                      "cost-class model for grid, refinement and probability)"}
 
 
 def cpu_sweep_baseline(wl):
@@ -1016,7 +1118,7 @@ def main():
     args = parse()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
-        if wl.get("kind") in ("grad", "sweep"):
+        if wl.get("kind") in ("grad", "sweep", "study"):
             print(json.dumps({"impl": "reference", "unavailable": "this workload has no "
                               "bounded oracle arm; run the default workload"}))
             return 0
@@ -1029,6 +1131,8 @@ def main():
         return run_fairness(args, wl)
     if wl.get("kind") == "sweep":
         return run_sweep(args, wl)
+    if wl.get("kind") == "study":
+        return run_study(args, wl)
     return run_ours(args, wl)
 
 

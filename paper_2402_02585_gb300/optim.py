@@ -38,6 +38,8 @@ class AngleOptimizer:
         self.value = torch.zeros(self.B, dtype=torch.float64, device=dev)
         self.ws = core.workspace(C.gqaoa_grad_batched_workspace_size(n, self.B, p), dev)
         self.t = 0
+        self.launches = 0        # kernels launched by the library for this optimizer
+        self.amp_evaluations = 0  # instances x 2^n x gradient evaluations
 
     def reset(self, gammas, betas):
         self.theta[0].copy_(torch.as_tensor(gammas, dtype=torch.float64))
@@ -54,6 +56,10 @@ class AngleOptimizer:
                              core.objective_code(self.objective), self.value.data_ptr(),
                              self.grad[0].data_ptr(), self.grad[1].data_ptr(), self.ws.data_ptr(),
                              self.ws.numel(), s)
+        # phase tables + one-CTA forward + adjoint below a tile, else phase
+        # tables, p forward rounds, lambda init, p adjoint rounds, finalize
+        self.launches += 3 if (1 << self.n) < 4096 else 2 * self.p + 3
+        self.amp_evaluations += self.B << self.n
         return self.value
 
     def step(self, lr: float = 0.05, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
@@ -63,6 +69,7 @@ class AngleOptimizer:
         C.gqaoa_adam_f64(self.theta.data_ptr(), self.grad.data_ptr(), self.m1.data_ptr(),
                          self.m2.data_ptr(), self.theta.numel(), lr, beta1, beta2, eps, self.t,
                          self.sign, torch.cuda.current_stream().cuda_stream)
+        self.launches += 1
         return v
 
     def run(self, steps: int, lr: float = 0.05, target: torch.Tensor | None = None):

@@ -38,6 +38,7 @@ class Proposer:
         self.loss = torch.zeros(1, dtype=torch.float64, device=self.device)
         self.t = 0
         self._ws = None
+        self.launches = 0  # kernels launched by the library for this proposer
 
     # ------------------------------------------------------------ features
     def features(self, hists, ns, ms) -> torch.Tensor:
@@ -54,6 +55,7 @@ class Proposer:
         x = torch.empty((B, d_in), dtype=torch.float32, device=self.device)
         C.gqaoa_mlp_features(Hd.data_ptr(), stride, nd.data_ptr(), md.data_ptr(), B, d_in,
                              x.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        self.launches += 1
         return x
 
     def _workspace(self, B):
@@ -70,6 +72,7 @@ class Proposer:
         ws = self._workspace(B)
         C.gqaoa_mlp_forward(self.params.data_ptr(), *self.dims, x.data_ptr(), B, out.data_ptr(),
                             ws.data_ptr(), ws.numel(), torch.cuda.current_stream().cuda_stream)
+        self.launches += 4  # three GEMMs with their epilogues, the output head
         return out
 
     def propose(self, x: torch.Tensor):
@@ -88,6 +91,10 @@ class Proposer:
         self.t += 1
         C.gqaoa_adam_f32(self.params.data_ptr(), self.grads.data_ptr(), self.m1.data_ptr(),
                          self.m2.data_ptr(), self.count, lr, 0.9, 0.999, 1e-8, self.t, 1.0, s)
+        # forward GEMMs (3), loss head and its sum (2), per layer the weight
+        # GEMM, the two-kernel bias column sum and (but the first) the input
+        # GEMM (4 + 4 + 3), Adam (1)
+        self.launches += 17
         return self.loss
 
     def fit(self, x: torch.Tensor, labels: torch.Tensor, epochs: int = 200, batch: int = 512,

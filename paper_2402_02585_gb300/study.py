@@ -29,6 +29,10 @@ from .optim import AngleOptimizer, canonicalize, single_angle_grid_start
 
 CKPT_BUDGET_BYTES = 8 << 30
 
+# kernels launched and instances x 2^n x gradient evaluations of the label
+# phase, accumulated by generate_labels / evaluate / features (run() resets them)
+counters = {"launches": 0, "label_amp_evaluations": 0}
+
 
 def make_instances(count: int, seed: int, n_values, d_lo: float, d_hi: float,
                    sat_only: bool = True, device="cuda"):
@@ -59,6 +63,7 @@ def features(insts, d_in: int = 130, device="cuda") -> torch.Tensor:
     x = torch.empty((B, d_in), dtype=torch.float32, device=device)
     C.gqaoa_mlp_features(Hd.data_ptr(), stride, nd.data_ptr(), md.data_ptr(), B, d_in, x.data_ptr(),
                          torch.cuda.current_stream().cuda_stream)
+    counters["launches"] += 1
     return x
 
 
@@ -86,6 +91,8 @@ def generate_labels(insts, p: int, grid: int = 16, steps: int = 150, lr: float =
         opt.reset(np.repeat(g0[:, None], p, 1), np.repeat(b0[:, None], p, 1))
         opt.run(steps, lr=lr)
         g, b = opt.angles()
+        counters["launches"] += 2 + opt.launches  # grid sweep: phase tables + sweep kernel
+        counters["label_amp_evaluations"] += opt.amp_evaluations
         labels[idx] = canonicalize(g.cpu().numpy(), b.cpu().numpy())
     X = features(insts, d_in)
     Y = torch.as_tensor(labels, dtype=torch.float32, device=X.device)
@@ -139,6 +146,7 @@ def evaluate(prop, test, p: int, plain_steps: int = 200, max_steps: int = 200, l
         infer.append(t_infer)
         opt.reset(g, b)
         run = opt.run(max_steps, lr=lr)
+        counters["launches"] += 2 + opt.launches  # the grid baseline's sweep + the optimizer
         P_prop.extend(run["values"][-1].tolist())
         for key, (pl, t_pre) in base.items():
             final = pl["values"][-1]
@@ -181,6 +189,8 @@ def run(train_count=20000, train_n=range(10, 19), test_count=2000, test_n=(20,),
         plain_steps=200, max_steps=200, seed=0, log=print):
     """The whole study; returns a dict of timings and the evaluation summary."""
     from .proposer import Proposer
+    counters["launches"] = 0
+    counters["label_amp_evaluations"] = 0
     t = {}
     t0 = time.perf_counter()
     train = make_instances(train_count, seed=seed + 1, n_values=train_n, d_lo=d_lo, d_hi=d_hi)
@@ -205,7 +215,9 @@ def run(train_count=20000, train_n=range(10, 19), test_count=2000, test_n=(20,),
     t["evaluate_s"] = time.perf_counter() - t0
     log(f"evaluation: {t['evaluate_s']:.1f} s")
     return {"timings": t, "loss_first": losses[0], "loss_last": losses[-1],
-            "train_instances": len(train), "test_instances": len(test), "p": p, **ev}
+            "train_instances": len(train), "test_instances": len(test), "p": p,
+            "gpu_launches": counters["launches"] + prop.launches,
+            "label_amplitudes_x_steps": counters["label_amp_evaluations"], **ev}
 
 
 if __name__ == "__main__":
