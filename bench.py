@@ -373,10 +373,12 @@ def run_ours(args, wl):
     state = torch.empty(N, dtype=torch.complex64, device=dev)
     out = torch.empty(3, dtype=torch.float64, device=dev)
     shots_out = torch.empty(shots, dtype=torch.int64, device=dev)
-    ws_ev = core.workspace(C.gqaoa_evolve_workspace_size(n, p), dev)
-    ws_sa = core.workspace(C.gqaoa_sample_workspace_size(n, shots), dev)
+    ws_es = core.workspace(C.gqaoa_evolve_sample_workspace_size(n, p, shots), dev)
     lits_c = np.ascontiguousarray(lits, dtype=np.int32)
     sh = stream.cuda_stream
+    # the fused call (rounds, readout pass with the sampler's tile pass, the
+    # tile scan, the shots) applies when 2^n >= 4096 and shots <= 64 per tile
+    fused = N >= 4096 and shots <= 64 * (N // 4096) and N // 4096 > 8
 
     ev_pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                 for _ in range(args.steps)]
@@ -385,14 +387,15 @@ def run_ours(args, wl):
         C.gqaoa_build_cost(lits_c.ctypes.data, n, m, cost.data_ptr(), hist.data_ptr(), sh)
         if pair:
             pair[0].record(stream)
-        C.gqaoa_evolve(cost.data_ptr(), n, m, gam.data_ptr(), bet.data_ptr(), p, state.data_ptr(),
-                       out.data_ptr(), None, ws_ev.data_ptr(), ws_ev.numel(), 0, sh)
+        C.gqaoa_evolve_sample(cost.data_ptr(), n, m, gam.data_ptr(), bet.data_ptr(), p,
+                              state.data_ptr(), out.data_ptr(), None, 12345, shots,
+                              shots_out.data_ptr(), ws_es.data_ptr(), ws_es.numel(), 0, sh)
         if pair:
             pair[1].record(stream)
-        C.gqaoa_sample(state.data_ptr(), n, 12345, shots, shots_out.data_ptr(), ws_sa.data_ptr(),
-                       ws_sa.numel(), sh)
 
-    launches_per_step = 1 + (p + 3) + (6 if N >= 4096 else 1)
+    # cost table; phase tables, p rounds, readout + tile pass, finalize, two
+    # scan launches, resolve (fused); else the evolve and sample launches
+    launches_per_step = 1 + ((p + 3 + 3) if fused else (p + 3) + (6 if N >= 4096 else 1))
 
     for _ in range(args.warmup):
         step()
@@ -452,11 +455,12 @@ def run_ours(args, wl):
     h2d = lits_c.nbytes + h_g.numel() * 8 + h_b.numel() * 8
     d2h = h_shots.numel() * 8 + h_out.numel() * 8
 
-    # ---- roofline of the fused round (evolve call: p rounds + materialise) --
+    # ---- roofline of the fused round (the evolve_sample call) -------------
     # algorithmic bytes: round 1 reads 1 B cost + writes 8 B; rounds 2..p read
-    # 8 B + 1 B and write 8 B; the materialise/readout pass reads 8 B + 1 B and
-    # writes 8 B.
-    alg_bytes = N * (9 + 17 * (p - 1) + 17)
+    # 8 B + 1 B and write 8 B; the readout + tile pass reads 8 B + 1 B (fused
+    # path; the materialising readout pass also writes 8 B). The sampler's scan
+    # and shot passes move a few MB and are counted as time only.
+    alg_bytes = N * (9 + 17 * (p - 1) + (9 if fused else 17 + 8))
     ev_s = statistics.median(evolve_ms) / 1e3
     achieved = alg_bytes / ev_s / 1e9
     peak, peak_kind = hbm_peak()
@@ -488,9 +492,11 @@ def run_ours(args, wl):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "alg_bytes_per_launch": 17 * N,
-                         "kernel": "round_kernel (K2): mean over the p+1 streaming passes of the evolve call",
+                         "kernel": "round_kernel (K2): mean over the p+1 streaming passes of "
+                                   "the evolve_sample call (p rounds, the readout + sampler tile "
+                                   "pass; the sampler's scans and shots included in the time)",
                          "peak_kind": peak_kind,
-                         "evolve_ms": statistics.median(evolve_ms)},
+                         "evolve_sample_ms": statistics.median(evolve_ms)},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -913,9 +919,9 @@ def run_fairness(args, wl):
     done = ta[ta > 0].astype(np.float64)
     # the sampler's ceiling is its issue rate: per shot Philox4x32-10, the tile
     # search, the chunk search and the search of the chunk's running sums
-    # execute ~318 thread-instructions (ncu instruction count of this path)
+    # execute ~307 thread-instructions (ncu instruction count of this path)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_peak = 4 * 32 * sms * 2.07e9 / 318
+    alu_peak = 4 * 32 * sms * 2.07e9 / 307
     samp_rate = shots_n * args.steps / t_samp
     if rank == 0:
         print(json.dumps({
@@ -929,7 +935,7 @@ def run_fairness(args, wl):
                          "unit": "shots/s", "frac": samp_rate / alu_peak,
                          "kernel": f"gqaoa_sample, resident-tile path ({100 * t_samp / el:.0f} % "
                                    "of the step)",
-                         "peak_derivation": "4 warp-instr/clk/SM x 32 x SMs x 2.07 GHz / 318 "
+                         "peak_derivation": "4 warp-instr/clk/SM x 32 x SMs x 2.07 GHz / 307 "
                                             "instructions per shot (measured count)"},
             "metrics_kernel_shots_per_s": shots_n * args.steps / t_fair,
             "shots_to_all_solutions": {"mean": float(done.mean()),

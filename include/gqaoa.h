@@ -175,6 +175,30 @@ int gqaoa_sample_workspace_size(int n, int64_t shots, size_t *bytes);
 int gqaoa_sample(const void *state, int n, uint64_t seed, int64_t shots, uint64_t *out_idx,
                  void *ws, size_t ws_bytes, void *stream);
 
+/*
+ * gqaoa_evolve followed by gqaoa_sample, as one call (Eqs. 2-3, then
+ * Section IV's shots), for callers that want the readouts and the shots of
+ * psi_p but not psi_p itself. The evolution's last mixer step adds the same
+ * a_p (e^{-i beta_p} - 1) <+|chi_p> to every amplitude; instead of writing
+ * psi_p = chi_p + a_p back (one more read and write of the whole state), the
+ * readout pass and the sampler add a_p as they read chi_p, with the same
+ * FP32 addition, so `out`, `trace` and the shots are those that gqaoa_evolve
+ * followed by gqaoa_sample on the same workspace sizes returns.
+ * Arguments as for gqaoa_evolve (one instance) and gqaoa_sample, except:
+ * state   device complex64 [2^n]: the evolution's working state (psi_0 on
+ *         entry if GQAOA_STATE_IN); on return it holds psi_p - a_p, not psi_p,
+ *         whenever the fused path is taken (2^n >= 4096 and at most 64 shots per
+ *         4096 amplitudes on average); otherwise psi_p.
+ * ws      device workspace of gqaoa_evolve_sample_workspace_size(n, p, shots)
+ *         bytes (16-byte aligned).
+ * Errors: those of gqaoa_evolve and gqaoa_sample.
+ */
+int gqaoa_evolve_sample_workspace_size(int n, int p, int64_t shots, size_t *bytes);
+int gqaoa_evolve_sample(const uint8_t *cost, int n, int m, const double *gammas,
+                        const double *betas, int p, void *state, double *out, double *trace,
+                        uint64_t seed, int64_t shots, uint64_t *out_idx, void *ws,
+                        size_t ws_bytes, unsigned flags, void *stream);
+
 /* Workspace bytes for gqaoa_grad(n, p, ...): the per-round checkpoints of the
  * state (p * 2^n * 8 bytes) plus reduction scratch. */
 int gqaoa_grad_workspace_size(int n, int p, size_t *bytes);

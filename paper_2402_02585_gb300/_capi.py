@@ -74,6 +74,8 @@ SIGNATURES = {
     "gqaoa_prob": [_P, _P, _I, _P, _P, _SZ, _P],
     "gqaoa_sample_workspace_size": [_I, _I64, _SZP],
     "gqaoa_sample": [_P, _I, _U64, _I64, _P, _P, _SZ, _P],
+    "gqaoa_evolve_sample_workspace_size": [_I, _I, _I64, _SZP],
+    "gqaoa_evolve_sample": [_P, _I, _I, _P, _P, _I, _P, _P, _P, _U64, _I64, _P, _P, _SZ, _U, _P],
     "gqaoa_grad_workspace_size": [_I, _I, _SZP],
     "gqaoa_grad": [_P, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P],
     "gqaoa_grad_batched_workspace_size": [_I, _I, _I, _SZP],
@@ -180,6 +182,16 @@ def gqaoa_sample_workspace_size(n, shots) -> int:
 
 def gqaoa_sample(state, n, seed, shots, out_idx, ws, ws_bytes, stream):
     _call("gqaoa_sample", state, n, seed, shots, out_idx, ws, ws_bytes, stream)
+
+
+def gqaoa_evolve_sample_workspace_size(n, p, shots) -> int:
+    return _size("gqaoa_evolve_sample_workspace_size", n, p, shots)
+
+
+def gqaoa_evolve_sample(cost, n, m, gammas, betas, p, state, out, trace, seed, shots, out_idx, ws,
+                        ws_bytes, flags, stream):
+    _call("gqaoa_evolve_sample", cost, n, m, gammas, betas, p, state, out, trace, seed, shots,
+          out_idx, ws, ws_bytes, flags, stream)
 
 
 def gqaoa_grad_workspace_size(n, p) -> int:

@@ -143,6 +143,34 @@ def sample(state: torch.Tensor, n: int, seed: int, shots: int, ws: torch.Tensor 
     return out
 
 
+def evolve_sample(cost: torch.Tensor, n: int, m: int, gammas, betas, seed: int, shots: int,
+                  state: torch.Tensor | None = None, state_in: bool = False, trace: bool = False,
+                  ws: torch.Tensor | None = None, readout_class: int = 0):
+    """Eq. 3 then Section IV's shots in one call (gqaoa_evolve_sample): returns
+    (out float64 [3], trace or None, shots int64 [shots]); `state` is working
+    memory and does not hold psi_p afterwards."""
+    _require_cuda(cost)
+    device = cost.device
+    g = _angles(gammas, device)
+    b = _angles(betas, device)
+    p = g.numel()
+    if state is None:
+        if state_in:
+            raise ValueError("state_in needs a state")
+        state = torch.empty(1 << n, dtype=torch.complex64, device=device)
+    out = torch.empty(3, dtype=torch.float64, device=device)
+    tr = torch.empty(p, dtype=torch.float64, device=device) if trace else None
+    shot_idx = torch.empty(int(shots), dtype=torch.int64, device=device)
+    need = C.gqaoa_evolve_sample_workspace_size(n, p, int(shots))
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, device)
+    flags = (C.GQAOA_STATE_IN if state_in else 0) | C.GQAOA_READOUT_CLASS(readout_class)
+    C.gqaoa_evolve_sample(_ptr(cost), n, m, _ptr(g), _ptr(b), p, _ptr(state), _ptr(out), _ptr(tr),
+                          int(seed) & 0xFFFFFFFFFFFFFFFF, int(shots), _ptr(shot_idx), _ptr(ws),
+                          ws.numel(), flags, _stream())
+    return out, tr, shot_idx
+
+
 def grad(cost: torch.Tensor, n: int, m: int, gammas, betas, objective: str = "p0",
          ws: torch.Tensor | None = None):
     """(L, dL/dgamma [p], dL/dbeta [p]) on the device, by the adjoint kernels."""

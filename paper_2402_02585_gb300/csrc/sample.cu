@@ -26,28 +26,29 @@
 // (a whole cost class has one magnitude) cannot make rounding errors pile up
 // the way FP32 sums would.
 //
-// Pass 1 computes tile totals; two launches scan them; each shot then finds
-// its tile by binary search, shots are bucketed by tile with a counting sort
-// (its counts scanned the same way), and pass 2 re-reads only the tiles that
-// received shots, rebuilds the same chunk sums and scan, and resolves each
-// shot by a binary search over chunks and a walk over its chunk's 16
-// weights. With at most eight tiles (n <= 15) every CTA keeps all tile scans
-// in shared memory and resolves its shots directly instead (no bucketing).
+// Pass 1 computes tile totals; two launches scan them. With few shots per
+// tile (up to 64 on average) pass 1 also stores every tile's chunk prefixes
+// and each shot is resolved on its own: binary searches over the tile and
+// chunk prefixes, then a walk over its chunk's 16 weights. With more shots,
+// each shot finds its tile by binary search, shots are bucketed by tile with
+// a counting sort (its counts scanned the same way), and pass 2 re-reads
+// only the tiles that received shots, rebuilds the same chunk sums and scan,
+// and resolves the shots with the same searches and walk. With at most eight
+// tiles (n <= 15) every CTA keeps all tile scans in shared memory and
+// resolves its shots directly instead (no bucketing).
 // Both passes compute the tile totals with the same instructions in the same
 // order, so the levels agree exactly; a target that rounding puts past the
 // end of a chunk or tile goes to its last amplitude of nonzero weight.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <mutex>
+
+#include "cdf.cuh"
 #include "common.cuh"
 
 namespace gq {
-
-constexpr int kSampTile = 4096;
-constexpr int kChunk = 16;
-constexpr int kChunksPerTile = kSampTile / kChunk;  // 256 = one per thread
-constexpr int kRowVec = kChunk / 2 + 1;  // float4 (2 amplitudes) per shared chunk row, 1 pad
-constexpr int kPad = kChunk + 1;         // floats per row of the resident running sums
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10: ten rounds of two 32x32 multiplies, key bumped by the Weyl
@@ -69,132 +70,29 @@ __device__ __forceinline__ double shot_uniform(uint64_t seed, uint64_t s) {
   return (double)(x >> 11) * (1.0 / 9007199254740992.0);
 }
 
-// a > b for non-negative doubles (CDF values and targets), decided on the
-// integer pipe: IEEE 754 orders non-negative values as their bit patterns
-// read as integers, so this equals the FP64 comparison without using GB300's
-// narrow FP64 pipe, which the shot searches would otherwise saturate.
-__device__ __forceinline__ bool gt_nonneg(double a, double b) {
-  return __double_as_longlong(a) > __double_as_longlong(b);
-}
-
-// (h, l) += (yh, yl) in double-float arithmetic (non-negative terms here).
-__device__ __forceinline__ void df_add(float &h, float &l, float yh, float yl) {
-  float s, e;
-  two_sum(h, yh, s, e);
-  h = s;
-  l = __fadd_rn(__fadd_rn(l, yl), e);
-}
-
-// Renormalise (h, l) so that h is the FP32 rounding of h + l (Fast2Sum,
-// |h| >= |l|).
-__device__ __forceinline__ void df_norm(float &h, float &l) {
-  const float s = __fadd_rn(h, l);
-  l = __fsub_rn(l, __fsub_rn(s, h));
-  h = s;
-}
-
-// |re + i im|^2 as a normalised double-float (h, l): re^2 = p1 + e1 and
-// im^2 = p2 + e2 exactly (e = fma(x, x, -p)), p1 + p2 = s + e exactly
-// (TwoSum), and the three small words are added in FP32, which leaves a
-// relative error below 2^-46.
-__device__ __forceinline__ void weight_df(float re, float im, float &h, float &l) {
-  const float p1 = __fmul_rn(re, re), e1 = fmaf(re, re, -p1);
-  const float p2 = __fmul_rn(im, im), e2 = fmaf(im, im, -p2);
-  float s, e;
-  two_sum(p1, p2, s, e);
-  h = s;
-  l = __fadd_rn(e, __fadd_rn(e1, e2));
-  df_norm(h, l);
-}
-
-// The first of a chunk's 16 amplitudes (row: 8 float4 in shared or global
-// memory) whose running weight sum exceeds rl: the sums are formed in
-// double-float in index order (the order of the chunk sum) and compared as
-// FP64. A target that rounding puts past the chunk's sum goes to its last
-// amplitude of nonzero weight.
-__device__ __forceinline__ int chunk_pick(const float4 *row, double rl) {
-  float h = 0.f, l = 0.f;
-  int pick = -1, last_nz = 0;
-#pragma unroll
-  for (int i = 0; i < kChunk / 2; ++i) {
-    const float4 v = row[i];
-    float wh, wl;
-    weight_df(v.x, v.y, wh, wl);
-    df_add(h, l, wh, wl);
-    if (wh > 0.f) last_nz = 2 * i;
-    if (pick < 0 && gt_nonneg((double)h + (double)l, rl)) pick = 2 * i;
-    weight_df(v.z, v.w, wh, wl);
-    df_add(h, l, wh, wl);
-    if (wh > 0.f) last_nz = 2 * i + 1;
-    if (pick < 0 && gt_nonneg((double)h + (double)l, rl)) pick = 2 * i + 1;
-  }
-  return pick >= 0 ? pick : last_nz;
-}
-
-// Per tile: the tile's amplitudes into shared memory, one row of 16 per
-// chunk (row stride kRowVec float4; chunk i = row i, amplitudes 16 i ..
-// 16 i + 15 of the tile), every thread's chunk sum in double-float, and the
-// inclusive in-tile scan of the chunk sums in double-float, rounded to FP64
-// into s_incl. (ch, cl) receives this thread's chunk sum, normalised.
-// Called by all 256 threads.
+// One tile from global memory (see tile_chunk_scan_regs).
 __device__ __forceinline__ void tile_chunk_scan(const float4 *__restrict__ st, uint64_t tile,
-                                                float4 *s_amp, double *s_incl, float2 *s_wtot,
-                                                float &ch, float &cl) {
+                                                double *s_incl, float2 *s_wtot, float &ch,
+                                                float &cl, float *cum) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // coalesced loads: a warp covers 512 amplitudes; load j of lane l is
-  // amplitudes 64 j + 2 l and 64 j + 2 l + 1 of the warp's 512, i.e. slot
-  // l mod 8 of row 4 j + l / 8
   const uint64_t vbase = tile * (kSampTile / 2) + (uint64_t)warp * 256 + lane;
-  float4 *sa = s_amp + warp * 32 * kRowVec;
+  float4 v[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) sa[(4 * j + (lane >> 3)) * kRowVec + (lane & 7)] = st[vbase + 32 * j];
-  __syncwarp();
-  const float4 *row = sa + lane * kRowVec;
-  float h = 0.f, l = 0.f;
-#pragma unroll
-  for (int i = 0; i < kChunk / 2; ++i) {
-    const float4 v = row[i];
-    float wh, wl;
-    weight_df(v.x, v.y, wh, wl);
-    df_add(h, l, wh, wl);
-    weight_df(v.z, v.w, wh, wl);
-    df_add(h, l, wh, wl);
-  }
-  df_norm(h, l);
-  ch = h;
-  cl = l;
-  // inclusive scan over the warp's 32 chunks
-  float xh = h, xl = l;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const float yh = __shfl_up_sync(0xffffffffu, xh, o);
-    const float yl = __shfl_up_sync(0xffffffffu, xl, o);
-    if (lane >= o) df_add(xh, xl, yh, yl);
-  }
-  if (lane == 31) s_wtot[warp] = make_float2(xh, xl);
-  __syncthreads();
-  float bh = 0.f, bl = 0.f;  // the warps before this one, in order
-  for (int w = 0; w < warp; ++w) df_add(bh, bl, s_wtot[w].x, s_wtot[w].y);
-  df_add(bh, bl, xh, xl);
-  s_incl[threadIdx.x] = (double)bh + (double)bl;
-  __syncthreads();
+  for (int j = 0; j < 8; ++j) v[j] = st[vbase + 32 * j];
+  tile_chunk_scan_regs(v, s_incl, s_wtot, ch, cl, cum);
 }
 
-__device__ __forceinline__ double tile_total(const float2 *s_wtot) {
-  float th = 0.f, tl = 0.f;
-  for (int w = 0; w < kWarps; ++w) df_add(th, tl, s_wtot[w].x, s_wtot[w].y);
-  return (double)th + (double)tl;
-}
-
-// Pass 1: tile totals.
+// Pass 1: tile totals and, when chunk_incl is not null, every tile's
+// in-tile chunk prefixes (chunk_incl[t * 256 + i] = s_incl[i] of tile t).
 __global__ void __launch_bounds__(kThreads)
-tile_sum_kernel(const float4 *__restrict__ st, uint64_t ntiles, double *__restrict__ tsum) {
-  __shared__ float4 s_amp[kWarps * 32 * kRowVec];
+tile_sum_kernel(const float4 *__restrict__ st, uint64_t ntiles, double *__restrict__ tsum,
+                double *__restrict__ chunk_incl) {
   __shared__ double s_incl[kChunksPerTile];
   __shared__ float2 s_wtot[kWarps];
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     float ch, cl;
-    tile_chunk_scan(st, t, s_amp, s_incl, s_wtot, ch, cl);
+    tile_chunk_scan(st, t, s_incl, s_wtot, ch, cl, nullptr);
+    if (chunk_incl) chunk_incl[t * kChunksPerTile + threadIdx.x] = s_incl[threadIdx.x];
     if (threadIdx.x == 0) tsum[t] = tile_total(s_wtot);
     __syncthreads();
   }
@@ -202,14 +100,16 @@ tile_sum_kernel(const float4 *__restrict__ st, uint64_t ntiles, double *__restri
 
 // ---------------------------------------------------------------------------
 // Exclusive scans over per-tile values (tile totals, shot counts) by many
-// CTAs in two launches: CTA g scans its 1024 values and their total; then
-// CTA g adds the total of the CTAs before it, summed in a fixed order, so the
-// result does not depend on scheduling. Tile totals are added in FP64 pairs
+// CTAs in two launches: CTA g scans its 256 values and their total; then
+// CTA g adds the total of the CTAs before it, summed once per CTA in a fixed
+// order, so the result does not depend on scheduling. (FP64 runs at a few
+// operations per clock per SM on GB300, so every FP64-pair addition is
+// spread over many CTAs and none is repeated per thread.) Tile totals are added in FP64 pairs
 // (the rounding error of each addition kept in the second word, TwoSum), so
 // a prefix over 2^22 tiles stays within a rounding unit of the exact sum;
 // counts are exact integers.
 // ---------------------------------------------------------------------------
-constexpr int kScanThreads = 1024;
+constexpr int kScanThreads = 256;
 
 struct DD {
   double hi, lo;
@@ -271,21 +171,22 @@ scan_local_kernel(const typename A::In *__restrict__ in, uint64_t count,
   }
   if (lane == 31) s_warp[warp] = inc;
   __syncthreads();
+  constexpr int kW = kScanThreads / 32;
   if (warp == 0) {
-    Acc w = s_warp[lane];  // kScanThreads / 32 == 32 warps
+    Acc w = lane < kW ? s_warp[lane] : A::zero();
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
+    for (int o = 1; o < kW; o <<= 1) {
       const Acc y = A::shfl_up(w, o);
       if (lane >= o) w = A::add(y, w);
     }
-    s_warp[lane] = w;  // inclusive over warps
+    if (lane < kW) s_warp[lane] = w;  // inclusive over warps
   }
   __syncthreads();
   Acc ex = A::shfl_up(inc, 1);
   if (lane == 0) ex = A::zero();
   if (warp > 0) ex = A::add(s_warp[warp - 1], ex);
   if (i < count) loc[i] = ex;
-  if (threadIdx.x == 0) gtot[blockIdx.x] = s_warp[31];
+  if (threadIdx.x == 0) gtot[blockIdx.x] = s_warp[kW - 1];
 }
 
 template <class A>
@@ -293,17 +194,18 @@ __global__ void __launch_bounds__(kScanThreads)
 scan_finish_kernel(const typename A::Acc *__restrict__ loc, uint64_t count,
                    const typename A::Acc *__restrict__ gtot, typename A::Out *__restrict__ out) {
   using Acc = typename A::Acc;
-  __shared__ Acc s_warp[kScanThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // total of the CTAs before this one: strided partial sums, then a fixed tree
-  Acc acc = A::zero();
-  for (uint32_t g = threadIdx.x; g < blockIdx.x; g += kScanThreads) acc = A::add(acc, gtot[g]);
+  __shared__ Acc s_base;
+  // total of the CTAs before this one, by warp 0: strided partial sums per
+  // lane, then a fixed butterfly
+  if (threadIdx.x < 32) {
+    Acc acc = A::zero();
+    for (uint32_t g = threadIdx.x; g < blockIdx.x; g += 32) acc = A::add(acc, gtot[g]);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc = A::add(acc, A::shfl_xor(acc, o));
-  if (lane == 0) s_warp[warp] = acc;
+    for (int o = 16; o > 0; o >>= 1) acc = A::add(acc, A::shfl_xor(acc, o));
+    if (threadIdx.x == 0) s_base = acc;
+  }
   __syncthreads();
-  Acc base = A::zero();
-  for (int w = 0; w < kScanThreads / 32; ++w) base = A::add(base, s_warp[w]);
+  const Acc base = s_base;
   const uint64_t i = (uint64_t)blockIdx.x * kScanThreads + threadIdx.x;
   if (i < count) out[i] = A::out(A::add(base, loc[i]));
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
@@ -370,7 +272,6 @@ __global__ void __launch_bounds__(kThreads)
 resolve_kernel(const float4 *__restrict__ st, uint64_t ntiles, const double *__restrict__ prefix,
                const uint32_t *__restrict__ offset, const uint32_t *__restrict__ bucket,
                uint64_t seed, uint64_t *__restrict__ out) {
-  __shared__ float4 s_amp[kWarps * 32 * kRowVec];
   __shared__ double s_incl[kChunksPerTile];
   __shared__ float2 s_wtot[kWarps];
   __shared__ float s_chunk[kChunksPerTile];
@@ -379,7 +280,7 @@ resolve_kernel(const float4 *__restrict__ st, uint64_t ntiles, const double *__r
     const uint32_t b0 = offset[t], b1 = offset[t + 1];
     if (b0 == b1) continue;  // uniform across the CTA
     float ch, cl;
-    tile_chunk_scan(st, t, s_amp, s_incl, s_wtot, ch, cl);
+    tile_chunk_scan(st, t, s_incl, s_wtot, ch, cl, nullptr);
     s_chunk[threadIdx.x] = ch;
     __syncthreads();
     const double tbase = prefix[t];
@@ -388,10 +289,49 @@ resolve_kernel(const float4 *__restrict__ st, uint64_t ntiles, const double *__r
       const double r = shot_uniform(seed, s) * total - tbase;
       const int c = find_chunk(s_incl, s_chunk, r);
       const double rl = r - (c > 0 ? s_incl[c - 1] : 0.0);
-      const int pick = chunk_pick(s_amp + c * kRowVec, rl);
-      out[s] = t * kSampTile + (uint64_t)c * kChunk + pick;
+      const uint64_t base = t * kSampTile + (uint64_t)c * kChunk;  // the tile is in L2 now
+      out[s] = base + chunk_pick(st + base / 2, rl, make_float2(0.f, 0.f));
     }
     __syncthreads();
+  }
+}
+
+// Few shots per tile (at most kDirectShotsPerTile on average, e.g. 10^6 shots
+// over the 65536 tiles of n = 28): pass 1 has stored every tile's chunk
+// prefixes, so a shot needs neither the counting sort nor a re-read of its
+// whole tile. Each thread takes a grid-stride range of shots and resolves
+// each from the tile prefixes, its tile's 256 chunk prefixes and its chunk's
+// 16 amplitudes (128 bytes), with the searches and the chunk walk of pass 2:
+// the same shots, about a twentieth of the memory traffic.
+constexpr uint64_t kDirectShotsPerTile = 64;
+
+// `add`: when not null, the pending mixer term a_p of a state st = psi_p - a_p
+// (gqaoa_evolve_sample), added to every amplitude as the chunk is walked.
+__global__ void __launch_bounds__(kThreads)
+resolve_direct_kernel(const float4 *__restrict__ st, uint64_t ntiles,
+                      const double *__restrict__ prefix, const double *__restrict__ chunk_incl,
+                      const float2 *__restrict__ add, uint64_t seed, int64_t shots,
+                      uint64_t *__restrict__ out) {
+  const double total = prefix[ntiles];
+  const float2 ad = add ? *add : make_float2(0.f, 0.f);
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < shots;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const double tt = shot_uniform(seed, (uint64_t)s) * total;
+    const uint32_t t = find_tile(prefix, ntiles, tt);
+    const double r = tt - prefix[t];
+    const double *incl = chunk_incl + (uint64_t)t * kChunksPerTile;
+    int lo = 0, hi = kChunksPerTile;  // chunk: smallest i with incl[i] > r
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (gt_nonneg(incl[mid], r)) hi = mid; else lo = mid + 1;
+    }
+    if (lo >= kChunksPerTile) {  // rounding past the tile end: last chunk of nonzero weight
+      lo = kChunksPerTile - 1;
+      while (lo > 0 && !(incl[lo] > incl[lo - 1])) --lo;
+    }
+    const double rl = r - (lo > 0 ? incl[lo - 1] : 0.0);
+    const uint64_t base = (uint64_t)t * kSampTile + (uint64_t)lo * kChunk;
+    out[s] = base + chunk_pick(st + base / 2, rl, ad);
   }
 }
 
@@ -404,13 +344,21 @@ resolve_kernel(const float4 *__restrict__ st, uint64_t ntiles, const double *__r
 // the exact running sums; only a target within 2^-17 of the chunk's sum of
 // one of them (about one shot in 10^4) is decided by chunk_pick on the
 // chunk's amplitudes reloaded from global memory (L2-resident at these
-// sizes), so every shot is the one pass 2 would give.
+// sizes), so every shot is the one pass 2 would give. A tile scan takes 20 KB
+// of shared memory, so up to four tiles (n <= 14) leave room for two CTAs per
+// SM.
 constexpr int kResidentTiles = 8;
 struct TileScan {
   float cum[kChunksPerTile * kPad];  // per chunk (row of kPad): FP32 running sums
   double incl[kChunksPerTile];
   float chunk[kChunksPerTile];       // leading word of each chunk's sum
 };
+
+// chunk_pick on global memory, kept out of line: the resident path takes it
+// for about one shot in 10^4, and inlined it would crowd the common path.
+__device__ __noinline__ int chunk_pick_global(const float4 *row, double rl) {
+  return chunk_pick(row, rl, make_float2(0.f, 0.f));
+}
 
 __device__ __forceinline__ uint64_t resolve_shot(const float4 *__restrict__ st, const TileScan *ts,
                                                  const double *s_prefix, uint64_t ntiles,
@@ -431,7 +379,7 @@ __device__ __forceinline__ uint64_t resolve_shot(const float4 *__restrict__ st, 
   const float tol = T.chunk[c] * 0x1p-17f;
   const bool clear = a < kChunk && row[a] > rlf + tol && (a == 0 || row[a - 1] < rlf - tol);
   const uint64_t base = (uint64_t)t * kSampTile + (uint64_t)c * kChunk;
-  const int pick = clear ? a : chunk_pick(st + base / 2, rl);
+  const int pick = clear ? a : chunk_pick_global(st + base / 2, rl);
   return base + pick;
 }
 
@@ -440,32 +388,16 @@ resolve_resident_kernel(const float4 *__restrict__ st, uint64_t ntiles,
                         const double *__restrict__ prefix, uint64_t seed, int64_t shots,
                         uint64_t *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
-  TileScan *ts = reinterpret_cast<TileScan *>(s_dyn);                      // [ntiles]
-  float4 *s_amp = reinterpret_cast<float4 *>(s_dyn + sizeof(TileScan) * ntiles);  // one tile
+  TileScan *ts = reinterpret_cast<TileScan *>(s_dyn);  // [ntiles]
   __shared__ float2 s_wtot[kWarps];
   __shared__ double s_prefix[kResidentTiles + 1];
   if (threadIdx.x <= ntiles) s_prefix[threadIdx.x] = prefix[threadIdx.x];
   for (uint64_t t = 0; t < ntiles; ++t) {
     float ch, cl;
-    tile_chunk_scan(st, t, s_amp, ts[t].incl, s_wtot, ch, cl);
+    tile_chunk_scan(st, t, ts[t].incl, s_wtot, ch, cl, ts[t].cum);
     ts[t].chunk[threadIdx.x] = ch;
-    // this thread's chunk: FP32 running sums of its weights' leading words
-    const float4 *arow = s_amp + threadIdx.x * kRowVec;
-    float *crow = ts[t].cum + threadIdx.x * kPad;
-    float run = 0.f;
-#pragma unroll
-    for (int i = 0; i < kChunk / 2; ++i) {
-      const float4 v = arow[i];
-      float wh, wl;
-      weight_df(v.x, v.y, wh, wl);
-      run += wh;
-      crow[2 * i] = run;
-      weight_df(v.z, v.w, wh, wl);
-      run += wh;
-      crow[2 * i + 1] = run;
-    }
-    __syncthreads();  // s_amp is rewritten for the next tile
   }
+  __syncthreads();
   const double total = s_prefix[ntiles];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // two shots per thread in flight: independent chains of shared-memory loads
@@ -517,6 +449,7 @@ sample_small_kernel(const float2 *__restrict__ st, int n, uint64_t seed, int64_t
 }
 
 struct SampleWs {
+  double *chunk_incl;  // [ntiles][256] (direct mode only)
   double *tsum;        // [ntiles]
   double *prefix;      // [ntiles + 1]
   DD *scan_loc;        // [ntiles]   in-CTA prefixes of the tile-total scan
@@ -530,7 +463,15 @@ struct SampleWs {
   uint32_t *bucket;    // [shots]
 };
 
+// Direct mode (few shots per tile, more tiles than the resident path takes):
+// the chunk prefixes instead of the counting sort's buffers.
+static bool sample_direct(uint64_t ntiles, int64_t shots) {
+  return ntiles > (uint64_t)kResidentTiles && (uint64_t)shots <= kDirectShotsPerTile * ntiles;
+}
+
 static size_t sample_ws_layout(uint64_t ntiles, int64_t shots, char *base, SampleWs *w) {
+  const bool direct = sample_direct(ntiles, shots);
+  if (direct) shots = 0;  // no per-shot buffers
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -548,7 +489,9 @@ static size_t sample_ws_layout(uint64_t ntiles, int64_t shots, char *base, Sampl
   size_t o8 = take(sizeof(uint32_t) * groups);
   size_t o9 = take(sizeof(uint32_t) * (size_t)shots);
   size_t o10 = take(sizeof(uint32_t) * (size_t)shots);
+  size_t o11 = direct ? take(sizeof(double) * ntiles * kChunksPerTile) : 0;
   if (w) {
+    w->chunk_incl = direct ? reinterpret_cast<double *>(base + o11) : nullptr;
     w->tsum = reinterpret_cast<double *>(base + o1);
     w->prefix = reinterpret_cast<double *>(base + o2);
     w->scan_loc = reinterpret_cast<DD *>(base + o3);
@@ -565,6 +508,59 @@ static size_t sample_ws_layout(uint64_t ntiles, int64_t shots, char *base, Sampl
 }
 
 int sm_count();
+
+// Resident CTAs per SM of the tile passes (shared memory bounds them),
+// queried once per device; 4 if no device answers.
+static int tile_pass_per_sm() {
+  constexpr int kMaxDev = 64;
+  static std::once_flag once[kMaxDev];
+  static int per_sm[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 4;
+  std::call_once(once[dev], [dev]() {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, tile_sum_kernel, kThreads, 0) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, resolve_kernel, kThreads, 0) !=
+            cudaSuccess)
+      a = b = 4;
+    per_sm[dev] = std::max(1, std::min(a, b));
+  });
+  return per_sm[dev];
+}
+
+// gqaoa_evolve_sample's use of the direct mode: whether it applies, the
+// buffers a fused pass fills (tile totals and chunk prefixes in the layout of
+// gqaoa_sample's workspace), and the passes after them.
+bool sample_direct_ok(uint64_t ntiles, int64_t shots) { return sample_direct(ntiles, shots); }
+
+size_t sample_direct_ws(uint64_t ntiles, int64_t shots, char *base, double **tsum,
+                        double **chunk_incl) {
+  SampleWs w;
+  const size_t bytes = sample_ws_layout(ntiles, shots, base, &w);
+  *tsum = w.tsum;
+  *chunk_incl = w.chunk_incl;
+  return bytes;
+}
+
+int sample_direct_tail(const float4 *state, const float2 *add, uint64_t ntiles, uint64_t seed,
+                       int64_t shots, uint64_t *out_idx, void *ws, cudaStream_t st) {
+  SampleWs w;
+  sample_ws_layout(ntiles, shots, static_cast<char *>(ws), &w);
+  const unsigned groups = (unsigned)((ntiles + kScanThreads - 1) / kScanThreads);
+  scan_local_kernel<SumDD><<<groups, kScanThreads, 0, st>>>(w.tsum, ntiles, w.scan_loc,
+                                                            w.scan_tot);
+  GQ_CHECK_LAUNCH();
+  scan_finish_kernel<SumDD><<<groups, kScanThreads, 0, st>>>(w.scan_loc, ntiles, w.scan_tot,
+                                                             w.prefix);
+  GQ_CHECK_LAUNCH();
+  const int64_t need = (shots + kThreads - 1) / kThreads;
+  const int64_t cap = (int64_t)(sm_count() > 0 ? sm_count() : 152) * 8;
+  resolve_direct_kernel<<<(unsigned)(need < cap ? need : cap), kThreads, 0, st>>>(
+      state, ntiles, w.prefix, w.chunk_incl, add, seed, shots, out_idx);
+  GQ_CHECK_LAUNCH();
+  return GQAOA_OK;
+}
 
 }  // namespace gq
 
@@ -606,10 +602,12 @@ extern "C" int gqaoa_sample(const void *state, int n, uint64_t seed, int64_t sho
   SampleWs w;
   sample_ws_layout(ntiles, shots, static_cast<char *>(ws), &w);
   const float4 *s4 = static_cast<const float4 *>(state);
+  // the tile passes run one wave of resident CTAs, each striding over tiles
+  const uint64_t twave = (uint64_t)sms0 * (uint64_t)tile_pass_per_sm();
+  const unsigned tgrid = (unsigned)(ntiles < twave ? ntiles : twave);
   const int sms = sms0;
-  const unsigned tgrid = (unsigned)(ntiles < (uint64_t)sms * 8 ? ntiles : (uint64_t)sms * 8);
   const unsigned groups = (unsigned)((ntiles + kScanThreads - 1) / kScanThreads);
-  tile_sum_kernel<<<tgrid, kThreads, 0, st>>>(s4, ntiles, w.tsum);
+  tile_sum_kernel<<<tgrid, kThreads, 0, st>>>(s4, ntiles, w.tsum, w.chunk_incl);
   GQ_CHECK_LAUNCH();
   scan_local_kernel<SumDD><<<groups, kScanThreads, 0, st>>>(w.tsum, ntiles, w.scan_loc,
                                                             w.scan_tot);
@@ -618,7 +616,7 @@ extern "C" int gqaoa_sample(const void *state, int n, uint64_t seed, int64_t sho
                                                              w.prefix);
   GQ_CHECK_LAUNCH();
   if (ntiles <= (uint64_t)kResidentTiles) {
-    const size_t dyn = sizeof(TileScan) * ntiles + sizeof(float4) * kWarps * 32 * kRowVec;
+    const size_t dyn = sizeof(TileScan) * ntiles;
     if (cudaFuncSetAttribute(resolve_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)dyn) != cudaSuccess)
       return GQAOA_ECUDA;
@@ -628,6 +626,12 @@ extern "C" int gqaoa_sample(const void *state, int n, uint64_t seed, int64_t sho
       return GQAOA_ECUDA;
     resolve_resident_kernel<<<shot_ctas(per_sm), kThreads, dyn, st>>>(s4, ntiles, w.prefix, seed,
                                                                        shots, out_idx);
+    GQ_CHECK_LAUNCH();
+    return GQAOA_OK;
+  }
+  if (w.chunk_incl) {
+    resolve_direct_kernel<<<shot_ctas(8), kThreads, 0, st>>>(s4, ntiles, w.prefix, w.chunk_incl,
+                                                             nullptr, seed, shots, out_idx);
     GQ_CHECK_LAUNCH();
     return GQAOA_OK;
   }

@@ -44,6 +44,7 @@
 
 #include <mutex>
 
+#include "cdf.cuh"
 #include "common.cuh"
 
 namespace gq {
@@ -551,6 +552,79 @@ __global__ void __launch_bounds__(kThreads, kFwdPerSm) readout_kernel(const Pass
   };
   pipelined_tiles(local, a.cpi, a.ntiles, load, proc);
   reduce_to_record<3>(a, b, local, acc, s_w, s_vals);
+}
+
+// K4 fused with the sampler's first pass (gqaoa_evolve_sample): psi_p =
+// chi_p + a_p is formed in registers exactly as readout_kernel<true> forms it
+// and is not written back; the pass makes the readouts of readout_kernel and,
+// per tile, the sampler's tile total and chunk prefixes of psi_p (cdf.cuh).
+// One instance (B = 1). add_out receives a_p as the float pair the pass
+// added, so the sampler can add it again when it walks a chunk.
+__global__ void __launch_bounds__(kThreads, kFwdPerSm)
+readout_sample_kernel(const PassArgs a, double *__restrict__ tsum, double *__restrict__ chunk_incl,
+                      float2 *__restrict__ add_out) {
+  __shared__ float2 s_a;
+  __shared__ double s_w[kWarps][kPartStride];
+  __shared__ double s_vals[kPartStride];
+  __shared__ double s_incl[kChunksPerTile];
+  __shared__ float2 s_wtot[kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int local = blockIdx.x;
+  pdl_wait_then_release();
+  if (warp == 0) {
+    const size_t bk = (size_t)a.round;  // the last round
+    const double Sre = w0_parts(a, 0, 0), Sim = w0_parts(a, 0, 1);
+    const double2 al = a.alpha[bk];
+    const double2 av = make_double2((al.x * Sre - al.y * Sim) * a.inv_n,
+                                    (al.x * Sim + al.y * Sre) * a.inv_n);
+    if (local == 0 && lane == 0) {
+      double *rec = a.record + 4 * bk;
+      rec[0] = Sre; rec[1] = Sim; rec[2] = av.x; rec[3] = av.y;
+      *add_out = make_float2((float)av.x, (float)av.y);
+    }
+    if (lane == 0) s_a = make_float2((float)av.x, (float)av.y);
+  }
+  __syncthreads();
+  const float2 ad = s_a;
+  DF acc[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) acc[j].zero();
+  const uint16_t *__restrict__ cost2 = reinterpret_cast<const uint16_t *>(a.cost);
+  const float4 *__restrict__ src = a.src;
+  const bool reverse = ((a.round + 1) & 1) != 0;
+  auto tile_of = [&](uint64_t t) { return reverse ? (a.ntiles - 1 - t) : t; };
+  auto load = [&](TileRegs &T, uint64_t t) {
+    const uint64_t vb = tile_vbase(tile_of(t), warp, lane);
+#pragma unroll
+    for (int j = 0; j < kVecPerThread; ++j) {
+      T.c2[j] = cost2[vb + 32 * j];
+      T.v[j] = src[vb + 32 * j];
+    }
+  };
+  auto proc = [&](TileRegs &T, uint64_t t) {
+    float tp = 0.f, te = 0.f, tn = 0.f;
+#pragma unroll
+    for (int j = 0; j < kVecPerThread; ++j) {
+      T.v[j] = make_float4(T.v[j].x + ad.x, T.v[j].y + ad.y, T.v[j].z + ad.x, T.v[j].w + ad.y);
+      const float w0 = T.v[j].x * T.v[j].x + T.v[j].y * T.v[j].y;
+      const float w1 = T.v[j].z * T.v[j].z + T.v[j].w * T.v[j].w;
+      const unsigned c_0 = T.c2[j] & 0xFFu, c_1 = T.c2[j] >> 8;
+      tn += w0 + w1;
+      te += (float)c_0 * w0 + (float)c_1 * w1;
+      tp += (c_0 == a.target ? w0 : 0.f) + (c_1 == a.target ? w1 : 0.f);
+    }
+    acc[0].add(tp);
+    acc[1].add(te);
+    acc[2].add(tn);
+    const uint64_t tile = tile_of(t);
+    float ch, cl;
+    tile_chunk_scan_regs(T.v, s_incl, s_wtot, ch, cl, nullptr);
+    chunk_incl[tile * kChunksPerTile + threadIdx.x] = s_incl[threadIdx.x];
+    if (threadIdx.x == 0) tsum[tile] = tile_total(s_wtot);
+    __syncthreads();  // s_wtot and s_incl are rewritten for the next tile
+  };
+  pipelined_tiles(local, a.cpi, a.ntiles, load, proc);
+  reduce_to_record<3>(a, 0, local, acc, s_w, s_vals);
 }
 
 // One warp per instance: out[b][0..2] from the readout records, and the
@@ -1291,6 +1365,94 @@ extern "C" int gqaoa_batched_geometry(int n, int batch, int adjoint, int *ctas_p
   *ctas_per_instance = g.cpi;
   *records_per_instance = g.nparts;
   return GQAOA_OK;
+}
+
+namespace gq {
+// The sampler's part of gqaoa_evolve_sample (sample.cu): direct mode, its
+// workspace layout and the passes after the tile totals.
+bool sample_direct_ok(uint64_t ntiles, int64_t shots);
+size_t sample_direct_ws(uint64_t ntiles, int64_t shots, char *base, double **tsum,
+                        double **chunk_incl);
+int sample_direct_tail(const float4 *state, const float2 *add, uint64_t ntiles, uint64_t seed,
+                       int64_t shots, uint64_t *out_idx, void *ws, cudaStream_t st);
+}  // namespace gq
+
+// Layout of gqaoa_evolve_sample's workspace: the evolution's, then a_p (256
+// bytes), then the sampler's.
+static size_t evolve_sample_layout(int n, int p, int64_t shots, size_t *o_add, size_t *o_samp) {
+  size_t ev = 0, sa = 0;
+  gqaoa_evolve_workspace_size(n, p, &ev);
+  gqaoa_sample_workspace_size(n, shots, &sa);
+  const size_t a0 = round_up(ev, 256), s0 = a0 + 256;
+  if (o_add) *o_add = a0;
+  if (o_samp) *o_samp = s0;
+  return s0 + sa;
+}
+
+extern "C" int gqaoa_evolve_sample_workspace_size(int n, int p, int64_t shots, size_t *bytes) {
+  if (!bytes) return GQAOA_EINVAL;
+  int rc = check_common(n, 0, 1, p);
+  if (rc) return rc;
+  if (shots < 0 || shots >= (1ll << 32)) return GQAOA_ERANGE;
+  *bytes = evolve_sample_layout(n, p, shots, nullptr, nullptr);
+  return GQAOA_OK;
+}
+
+extern "C" int gqaoa_evolve_sample(const uint8_t *cost, int n, int m, const double *gammas,
+                                   const double *betas, int p, void *state, double *out,
+                                   double *trace, uint64_t seed, int64_t shots, uint64_t *out_idx,
+                                   void *ws, size_t ws_bytes, unsigned flags, void *stream) {
+  gq::NvtxRange nvtx_range("gqaoa_evolve_sample");
+  int rc = check_common(n, m, 1, p);
+  if (rc) return rc;
+  if (shots < 0 || shots >= (1ll << 32)) return GQAOA_ERANGE;
+  if (!cost || !gammas || !betas || !state || !ws || (shots > 0 && !out_idx)) return GQAOA_EINVAL;
+  if (flags & ~(GQAOA_STATE_IN | GQAOA_READOUT_CLASS(255))) return GQAOA_EINVAL;
+  const unsigned target = (flags >> 8) & 0xFFu;
+  if (target != 0u && trace) return GQAOA_EINVAL;
+  if (!aligned16(state) || !aligned16(cost) || !aligned8(gammas) || !aligned8(betas) ||
+      (out && !aligned8(out)) || (trace && !aligned8(trace)) || !aligned16(ws) ||
+      (out_idx && !aligned8(out_idx)))
+    return GQAOA_EINVAL;
+  size_t o_add = 0, o_samp = 0;
+  if (ws_bytes < evolve_sample_layout(n, p, shots, &o_add, &o_samp)) return GQAOA_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char *base = static_cast<char *>(ws);
+  size_t ev_bytes = 0, sa_bytes = 0;
+  gqaoa_evolve_workspace_size(n, p, &ev_bytes);
+  gqaoa_sample_workspace_size(n, shots, &sa_bytes);
+  const Geometry g = make_geometry(n, 1, kFwdPerSm);
+  if (g.small || shots == 0 || !sample_direct_ok(g.ntiles, shots)) {
+    // one CTA per state, no shots, or many shots per tile: the evolution
+    // materialises psi_p and the sampler runs on it
+    rc = evolve_impl(cost, 0, n, m, 1, gammas, betas, p, state, out, trace, ws, ev_bytes, flags,
+                     st);
+    if (rc) return rc;
+    return gqaoa_sample(state, n, seed, shots, out_idx, base + o_samp, sa_bytes, stream);
+  }
+  Ws w;
+  ws_layout(g, p, false, base, &w, g.nparts);
+  rc = launch_phase_tables(gammas, betas, p, w, st);
+  if (rc) return rc;
+  rc = run_forward(g, w, cost, 0, p, static_cast<float2 *>(state), (flags & GQAOA_STATE_IN) != 0,
+                   trace, nullptr, st);
+  if (rc) return rc;
+  double *tsum = nullptr, *chunk_incl = nullptr;
+  sample_direct_ws(g.ntiles, shots, base + o_samp, &tsum, &chunk_incl);
+  float2 *add = reinterpret_cast<float2 *>(base + o_add);
+  PassArgs pa;
+  init_pass(pa, g, w, cost, 0, p);
+  pa.round = p - 1;
+  pa.parts_in = parts_half(w, p - 1);
+  pa.parts_out = parts_half(w, p);
+  pa.src = static_cast<const float4 *>(state);
+  pa.target = target;
+  if (launch_pass(g, readout_sample_kernel, st, pa, tsum, chunk_incl, add) != cudaSuccess)
+    return GQAOA_ECUDA;
+  finalize_readout_kernel<<<1, 32, 0, st>>>(pa.parts_out, g.nparts, p, out, trace);
+  GQ_CHECK_LAUNCH();
+  return sample_direct_tail(static_cast<const float4 *>(state), add, g.ntiles, seed, shots,
+                            out_idx, base + o_samp, st);
 }
 
 extern "C" int gqaoa_grad_workspace_size(int n, int p, size_t *bytes) {

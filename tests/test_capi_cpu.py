@@ -56,6 +56,21 @@ def test_workspace_sizes_monotone():
     assert C.gqaoa_prob_workspace_size(28) > 0
 
 
+def test_evolve_sample_workspace_and_arguments():
+    # the fused call's workspace holds the evolution's and the sampler's
+    assert C.gqaoa_evolve_sample_workspace_size(20, 8, 1000) >= (
+        C.gqaoa_evolve_workspace_size(20, 8) + C.gqaoa_sample_workspace_size(20, 1000))
+    with pytest.raises(C.GQAOAError) as e:
+        C.gqaoa_evolve_sample_workspace_size(20, 8, 1 << 32)
+    assert e.value.status == C.GQAOA_ERANGE
+    fake = 1 << 20
+    with pytest.raises(C.GQAOAError) as e:  # a workspace one byte short, before any launch
+        need = C.gqaoa_evolve_sample_workspace_size(20, 8, 1000)
+        C.gqaoa_evolve_sample(fake, 20, 84, fake, fake, 8, fake, None, None, 1, 1000, fake, fake,
+                              need - 1, 0, None)
+    assert e.value.status == C.GQAOA_ENOMEM
+
+
 def test_batched_geometry_query():
     # below one 4096-amplitude tile an instance is one CTA; at n = 16 a batch
     # spreads each instance over several CTAs and reduction records, never

@@ -120,6 +120,30 @@ def test_shots_match_oracle_on_the_same_state(run):
     compare_same_state(run["shots"], ref, cdf, 12345, eps=1e-14 * cdf[-1], label="n=28")
 
 
+def test_fused_evolve_sample_equals_separate_calls(run):
+    # the benchmark's call: gqaoa_evolve_sample adds a_p on the fly instead of
+    # materialising psi_p; readouts and every one of the 10^6 shots must equal
+    # those of gqaoa_evolve followed by gqaoa_sample
+    n, m, p = N_VARS, M_CLAUSES, P_ROUNDS
+    dev = torch.device("cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    cost = torch.as_tensor(run["cost"], device=dev)
+    gd = torch.as_tensor(run["g"], device=dev)
+    bd = torch.as_tensor(run["b"], device=dev)
+    state = torch.empty(1 << n, dtype=torch.complex64, device=dev)
+    out = torch.empty(3, dtype=torch.float64, device=dev)
+    trace = torch.empty(p, dtype=torch.float64, device=dev)
+    shots = torch.empty(SHOTS, dtype=torch.int64, device=dev)
+    ws = core.workspace(C.gqaoa_evolve_sample_workspace_size(n, p, SHOTS))
+    C.gqaoa_evolve_sample(cost.data_ptr(), n, m, gd.data_ptr(), bd.data_ptr(), p, state.data_ptr(),
+                          out.data_ptr(), trace.data_ptr(), 12345, SHOTS, shots.data_ptr(),
+                          ws.data_ptr(), ws.numel(), 0, s)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), run["out"])
+    assert np.array_equal(trace.cpu().numpy(), run["trace"])
+    assert np.array_equal(shots.cpu().numpy(), run["shots"])
+
+
 def test_shot_classes_follow_cost_class_weights(run):
     import scipy.stats
     c = run["ref_cost"][run["shots"]]

@@ -220,14 +220,17 @@ def check_shots_valid(shots, psi_ref, seed, tol):
 
 
 @pytest.mark.parametrize("n,shots", [(6, 3000), (10, 20000), (12, 20000), (13, 50000),
-                                     (15, 1_000_000), (16, 50000), (20, 200000)])
+                                     (15, 1_000_000), (16, 50000), (20, 200000), (16, 1000),
+                                     (20, 16384), (22, 65536)])
 def test_sample_matches_oracle_on_the_same_state(n, shots):
     # Sampling is index work: given the same complex64 state (upcast to FP64
     # for the oracle) and the same Philox uniforms, every shot must be the
     # oracle's, except where a target lies within the CDFs' rounding (a few
     # FP64 units of the norm on both sides) of a boundary. n = 6, 10: one-CTA
-    # path; 12..15: all tiles resident in shared memory; 16, 20: shots
-    # bucketed by tile.
+    # path; 12..15: all tiles resident in shared memory; 16 with 50000 and 20
+    # with 200000 shots: shots bucketed by tile; 16 with 1000, 20 with 16384
+    # and 22 with 65536 shots (at most 64 per tile): each shot resolved from
+    # the stored chunk prefixes.
     m, p, seed = 4 * n, 5, 71
     lits = instances.random_3sat(n, m, seed)
     g, b = instances.random_angles(p, seed)
