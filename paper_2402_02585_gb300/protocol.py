@@ -28,6 +28,8 @@ statevector decides.
 
 from __future__ import annotations
 
+import contextlib
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -60,11 +62,62 @@ def grid_for(n: int, seed: int = 0):
     return instances.protocol_random_angles(4000, seed)
 
 
+class _CaptureGate:
+    """Protocol threads issue CUDA work side by side, but a CUDA graph is
+    captured with no other protocol thread inside a CUDA call: even in
+    thread-local capture mode, PyTorch's allocator and copies on other
+    threads meet the open capture (an invalidated capture, failed copies).
+    Work sections run concurrently; a capture waits for the running ones to
+    leave and holds new ones back until it is done. Captures are rare (one
+    per instance and depth), so the waits are short."""
+
+    def __init__(self):
+        self._cv = threading.Condition()
+        self._active = 0
+        self._capturing = False
+
+    @contextlib.contextmanager
+    def work(self):
+        with self._cv:
+            while self._capturing:
+                self._cv.wait()
+            self._active += 1
+        try:
+            yield
+        finally:
+            with self._cv:
+                self._active -= 1
+                if self._active == 0:
+                    self._cv.notify_all()
+
+    @contextlib.contextmanager
+    def capture(self):
+        with self._cv:
+            while self._capturing:
+                self._cv.wait()
+            self._capturing = True
+            while self._active > 0:
+                self._cv.wait()
+        try:
+            yield
+        finally:
+            with self._cv:
+                self._capturing = False
+                self._cv.notify_all()
+
+
+_GATE = _CaptureGate()
+
+
 class _EnergyGrad:
     """<H_P> and its adjoint gradient at a fixed depth p with resident
     buffers: the angles go to the device in one copy from pinned host memory
-    and the value and both gradients come back in one (an L-BFGS-B search
-    makes hundreds of these small calls, so their host cost matters)."""
+    and the value and both gradients come back in one. An L-BFGS-B search
+    makes hundreds of these small calls and each is 2p + 3 kernel launches
+    on the streaming path, so after one direct call the library call is
+    captured once into a CUDA graph and every further evaluation is one copy
+    up, one graph launch and one copy down (the same kernels in the same
+    order, so the same results)."""
 
     def __init__(self, prot: "Protocol", p: int):
         dev = prot.cost.device
@@ -80,16 +133,46 @@ class _EnergyGrad:
         self.args = (prot.cost.data_ptr(), prot.n, prot.m, ang, ang + 8 * p, p,
                      core.objective_code("energy"), out, out + 8, out + 8 + 8 * p,
                      self.ws.data_ptr(), self.ws.numel())
+        self.graph = None
+
+    def _capture(self, stream):
+        # Only the library call is captured (the two small pinned-memory
+        # copies stay outside: PyTorch's pinned-memory allocator records and
+        # later queries an event per copy, which must not land in a capture).
+        # The capture runs on a side stream in thread-local mode, with
+        # capture_begin / capture_end called directly, because the
+        # torch.cuda.graph context synchronises the whole device on entry;
+        # protocol searches on other host threads keep running meanwhile.
+        with _GATE.capture():
+            side = torch.cuda.Stream(stream.device)
+            side.wait_stream(stream)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(side):
+                g.capture_begin(capture_error_mode="thread_local")
+                try:
+                    C.gqaoa_grad(*self.args, side.cuda_stream)
+                finally:
+                    g.capture_end()
+            stream.wait_stream(side)
+            side.synchronize()
+        self.graph = g
 
     def __call__(self, gammas, betas):
         p = self.p
         self.a_ang[:p] = gammas
         self.a_ang[p:] = betas
-        st = torch.cuda.current_stream()
-        self.d_ang.copy_(self.h_ang, non_blocking=True)
-        C.gqaoa_grad(*self.args, st.cuda_stream)
-        self.h_out.copy_(self.d_out, non_blocking=True)
-        st.synchronize()  # also frees the pinned buffers for the next call
+        with _GATE.work():
+            st = torch.cuda.current_stream()
+            self.d_ang.copy_(self.h_ang, non_blocking=True)
+            if self.graph is not None:
+                self.graph.replay()
+            else:
+                # the first call also sets the library's per-device caches up
+                C.gqaoa_grad(*self.args, st.cuda_stream)
+            self.h_out.copy_(self.d_out, non_blocking=True)
+            st.synchronize()  # also frees the pinned buffers for the next call
+        if self.graph is None:
+            self._capture(st)
         return float(self.a_out[0]), self.a_out[1:1 + p].copy(), self.a_out[1 + p:].copy()
 
 
@@ -119,7 +202,8 @@ class Protocol:
         p = len(gammas)
         call = self._grad_calls.get(p)
         if call is None:
-            call = self._grad_calls[p] = _EnergyGrad(self, p)
+            with _GATE.work():
+                call = self._grad_calls[p] = _EnergyGrad(self, p)
         self.evaluations += 1
         self.launches += 3 if self._small else 2 * p + 3
         return call(gammas, betas)
@@ -148,37 +232,45 @@ class Protocol:
 
     def probability(self, gammas, betas, cls: int = 0) -> float:
         """Probability of cost value cls in the evolved state (statevector)."""
-        _, out, _ = core.evolve(self.cost, self.n, self.m, gammas, betas,
-                                ws=self._evolve_workspace(len(gammas)), readout_class=cls)
-        self.launches += 2 if self._small else len(gammas) + 3
-        return float(out[0].item())
+        with _GATE.work():
+            _, out, _ = core.evolve(self.cost, self.n, self.m, gammas, betas,
+                                    ws=self._evolve_workspace(len(gammas)), readout_class=cls)
+            self.launches += 2 if self._small else len(gammas) + 3
+            return float(out[0].item())
 
     def min_rounds(self, S: float = 0.5, p_max: int = 64, single: bool = True,
-                   grid=None, seed: int = 0, target: str = "P") -> MinRounds:
-        """target "P": probability of a solution; "D": of a Max-SAT assignment."""
+                   grid=None, seed: int = 0, target: str = "P", p_start: int = 1) -> MinRounds:
+        """target "P": probability of a solution; "D": of a Max-SAT assignment.
+        Depths p_start..p_max are searched (each depth's refinement depends
+        only on its own grid seed, so a search continued at p_start = k + 1
+        after depths 1..k failed returns what a search from depth 1 would)."""
         t0 = time.perf_counter()
         self.evaluations = 0
         self.launches = 0
         G, B = grid if grid is not None else grid_for(self.n, seed)
-        out, best = core.reduced_sweep(self.hist[None], self.n, G, B, p_max)
-        self.launches += 3  # phase tables, the cost-class evolution, the argmin
-        bi = best[0].long()
-        seed_vals = out[0, bi, torch.arange(p_max, device=out.device)].cpu().numpy()
-        bi = bi.cpu().numpy()
+        with _GATE.work():
+            out, best = core.reduced_sweep(self.hist[None], self.n, G, B, p_max)
+            self.launches += 3  # phase tables, the cost-class evolution, the argmin
+            bi = best[0].long()
+            seed_vals = out[0, bi, torch.arange(p_max, device=out.device)].cpu().numpy()
+            bi = bi.cpu().numpy()
+            del out, best
         col = 0 if target == "P" else 2
         cls = 0 if target == "P" else self.min_class
         res = MinRounds(None, None, None, None, None, grid_prob=seed_vals[:, col].copy())
-        for k in range(1, p_max + 1):
+        for k in range(max(1, p_start), p_max + 1):
             a = int(bi[k - 1])
             g, b, e, _ = self.refine([G[a]] * k, [B[a]] * k, single=single)
-            self._grad_calls.pop(k, None)  # this depth's checkpoints, k 2^n 8 bytes
+            with _GATE.work():
+                self._grad_calls.pop(k, None)  # this depth's checkpoints, k 2^n 8 bytes
             prob = self.probability(g, b, cls)
             if prob >= S:
                 res.p, res.gammas, res.betas, res.prob, res.energy = k, g, b, prob, e
                 break
         res.evaluations = self.evaluations
         res.launches = self.launches
-        torch.cuda.current_stream().synchronize()
+        with _GATE.work():
+            torch.cuda.current_stream().synchronize()
         res.seconds = time.perf_counter() - t0
         return res
 
@@ -190,24 +282,29 @@ def min_rounds_many(protocols, workers: int = 8, retry_p_max: int | None = None,
     threads, each on its own CUDA stream, keep the GPU busy while the others
     wait on the host. Instances are independent, so the results are those of
     calling min_rounds one instance after another. An instance that does not
-    reach S within p_max is searched again up to retry_p_max (if given)."""
+    reach S within p_max is searched further, up to retry_p_max (if given)."""
     from concurrent.futures import ThreadPoolExecutor
 
     device = protocols[0].cost.device if protocols else None
-    streams = [torch.cuda.Stream(device) for _ in range(max(1, workers))]
+    local = threading.local()  # one CUDA stream per worker thread
 
     def one(i):
-        with torch.cuda.stream(streams[i % len(streams)]):
+        if not hasattr(local, "stream"):
+            with _GATE.work():
+                local.stream = torch.cuda.Stream(device)
+        with torch.cuda.stream(local.stream):
             r = protocols[i].min_rounds(**kwargs)
             if r.p is None and retry_p_max:
                 first = r
-                r = protocols[i].min_rounds(**dict(kwargs, p_max=retry_p_max))
+                r = protocols[i].min_rounds(**dict(kwargs, p_max=retry_p_max,
+                                                   p_start=kwargs.get("p_max", 64) + 1))
                 r.launches += first.launches
                 r.evaluations += first.evaluations
-            torch.cuda.current_stream().synchronize()
+            with _GATE.work():
+                torch.cuda.current_stream().synchronize()
             return r
 
-    with ThreadPoolExecutor(max_workers=len(streams)) as pool:
+    with ThreadPoolExecutor(max_workers=max(1, workers)) as pool:
         return list(pool.map(one, range(len(protocols))))
 
 
