@@ -59,7 +59,7 @@ WORKLOADS = {
     # the paper's angle protocol (Appendix C) on satisfiable instances of
     # Section III's density range; one step = the protocol for every instance
     "protocol": dict(kind="protocol", count=32, n_values=list(range(10, 17)), d_lo=2.0, d_hi=4.5,
-                     S=0.5, p_max=64, seed=0,
+                     S=0.5, p_max=64, seed=0, window=16, workers=4,
                      desc="32 satisfiable random 3-SAT instances, n uniform in 10..16, d uniform "
                           "in (2, 4.5); pi/180 <H_P> grid (cost-class model), L-BFGS-B with "
                           "statevector adjoint gradients, fewest single-angle-pair rounds to "
@@ -67,7 +67,7 @@ WORKLOADS = {
     # the same protocol for Max-SAT on unsatisfiable instances of the (4.6, 8)
     # range, target D = probability of the lowest non-empty cost class
     "protocol_maxsat": dict(kind="protocol", count=32, n_values=list(range(10, 17)), d_lo=4.6,
-                            d_hi=8.0, S=0.5, p_max=64, seed=1, target="D",
+                            d_hi=8.0, S=0.5, p_max=64, seed=1, target="D", window=16, workers=4,
                             desc="32 unsatisfiable random 3-SAT instances, n uniform in 10..16, d "
                                  "uniform in (4.6, 8); pi/180 <H_P> grid (cost-class model), "
                                  "L-BFGS-B with statevector adjoint gradients, fewest "
@@ -79,6 +79,7 @@ WORKLOADS = {
     # warm-up pass runs the first warm_count instances only
     "protocol_scaling": dict(kind="protocol", count=45, n_values=list(range(10, 25)), d_lo=2.0,
                              d_hi=4.5, S=0.5, p_max=64, retry_p_max=256, seed=2, warm_count=4,
+                             window=8, workers=4,
                              desc="45 satisfiable random 3-SAT instances, n uniform in 10..24, d "
                                   "uniform in (2, 4.5); <H_P> on the pi/180 grid (n <= 20) or 4000 "
                                   "sampled angle pairs (n > 20) by the cost-class model, L-BFGS-B "
@@ -763,7 +764,8 @@ def run_protocol(args, wl):
                                 wl["d_hi"], satisfiable=target == "P")
     prots = [(n, m, hist, Protocol(cost, hist, n, m)) for n, m, _, _, cost, hist in shapes]
 
-    workers = int(os.environ.get("GQAOA_PROTOCOL_WORKERS", "8"))
+    workers = int(os.environ.get("GQAOA_PROTOCOL_WORKERS", str(wl.get("workers", 8))))
+    window = int(os.environ.get("GQAOA_PROTOCOL_WINDOW", str(wl.get("window", 8))))
 
     retry = wl.get("retry_p_max", 4 * wl["p_max"])
 
@@ -771,7 +773,7 @@ def run_protocol(args, wl):
         # several instances in flight (host threads, one CUDA stream each)
         sel = prots if count is None else prots[:count]
         return min_rounds_many([pr for _, _, _, pr in sel], workers=workers, retry_p_max=retry,
-                               S=wl["S"], p_max=wl["p_max"], target=target)
+                               S=wl["S"], p_max=wl["p_max"], target=target, window=window)
 
     for _ in range(args.warmup):
         one_pass(wl.get("warm_count"))
@@ -842,6 +844,7 @@ def run_protocol(args, wl):
             "data": "synthetic",
             "config": {"workload": wl["desc"], "instances": len(prots), "S": wl["S"],
                        "p_max": wl["p_max"], "retry_p_max": retry, "host_threads": workers,
+                       "depth_window": window,
                        "warmup_pass": "all instances" if wl.get("warm_count") is None
                        else f"the first {wl['warm_count']} instances"},
             "roofline": {"bound": "alu", "achieved": grid_rate, "peak": alu_peak,
@@ -855,6 +858,7 @@ def run_protocol(args, wl):
             "p_min": [None if r.p is None else int(r.p) for r in results],
             "n": [int(n) for n, _, _, _ in prots],
             "seconds_per_instance": [round(float(r.seconds), 4) for r in results],
+            "evaluations_per_instance": [int(r.evaluations) for r in results],
             "target": target,
             "random_guess_probability": [float(x) for x in pr],
             "fitted_exponent": slope,

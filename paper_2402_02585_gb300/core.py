@@ -96,9 +96,10 @@ def evolve(cost: torch.Tensor, n: int, m: int, gammas, betas, state: torch.Tenso
 
 def evolve_batched(cost: torch.Tensor, n: int, m: int, gammas, betas, shared_cost: bool = False,
                    state: torch.Tensor | None = None, state_in: bool = False, trace: bool = False,
-                   ws: torch.Tensor | None = None):
+                   ws: torch.Tensor | None = None, readout_class: int = 0):
     """Batched Eq. 3. gammas, betas [B, p]; cost [B, 2^n] or [2^n] if shared_cost.
-    Returns (state [B, 2^n], out [B, 3], trace [B, p] or None)."""
+    Returns (state [B, 2^n], out [B, 3], trace [B, p] or None); out[:, 0] is the
+    probability of cost value readout_class (default 0: P(C=0))."""
     _require_cuda(cost)
     device = cost.device
     g = _angles(gammas, device)
@@ -112,9 +113,9 @@ def evolve_batched(cost: torch.Tensor, n: int, m: int, gammas, betas, shared_cos
     if ws is None or ws.numel() < need:
         ws = workspace(need, device)
     stride = 0 if shared_cost else (1 << n)
+    flags = (C.GQAOA_STATE_IN if state_in else 0) | C.GQAOA_READOUT_CLASS(readout_class)
     C.gqaoa_evolve_batched(_ptr(cost), stride, n, m, B, _ptr(g), _ptr(b), p, _ptr(state), _ptr(out),
-                           _ptr(tr), _ptr(ws), ws.numel(), C.GQAOA_STATE_IN if state_in else 0,
-                           _stream())
+                           _ptr(tr), _ptr(ws), ws.numel(), flags, _stream())
     return state, out, tr
 
 

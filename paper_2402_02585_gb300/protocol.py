@@ -54,6 +54,10 @@ class MinRounds:
     seconds: float = 0.0
 
 
+# device memory the checkpoints of one refinement window may take
+WINDOW_BUDGET_BYTES = 16 << 30
+
+
 def grid_for(n: int, seed: int = 0):
     """The protocol's angle set: the pi/180 grid for n <= 20, 4000 sampled
     angle pairs above."""
@@ -176,6 +180,99 @@ class _EnergyGrad:
         return float(self.a_out[0]), self.a_out[1:1 + p].copy(), self.a_out[1 + p:].copy()
 
 
+class _DepthBatch:
+    """<H_P> and its adjoint gradient for several depths of one instance in
+    one gqaoa_grad_batched call on the shared cost table. Depth k's angles sit
+    at the end of a row of P rounds whose first P - k rounds have
+    gamma = beta = 0: their phase factor is exactly 1 and their mixer term
+    exactly 0, so the row evolves, reads out and differentiates the depth-k
+    circuit (the padding rounds' derivatives are dropped)."""
+
+    def __init__(self, prot: "Protocol"):
+        self.prot = prot
+        self.ws = None
+
+    def __call__(self, rows):
+        """rows: list of (k, gammas [k], betas [k]). Returns a list of
+        (<H_P>, dL/dgamma [k], dL/dbeta [k])."""
+        prot = self.prot
+        dev = prot.cost.device
+        B = len(rows)
+        P = max(k for k, _, _ in rows)
+        h = torch.zeros((2, B, P), dtype=torch.float64, pin_memory=True)
+        a = h.numpy()
+        for i, (k, g, b) in enumerate(rows):
+            a[0, i, P - k:] = g
+            a[1, i, P - k:] = b
+        with _GATE.work():
+            ang = h.to(dev, non_blocking=True)
+            val = torch.empty(B, dtype=torch.float64, device=dev)
+            grad = torch.empty((2, B, P), dtype=torch.float64, device=dev)
+            need = C.gqaoa_grad_batched_workspace_size(prot.n, B, P)
+            if self.ws is None or self.ws.numel() < need:
+                self.ws = core.workspace(need, dev)
+            C.gqaoa_grad_batched(prot.cost.data_ptr(), 0, prot.n, prot.m, B, ang[0].data_ptr(),
+                                 ang[1].data_ptr(), P, core.objective_code("energy"),
+                                 val.data_ptr(), grad[0].data_ptr(), grad[1].data_ptr(),
+                                 self.ws.data_ptr(), self.ws.numel(),
+                                 torch.cuda.current_stream().cuda_stream)
+            v = val.cpu().numpy()
+            gr = grad.cpu().numpy()
+        prot.evaluations += B
+        prot.launches += 3 if prot._small else 2 * P + 3
+        return [(float(v[i]), gr[0, i, P - k:].copy(), gr[1, i, P - k:].copy())
+                for i, (k, _, _) in enumerate(rows)]
+
+
+class _Lockstep:
+    """Runs several L-BFGS-B searches side by side, one host thread each, and
+    gathers every wave of their evaluation requests into one call: a wave is
+    served once each search still running has asked for its next point."""
+
+    def __init__(self, count: int):
+        self.cv = threading.Condition()
+        self.pending = {}
+        self.results = {}
+        self.live = count
+        self.error = None
+
+    def request(self, i, x):
+        with self.cv:
+            self.pending[i] = x
+            self.cv.notify_all()
+            while i not in self.results and self.error is None:
+                self.cv.wait()
+            if self.error is not None:
+                raise RuntimeError("lockstep evaluation failed") from self.error
+            return self.results.pop(i)
+
+    def finished(self):
+        with self.cv:
+            self.live -= 1
+            self.cv.notify_all()
+
+    def serve(self, evaluate):
+        """evaluate(dict i -> x) -> dict i -> (value, gradient); runs on the
+        calling thread until every search has finished."""
+        while True:
+            with self.cv:
+                while len(self.pending) < self.live:
+                    self.cv.wait()
+                if self.live == 0:
+                    return
+                batch, self.pending = self.pending, {}
+            try:
+                out = evaluate(batch)
+            except BaseException as exc:  # wake the searches, then re-raise
+                with self.cv:
+                    self.error = exc
+                    self.cv.notify_all()
+                raise
+            with self.cv:
+                self.results.update(out)
+                self.cv.notify_all()
+
+
 class Protocol:
     """The protocol for one instance: cost [2^n] uint8 and hist [m + 1] int64
     on the device (core.build_cost). An instance keeps per-depth device and
@@ -238,12 +335,89 @@ class Protocol:
             self.launches += 2 if self._small else len(gammas) + 3
             return float(out[0].item())
 
+    def refine_window(self, depths, seeds, single: bool):
+        """L-BFGS-B on <H_P> for several depths at once (depth k from the
+        single angle pair seeds[k]): the searches run side by side and each
+        wave of their gradient requests is one batched call (_DepthBatch).
+        Each depth's search is the one refine() makes, so the results equal
+        refine()'s up to the rounding of the batched sums. Returns
+        {k: (gammas, betas, <H_P>)}."""
+        batch = _DepthBatch(self)
+        steps = _Lockstep(len(depths))
+        results, errors = {}, []
+
+        def rows_of(wave):
+            rows = []
+            for k, x in wave.items():
+                if single:
+                    rows.append((k, np.full(k, x[0]), np.full(k, x[1])))
+                else:
+                    rows.append((k, x[:k], x[k:]))
+            return rows
+
+        def evaluate(wave):
+            out = batch(rows_of(wave))
+            res = {}
+            for (k, _), (e, dg, db) in zip(wave.items(), out):
+                res[k] = (e, np.array([dg.sum(), db.sum()]) if single else np.concatenate([dg, db]))
+            return res
+
+        def search(k):
+            try:
+                g0, b0 = seeds[k]
+                x0 = np.array([g0, b0]) if single else np.concatenate([np.full(k, g0), np.full(k, b0)])
+                r = scipy.optimize.minimize(lambda x: steps.request(k, x), x0, jac=True,
+                                            method="L-BFGS-B",
+                                            options=dict(ftol=1e-6, gtol=1e-10, maxiter=500))
+                if single:
+                    results[k] = (np.full(k, r.x[0]), np.full(k, r.x[1]), float(r.fun))
+                else:
+                    results[k] = (r.x[:k].copy(), r.x[k:].copy(), float(r.fun))
+            except BaseException as exc:
+                errors.append(exc)
+            finally:
+                steps.finished()
+
+        stream = torch.cuda.current_stream()
+        threads = [threading.Thread(target=search, args=(k,)) for k in depths]
+        for t in threads:
+            t.start()
+        try:
+            with torch.cuda.stream(stream):
+                steps.serve(evaluate)
+        finally:
+            for t in threads:
+                t.join()
+        if errors:
+            raise errors[0]
+        return results
+
+    def probabilities(self, rows, cls: int = 0):
+        """Probability of cost value cls after each (gammas, betas) of rows
+        (several depths at once, padded as in _DepthBatch; statevector)."""
+        P = max(len(g) for g, _ in rows)
+        G = np.zeros((len(rows), P))
+        Bt = np.zeros((len(rows), P))
+        for i, (g, b) in enumerate(rows):
+            G[i, P - len(g):] = g
+            Bt[i, P - len(b):] = b
+        with _GATE.work():
+            _, out, _ = core.evolve_batched(self.cost, self.n, self.m, G, Bt, shared_cost=True,
+                                            readout_class=cls)
+            self.launches += 2 if self._small else P + 3
+            return out[:, 0].cpu().numpy()
+
     def min_rounds(self, S: float = 0.5, p_max: int = 64, single: bool = True,
-                   grid=None, seed: int = 0, target: str = "P", p_start: int = 1) -> MinRounds:
+                   grid=None, seed: int = 0, target: str = "P", p_start: int = 1,
+                   window: int = 1) -> MinRounds:
         """target "P": probability of a solution; "D": of a Max-SAT assignment.
         Depths p_start..p_max are searched (each depth's refinement depends
         only on its own grid seed, so a search continued at p_start = k + 1
-        after depths 1..k failed returns what a search from depth 1 would)."""
+        after depths 1..k failed returns what a search from depth 1 would).
+        window > 1 refines that many consecutive depths at once
+        (refine_window, with batched gradient calls) and accepts the
+        shallowest of them that reaches S; its checkpoints are kept within
+        WINDOW_BUDGET_BYTES by narrowing the window for large states."""
         t0 = time.perf_counter()
         self.evaluations = 0
         self.launches = 0
@@ -258,7 +432,24 @@ class Protocol:
         col = 0 if target == "P" else 2
         cls = 0 if target == "P" else self.min_class
         res = MinRounds(None, None, None, None, None, grid_prob=seed_vals[:, col].copy())
-        for k in range(max(1, p_start), p_max + 1):
+        k0 = max(1, p_start)
+        while window > 1 and k0 <= p_max:
+            W = window
+            while W > 1 and W * (k0 + W - 1) * (8 << self.n) > WINDOW_BUDGET_BYTES:
+                W -= 1
+            depths = list(range(k0, min(p_max, k0 + W - 1) + 1))
+            seeds = {k: (G[int(bi[k - 1])], B[int(bi[k - 1])]) for k in depths}
+            ref = self.refine_window(depths, seeds, single)
+            probs = self.probabilities([(ref[k][0], ref[k][1]) for k in depths], cls)
+            for k, prob in zip(depths, probs):
+                if prob >= S:
+                    g, b, e = ref[k]
+                    res.p, res.gammas, res.betas, res.prob, res.energy = k, g, b, float(prob), e
+                    break
+            if res.p is not None:
+                break
+            k0 = depths[-1] + 1
+        for k in range(k0, p_max + 1) if window <= 1 else ():
             a = int(bi[k - 1])
             g, b, e, _ = self.refine([G[a]] * k, [B[a]] * k, single=single)
             with _GATE.work():

@@ -341,6 +341,29 @@ def test_grad_batched_and_autograd():
         assert np.max(np.abs(Bt.grad[i].cpu().numpy() - rdb)) < 2e-5
 
 
+@pytest.mark.parametrize("n", [10, 14])
+def test_leading_zero_angle_rounds_are_identities(n):
+    # gamma = beta = 0: phase factor exactly 1, mixer term exactly 0, so
+    # padding a circuit with such rounds in front changes no bit of the state,
+    # the readouts or the gradient of the real rounds (the protocol's depth
+    # windows batch depths this way). The streaming passes alternate their
+    # sweep direction by round parity, which fixes the order of the partial
+    # sums, so the padding is even here; an odd one agrees to rounding.
+    m, p, pad = 4 * n, 6, 2
+    lits = instances.random_3sat(n, m, 17)
+    g, b = instances.random_angles(p, 17)
+    cost, _ = gpu_cost(lits, n)
+    gp = np.concatenate([np.zeros(pad), g])
+    bp = np.concatenate([np.zeros(pad), b])
+    s1, o1, _ = core.evolve(cost, n, m, g, b)
+    s2, o2, _ = core.evolve(cost, n, m, gp, bp)
+    assert torch.equal(s1, s2) and torch.equal(o1, o2)
+    v1, dg1, db1 = core.grad(cost, n, m, g, b, "energy")
+    v2, dg2, db2 = core.grad(cost, n, m, gp, bp, "energy")
+    assert torch.equal(v1, v2)
+    assert torch.equal(dg1, dg2[pad:]) and torch.equal(db1, db2[pad:])
+
+
 def test_single_angle_gradient_is_round_sum():
     n, m, p = 12, 50, 8
     lits = instances.random_3sat(n, m, 91)

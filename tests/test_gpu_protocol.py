@@ -110,6 +110,40 @@ def test_protocol_above_twenty_qubits_matches_oracle():
     assert abs(got.energy - e) < 0.01 * e
 
 
+@pytest.mark.parametrize("n,m,seed", [(8, 30, 11), (9, 36, 3), (10, 40, 2), (13, 52, 5)])
+def test_protocol_windowed_matches_oracle(n, m, seed):
+    # eight depths refined side by side, each wave of gradient requests one
+    # batched call with the shorter depths padded by identity rounds
+    lits = instances.random_3sat(n, m, seed)
+    _, ohist = sv.cost_table(lits, n)
+    if ohist[0] == 0:
+        pytest.skip("unsatisfiable")
+    cost, hist = core.build_cost(lits, n)
+    G, B = instances.protocol_grid(2)
+    prot = Protocol(cost, hist, n, m)
+    got = prot.min_rounds(S=0.5, p_max=24, grid=(G, B), window=8)
+    one = prot.min_rounds(S=0.5, p_max=24, grid=(G, B))
+    k, g, b, val, e = oprot.min_rounds(ohist, G, B, S=0.5, p_max=24)
+    assert got.p == one.p == k
+    assert abs(got.energy - e) < 1e-5 * m
+    assert abs(got.prob - val) < 2e-4 and got.prob >= 0.5
+    r = reduced.readouts_trace(ohist, got.gammas, got.betas)[-1]
+    assert abs(got.prob - r[0]) < 2e-5
+
+
+def test_protocol_windowed_all_angles_weak_seed():
+    n, m, seed = 10, 35, 21
+    lits = instances.random_3sat(n, m, seed)
+    _, ohist = sv.cost_table(lits, n)
+    cost, hist = core.build_cost(lits, n)
+    G, B = instances.protocol_grid(2)
+    got = Protocol(cost, hist, n, m).min_rounds(S=0.5, p_max=24, single=False, grid=(G, B),
+                                                window=6)
+    assert got.p == 17 and got.grid_prob[16] < 0.25 and got.prob >= 0.5
+    r = reduced.readouts_trace(ohist, got.gammas, got.betas)[-1]
+    assert abs(got.prob - r[0]) < 2e-5
+
+
 def test_protocol_full_angles_not_worse_than_single():
     n, m = 10, 40
     lits = instances.random_3sat(n, m, 2)
