@@ -334,12 +334,13 @@ __device__ __forceinline__ void l2_fold(float (&v)[kSlots], DF (&acc)[kSlots]) {
 
 // A streaming thread's round: nb batches of kL2Batch float4 from its slot
 // (gp: its first float4; gc: their cost bytes), kL2Ring - 1 batches ahead.
-template <bool kExtra>
+template <bool kExtra, bool kFirst>
 __device__ __forceinline__ void l2_stream_round(float4 (&ring)[kL2RegVec],
                                                 uint32_t (&cring)[kL2Ring], float4 *gp,
                                                 const uint16_t *gc, int nb, const float2 *s_T,
                                                 float2 ad, float amp0, DF (&acc)[kSlots],
-                                                bool ro, bool first) {
+                                                bool ro) {
+  constexpr bool first = kFirst;
   constexpr int T = kL2RoleThreads;
   constexpr int kStep = kL2Batch * T;
   const float4 plus = make_float4(amp0, 0.f, amp0, 0.f);
@@ -372,7 +373,7 @@ __device__ __forceinline__ void l2_stream_round(float4 (&ring)[kL2RegVec],
 #pragma unroll
         for (int k = 0; k < kL2Batch; ++k) __stcg(sp + k * T, ring[d * kL2Batch + k]);
         sp += kStep;
-        if (d & 1) l2_fold<kExtra>(v, acc);
+        if ((d & 3) == 3) l2_fold<kExtra>(v, acc);
       }
     }
   }
@@ -381,12 +382,13 @@ __device__ __forceinline__ void l2_stream_round(float4 (&ring)[kL2RegVec],
 
 // An on-chip thread's round: its kL2RegVec register float4, then its
 // kL2SmemVec shared-memory float4 ([j][thread] layout: conflict-free).
-template <bool kExtra>
+template <bool kExtra, bool kFirst>
 __device__ __forceinline__ void l2_onchip_round(float4 (&xr)[kL2RegVec],
                                                 const uint32_t (&cr)[kL2Ring], float4 *s_state,
                                                 const uint16_t *s_cost, int u, const float2 *s_T,
                                                 float2 ad, float amp0, DF (&acc)[kSlots],
-                                                bool ro, bool first) {
+                                                bool ro) {
+  constexpr bool first = kFirst;
   constexpr int T = kL2RoleThreads;
   const float4 plus = make_float4(amp0, 0.f, amp0, 0.f);
   float v[kSlots] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -394,12 +396,13 @@ __device__ __forceinline__ void l2_onchip_round(float4 (&xr)[kL2RegVec],
   for (int k = 0; k < kL2RegVec; ++k) {
     if (first) xr[k] = plus;
     l2_vec<kExtra>(xr[k], cr[k >> 1] >> (16 * (k & 1)), s_T, ad, v, ro, first);
-    if ((k & 3) == 3) l2_fold<kExtra>(v, acc);
+    if ((k & 7) == 7) l2_fold<kExtra>(v, acc);
   }
+  l2_fold<kExtra>(v, acc);
 #pragma unroll 1
-  for (int j0 = 0; j0 < kL2SmemVec; j0 += 4) {
+  for (int j0 = 0; j0 < kL2SmemVec; j0 += 8) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 8; ++k) {
       float4 y = first ? plus : s_state[(j0 + k) * T + u];
       l2_vec<kExtra>(y, s_cost[(j0 + k) * T + u], s_T, ad, v, ro, first);
       s_state[(j0 + k) * T + u] = y;
@@ -461,15 +464,19 @@ __global__ void __launch_bounds__(kL2Threads, 1) sweep_l2_kernel(const __grid_co
 #pragma unroll
       for (int k = 0; k < kSlots; ++k) acc[k].zero();
       if (streaming) {
-        if (extra)
-          l2_stream_round<true>(xr, cr, gp, gc, nb, s_T, ad, amp0, acc, ro, first);
+        if (first)
+          l2_stream_round<true, true>(xr, cr, gp, gc, nb, s_T, ad, amp0, acc, ro);
+        else if (extra)
+          l2_stream_round<true, false>(xr, cr, gp, gc, nb, s_T, ad, amp0, acc, ro);
         else
-          l2_stream_round<false>(xr, cr, gp, gc, nb, s_T, ad, amp0, acc, false, false);
+          l2_stream_round<false, false>(xr, cr, gp, gc, nb, s_T, ad, amp0, acc, false);
       } else {
-        if (extra)
-          l2_onchip_round<true>(xr, cr, s_state, s_cost, u, s_T, ad, amp0, acc, ro, first);
+        if (first)
+          l2_onchip_round<true, true>(xr, cr, s_state, s_cost, u, s_T, ad, amp0, acc, ro);
+        else if (extra)
+          l2_onchip_round<true, false>(xr, cr, s_state, s_cost, u, s_T, ad, amp0, acc, ro);
         else
-          l2_onchip_round<false>(xr, cr, s_state, s_cost, u, s_T, ad, amp0, acc, false, false);
+          l2_onchip_round<false, false>(xr, cr, s_state, s_cost, u, s_T, ad, amp0, acc, false);
       }
       float hi[kSlots], lo[kSlots];
 #pragma unroll
