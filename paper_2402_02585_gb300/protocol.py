@@ -186,38 +186,52 @@ class _DepthBatch:
     at the end of a row of P rounds whose first P - k rounds have
     gamma = beta = 0: their phase factor is exactly 1 and their mixer term
     exactly 0, so the row evolves, reads out and differentiates the depth-k
-    circuit (the padding rounds' derivatives are dropped)."""
+    circuit (the padding rounds' derivatives are dropped). Buffers for up to
+    rows_max rows of p_max rounds are allocated once; a wave moves its angles
+    up in one copy from pinned memory and its values and gradients down in
+    one."""
 
-    def __init__(self, prot: "Protocol"):
+    def __init__(self, prot: "Protocol", rows_max: int, p_max: int):
         self.prot = prot
+        dev = prot.cost.device
+        n_in, n_out = 2 * rows_max * p_max, rows_max + 2 * rows_max * p_max
+        with _GATE.work():
+            self.h_in = torch.empty(n_in, dtype=torch.float64, pin_memory=True)
+            self.h_out = torch.empty(n_out, dtype=torch.float64, pin_memory=True)
+            self.d_in = torch.empty(n_in, dtype=torch.float64, device=dev)
+            self.d_out = torch.empty(n_out, dtype=torch.float64, device=dev)
+        self.a_in = self.h_in.numpy()
+        self.a_out = self.h_out.numpy()
         self.ws = None
 
     def __call__(self, rows):
         """rows: list of (k, gammas [k], betas [k]). Returns a list of
         (<H_P>, dL/dgamma [k], dL/dbeta [k])."""
         prot = self.prot
-        dev = prot.cost.device
         B = len(rows)
         P = max(k for k, _, _ in rows)
-        h = torch.zeros((2, B, P), dtype=torch.float64, pin_memory=True)
-        a = h.numpy()
+        a = self.a_in[:2 * B * P].reshape(2, B, P)
+        a[:] = 0.0
         for i, (k, g, b) in enumerate(rows):
             a[0, i, P - k:] = g
             a[1, i, P - k:] = b
+        nb = B + 2 * B * P
         with _GATE.work():
-            ang = h.to(dev, non_blocking=True)
-            val = torch.empty(B, dtype=torch.float64, device=dev)
-            grad = torch.empty((2, B, P), dtype=torch.float64, device=dev)
+            st = torch.cuda.current_stream()
+            d_in = self.d_in[:2 * B * P]
+            d_in.copy_(self.h_in[:2 * B * P], non_blocking=True)
             need = C.gqaoa_grad_batched_workspace_size(prot.n, B, P)
             if self.ws is None or self.ws.numel() < need:
-                self.ws = core.workspace(need, dev)
-            C.gqaoa_grad_batched(prot.cost.data_ptr(), 0, prot.n, prot.m, B, ang[0].data_ptr(),
-                                 ang[1].data_ptr(), P, core.objective_code("energy"),
-                                 val.data_ptr(), grad[0].data_ptr(), grad[1].data_ptr(),
-                                 self.ws.data_ptr(), self.ws.numel(),
-                                 torch.cuda.current_stream().cuda_stream)
-            v = val.cpu().numpy()
-            gr = grad.cpu().numpy()
+                self.ws = core.workspace(need, prot.cost.device)
+            ang, out = d_in.data_ptr(), self.d_out.data_ptr()
+            C.gqaoa_grad_batched(prot.cost.data_ptr(), 0, prot.n, prot.m, B, ang, ang + 8 * B * P, P,
+                                 core.objective_code("energy"), out, out + 8 * B,
+                                 out + 8 * (B + B * P), self.ws.data_ptr(), self.ws.numel(),
+                                 st.cuda_stream)
+            self.h_out[:nb].copy_(self.d_out[:nb], non_blocking=True)
+            st.synchronize()
+        v = self.a_out[:B]
+        gr = self.a_out[B:nb].reshape(2, B, P)
         prot.evaluations += B
         prot.launches += 3 if prot._small else 2 * P + 3
         return [(float(v[i]), gr[0, i, P - k:].copy(), gr[1, i, P - k:].copy())
@@ -227,50 +241,59 @@ class _DepthBatch:
 class _Lockstep:
     """Runs several L-BFGS-B searches side by side, one host thread each, and
     gathers every wave of their evaluation requests into one call: a wave is
-    served once each search still running has asked for its next point."""
+    served once each search still running has asked for its next point. Each
+    search waits on its own event and the serving thread on one more, so a
+    wave wakes every thread once."""
 
-    def __init__(self, count: int):
-        self.cv = threading.Condition()
+    def __init__(self, keys):
+        self.lock = threading.Lock()
+        self.ready = threading.Event()  # the serving thread's
+        self.done = {k: threading.Event() for k in keys}
         self.pending = {}
         self.results = {}
-        self.live = count
+        self.live = len(self.done)
         self.error = None
 
     def request(self, i, x):
-        with self.cv:
+        ev = self.done[i]
+        ev.clear()
+        with self.lock:
             self.pending[i] = x
-            self.cv.notify_all()
-            while i not in self.results and self.error is None:
-                self.cv.wait()
-            if self.error is not None:
-                raise RuntimeError("lockstep evaluation failed") from self.error
-            return self.results.pop(i)
+            if len(self.pending) >= self.live:
+                self.ready.set()
+        ev.wait()
+        if self.error is not None:
+            raise RuntimeError("lockstep evaluation failed") from self.error
+        return self.results.pop(i)
 
     def finished(self):
-        with self.cv:
+        with self.lock:
             self.live -= 1
-            self.cv.notify_all()
+            if len(self.pending) >= self.live:
+                self.ready.set()
 
     def serve(self, evaluate):
         """evaluate(dict i -> x) -> dict i -> (value, gradient); runs on the
         calling thread until every search has finished."""
         while True:
-            with self.cv:
-                while len(self.pending) < self.live:
-                    self.cv.wait()
+            self.ready.wait()
+            with self.lock:
+                self.ready.clear()
                 if self.live == 0:
                     return
+                if len(self.pending) < self.live:
+                    continue
                 batch, self.pending = self.pending, {}
             try:
                 out = evaluate(batch)
             except BaseException as exc:  # wake the searches, then re-raise
-                with self.cv:
-                    self.error = exc
-                    self.cv.notify_all()
+                self.error = exc
+                for k in batch:
+                    self.done[k].set()
                 raise
-            with self.cv:
-                self.results.update(out)
-                self.cv.notify_all()
+            self.results.update(out)
+            for k in out:
+                self.done[k].set()
 
 
 class Protocol:
@@ -342,8 +365,8 @@ class Protocol:
         Each depth's search is the one refine() makes, so the results equal
         refine()'s up to the rounding of the batched sums. Returns
         {k: (gammas, betas, <H_P>)}."""
-        batch = _DepthBatch(self)
-        steps = _Lockstep(len(depths))
+        batch = _DepthBatch(self, len(depths), max(depths))
+        steps = _Lockstep(depths)
         results, errors = {}, []
 
         def rows_of(wave):

@@ -28,7 +28,7 @@ def test_lockstep_equals_independent_searches():
     x0 = {k: np.array([0.1 * k, 1.0 - 0.05 * k]) for k in ks}
     alone = {k: _minimize(lambda x, k=k: _fun(k, x), x0[k]) for k in ks}
 
-    steps = _Lockstep(len(ks))
+    steps = _Lockstep(ks)
     waves, got = [], {}
 
     def search(k):
@@ -57,7 +57,7 @@ def test_lockstep_equals_independent_searches():
 
 
 def test_lockstep_error_reaches_the_searches():
-    steps = _Lockstep(2)
+    steps = _Lockstep([0, 1])
     seen = []
 
     def search(k):
