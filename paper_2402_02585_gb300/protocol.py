@@ -24,6 +24,15 @@ single angle pair, or, for G-QAOA with per-round angles, from the same seed
 over all 2k angles. The cost-class and statevector evaluations agree to
 complex64 precision (tested), so the grid ranks candidates and the
 statevector decides.
+
+Evaluations are issued in one of two ways. Depth by depth (window = 1), each
+depth's gqaoa_grad call is captured once into a CUDA graph and replayed for
+every L-BFGS-B evaluation. With a depth window (window = W), W consecutive
+depths are refined side by side: their L-BFGS-B searches run on host
+threads in lockstep and every wave of their gradient requests is one
+gqaoa_grad_batched call, the shallower depths padded with identity rounds;
+the shallowest depth of the window that reaches S is the answer, as in the
+depth-by-depth scan.
 """
 
 from __future__ import annotations
