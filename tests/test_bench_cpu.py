@@ -33,3 +33,27 @@ def test_reference_arm_json_line():
 def test_reference_arm_unavailable_for_device_only_workloads():
     d = run("--impl", "reference", "--workload", "grad")
     assert d["impl"] == "reference" and "unavailable" in d
+
+
+def test_workload_table():
+    # every workload names its kind's required fields and a description of
+    # what it runs (the JSON line's config.workload)
+    sys.path.insert(0, ROOT)
+    import bench
+    need = {None: ("n", "m", "p", "shots", "seed"),
+            "grad": ("n", "m", "p", "batch", "lr"),
+            "sweep": ("count", "grid", "p", "rounds"),
+            "protocol": ("count", "n_values", "d_lo", "d_hi", "S", "p_max"),
+            "fairness": ("n", "runs", "shots_per_run", "alpha"),
+            "study": ("train", "train_n", "test", "test_n", "p")}
+    for name, wl in bench.WORKLOADS.items():
+        assert isinstance(wl.get("desc"), str) and wl["desc"], name
+        for key in need[wl.get("kind")]:
+            assert key in wl, (name, key)
+    assert bench.WORKLOADS["study"]["train"] == 20000 and bench.WORKLOADS["study"]["test"] == 2000
+    assert bench.WORKLOADS["protocol_scaling"]["n_values"] == list(range(10, 25))
+
+
+def test_reference_arm_unavailable_for_the_study():
+    d = run("--impl", "reference", "--workload", "study")
+    assert d["impl"] == "reference" and "unavailable" in d
