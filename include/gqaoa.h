@@ -157,10 +157,13 @@ int gqaoa_sample_workspace_size(int n, int64_t shots, size_t *bytes);
  * Fair sampling of measurement shots (Section IV, "sample all solutions";
  * Section II.B: the Grover mixer weights every solution equally):
  *   shot s = smallest z with CDF(z) > u_s * CDF(2^n - 1),
- *   CDF(z) = sum_{y <= z} |psi(y)|^2, accumulated as FP32 sums of 16
- *            consecutive |psi|^2, prefixes of those within a tile of 4096
- *            amplitudes in double-float (about 2^-44 relative, rounded to
- *            FP64) and prefixes of the tile totals in FP64,
+ *   CDF(z) = sum_{y <= z} |psi(y)|^2, each |psi(y)|^2 formed from the
+ *            complex64 parts as a double-float pair (relative error below
+ *            2^-46), sums of 16 consecutive weights and their prefixes within
+ *            a tile of 4096 amplitudes in double-float (rounded to FP64), and
+ *            prefixes of the tile totals in FP64 pairs rounded to FP64: every
+ *            CDF value lies within a few FP64 rounding units of the total of
+ *            the exact prefix sum,
  *   u_s    = uniform double in [0,1) from Philox4x32-10 (Salmon et al.,
  *            SC 2011) with counter (s mod 2^32, s >> 32, 0, 0) and key
  *            (seed mod 2^32, seed >> 32); the top 53 bits of the 64-bit word
