@@ -69,6 +69,21 @@ def test_evolve_sample_workspace_and_arguments():
         C.gqaoa_evolve_sample(fake, 20, 84, fake, fake, 8, fake, None, None, 1, 1000, fake, fake,
                               need - 1, 0, None)
     assert e.value.status == C.GQAOA_ENOMEM
+    ws = C.gqaoa_evolve_sample_workspace_size(20, 8, 1000)
+    bad = [
+        # (n, shots, out_idx, trace, flags) -> status, all before any launch
+        ((20, 1000, fake, fake, C.GQAOA_READOUT_CLASS(3)), C.GQAOA_EINVAL),  # class + trace
+        ((20, 1000, fake, None, 1 << 20), C.GQAOA_EINVAL),                    # unknown flag
+        ((20, 1000, None, None, 0), C.GQAOA_EINVAL),                          # shots, no output
+        ((20, -1, fake, None, 0), C.GQAOA_ERANGE),
+        ((40, 1000, fake, None, 0), C.GQAOA_ERANGE),
+        ((20, 1000, fake + 4, None, 0), C.GQAOA_EINVAL),                      # misaligned
+    ]
+    for (n, shots, oi, tr, flags), code in bad:
+        with pytest.raises(C.GQAOAError) as e:
+            C.gqaoa_evolve_sample(fake, n, 84, fake, fake, 8, fake, None, tr, 1, shots, oi, fake,
+                                  ws, flags, None)
+        assert e.value.status == code, (n, shots, flags)
 
 
 def test_batched_geometry_query():
