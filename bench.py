@@ -777,22 +777,25 @@ def run_protocol(args, wl):
 
     for _ in range(args.warmup):
         one_pass(wl.get("warm_count"))
-    # the grid call alone (phase tables + cost-class kernel, no argmin), on
-    # the full pi/180 grid of the first instance, buffers resident
+    # the grid call alone as the protocol makes it (phase tables, cost-class
+    # kernel with the per-round argmin), on the full pi/180 grid of the first
+    # instance, buffers resident
     G, B = instances.protocol_grid()
-    n0, _, h0, _ = prots[0]
+    n0, _, h0, prot0 = prots[0]
     dev = torch.device("cuda", local)
-    h0d = h0.reshape(1, -1).contiguous()
+    h0d = prot0.grid_hist
     Gd = torch.as_tensor(G, dtype=torch.float64, device=dev)
     Bd = torch.as_tensor(B, dtype=torch.float64, device=dev)
     grid_out = torch.empty((1, len(G), wl["p_max"], 3), dtype=torch.float64, device=dev)
-    grid_ws = core.workspace(C.gqaoa_reduced_sweep_workspace_size(len(G)), dev)
+    grid_best = torch.empty((1, wl["p_max"]), dtype=torch.int32, device=dev)
+    grid_ws = core.workspace(
+        C.gqaoa_reduced_sweep_workspace_size(h0d.shape[1], 1, len(G), wl["p_max"]), dev)
     st = torch.cuda.current_stream().cuda_stream
 
     def grid_call():
         C.gqaoa_reduced_sweep(h0d.data_ptr(), h0d.shape[1], n0, 1, Gd.data_ptr(), Bd.data_ptr(),
-                              len(G), wl["p_max"], grid_out.data_ptr(), None, grid_ws.data_ptr(),
-                              grid_ws.numel(), st)
+                              len(G), wl["p_max"], grid_out.data_ptr(), grid_best.data_ptr(),
+                              grid_ws.data_ptr(), grid_ws.numel(), st)
 
     grid_call()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -828,12 +831,14 @@ def run_protocol(args, wl):
     slope_big = (float(np.polyfit(np.log(1 / pr[big]), np.log(pm[big]), 1)[0])
                  if big.sum() > 2 else None)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    # grid call: the cost-class arithmetic is 14 FP32 instructions per class
-    # and round (phase and mixer 8, readout 6); the ceiling issues them at
-    # 4 warp-instructions (128 lanes) per clock per SM, so an item-round of
-    # m + 1 classes costs 14 (m + 1) / 32 warp-instructions
-    classes = int(h0.numel())
-    alu_peak = 4 * sms * 2.07e9 / (14 * classes / 32)
+    # grid call: the cost-class arithmetic is 11 FP32 instructions per class
+    # and round (complex phase multiply 4, the S sum 2, mixer add 2, the
+    # <H_P> term 3) over the classes from the lowest to the highest non-empty
+    # one; the ceiling issues them at 4 warp-instructions (128 lanes) per
+    # clock per SM, so an item-round of that many classes costs 11 classes / 32
+    nz = torch.nonzero(h0).flatten()
+    classes = int(nz[-1]) - int(nz[0]) + 1
+    alu_peak = 4 * sms * 2.07e9 / (11 * classes / 32)
     grid_rate = len(G) * wl["p_max"] / t_grid
     if rank == 0:
         print(json.dumps({
@@ -849,10 +854,11 @@ def run_protocol(args, wl):
                        else f"the first {wl['warm_count']} instances"},
             "roofline": {"bound": "alu", "achieved": grid_rate, "peak": alu_peak,
                          "unit": "item-rounds/s", "frac": grid_rate / alu_peak,
-                         "kernel": f"gqaoa_reduced_sweep (phase tables + reduced_sweep_kernel): "
-                                   f"pi/180 grid ({len(G)} angle pairs) x p = {wl['p_max']}, "
-                                   f"n = {n0}, {classes} classes, {t_grid * 1e3:.3f} ms",
-                         "peak_derivation": "4 warp-instr/clk/SM x SMs x 2.07 GHz / (14 FP32 "
+                         "kernel": f"gqaoa_reduced_sweep (phase tables, reduced_sweep_kernel "
+                                   f"with the per-round argmin): pi/180 grid ({len(G)} angle "
+                                   f"pairs) x p = {wl['p_max']}, n = {n0}, {classes} classes "
+                                   f"(histogram stride {h0d.shape[1]}), {t_grid * 1e3:.3f} ms",
+                         "peak_derivation": "4 warp-instr/clk/SM x SMs x 2.07 GHz / (11 FP32 "
                                             f"instructions x {classes} classes / 32 lanes) per "
                                             "item-round"},
             "p_min": [None if r.p is None else int(r.p) for r in results],

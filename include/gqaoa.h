@@ -321,30 +321,39 @@ int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const double *gamm
  * entry points above remain the evolution itself.
  * For every instance b < batch and angle point a < angles it evolves p
  * rounds with gamma_k = gammas[a], beta_k = betas[a] from |+> and writes,
- * after every round k (0-based),
- *   out[((b * angles + a) * p + k) * 3 + 0] = P(C=0),
- *   out[... + 1] = <H_P> (Eq. 4),
- *   out[... + 2] = D, the probability of the lowest non-empty cost class
- *                  (a Max-SAT assignment; D = P for a satisfiable instance).
+ * after every round k (0-based), round-major (the angle points of one round
+ * and readout contiguous),
+ *   out[((b * p + k) * 3 + 0) * angles + a] = P(C=0),
+ *   out[((b * p + k) * 3 + 1) * angles + a] = <H_P> (Eq. 4),
+ *   out[((b * p + k) * 3 + 2) * angles + a] = D, the probability of the
+ *        lowest non-empty cost class (a Max-SAT assignment; D = P for a
+ *        satisfiable instance).
  * hist   device uint64 [batch][hist_stride] (8-byte aligned): h[b][c], the
  *        number of assignments with cost c; each row sums to 2^n.
  *        hist_stride in 1..256 (m + 1 for m clauses).
  * gammas, betas  device double [angles].
- * out    device double [batch][angles][p][3], written.
+ * out    device double [batch][p][3][angles], written.
  * best   optional device int32 [batch][p]: the angle point with the smallest
- *        <H_P> after round k (the smallest index among equal values);
- *        batch * p must stay below 2^31. NULL skips it.
- * ws     device workspace of gqaoa_reduced_sweep_workspace_size(angles)
- *        bytes (16-byte aligned, caller-owned): the phase tables.
+ *        written <H_P> after round k (the smallest index among equal values;
+ *        -1 where every value is NaN). NULL skips it.
+ * ws     device workspace of gqaoa_reduced_sweep_workspace_size(hist_stride,
+ *        batch, angles, p) bytes (16-byte aligned, caller-owned): the phase
+ *        tables (hist_stride rounded up to 32 entries per angle point), the
+ *        FP32 class weights and the per-warp minima behind `best`.
+ * The kernel's work grows with hist_stride (8 to 16 classes per lane, 1 to 16
+ * lanes per item): a caller that knows its last non-empty class can pass the
+ * histogram cut after it (classes past the stride are empty).
  * Precision: complex64 class amplitudes and phases rounded to complex64 (as
- * the statevector path); the class sums are FP32 per lane and double-float
- * across the 1..16 lanes that hold one item's classes.
+ * the statevector path); the class sums are FP32. Every written value is a
+ * float widened exactly to double.
  * Errors: GQAOA_ERANGE for n outside 1..GQAOA_MAX_N, hist_stride outside
- * 1..256, batch < 1, angles outside 1..2^24, p outside 1..2^20;
- * GQAOA_EINVAL for NULL or misaligned pointers; GQAOA_ENOMEM for a short
- * workspace.
+ * 1..256, batch < 1, angles outside 1..2^24, p outside 1..2^20, batch * angles
+ * above 2^40 or batch * p of 2^31 or more; GQAOA_EINVAL for NULL or
+ * misaligned pointers; GQAOA_ENOMEM for a short workspace. All are checked
+ * before any launch; the workspace query checks the same shape limits.
  */
-int gqaoa_reduced_sweep_workspace_size(int angles, size_t *bytes);
+int gqaoa_reduced_sweep_workspace_size(int hist_stride, int batch, int angles, int p,
+                                       size_t *bytes);
 int gqaoa_reduced_sweep(const uint64_t *hist, int hist_stride, int n, int batch,
                         const double *gammas, const double *betas, int angles, int p,
                         double *out, int32_t *best, void *ws, size_t ws_bytes, void *stream);

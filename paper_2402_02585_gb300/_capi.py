@@ -83,7 +83,7 @@ SIGNATURES = {
     "gqaoa_batched_geometry": [_I, _I, _I, _P, _P],
     "gqaoa_evolve_noalloc": [_P, _I, _I, _P, _P, _I, _P, _P, _P, _U, _P],
     "gqaoa_sweep_workspace_size": [_I, _I, _I, _SZP],
-    "gqaoa_reduced_sweep_workspace_size": [_I, _SZP],
+    "gqaoa_reduced_sweep_workspace_size": [_I, _I, _I, _I, _SZP],
     "gqaoa_fairness_workspace_size": [_I, _I64, _I, _SZP],
     "gqaoa_fairness": [_P, _I64, _I64, _P, _I, _I, _I, _D, _I64, _P, _P, _P, _SZ, _P],
     "gqaoa_reduced_sweep": [_P, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P, _SZ, _P],
@@ -223,8 +223,8 @@ def gqaoa_sweep(cost, n, m, batch, gammas, betas, angles, p, rounds, nrounds, am
           amps_per_thread, out, ws, ws_bytes, stream)
 
 
-def gqaoa_reduced_sweep_workspace_size(angles) -> int:
-    return _size("gqaoa_reduced_sweep_workspace_size", angles)
+def gqaoa_reduced_sweep_workspace_size(hist_stride, batch, angles, p) -> int:
+    return _size("gqaoa_reduced_sweep_workspace_size", hist_stride, batch, angles, p)
 
 
 def gqaoa_reduced_sweep(hist, hist_stride, n, batch, gammas, betas, angles, p, out, best, ws,

@@ -213,10 +213,12 @@ def grad_batched(cost: torch.Tensor, n: int, m: int, gammas, betas, objective: s
 
 def reduced_sweep(hist: torch.Tensor, n: int, gammas, betas, p: int, best: bool = True,
                   ws: torch.Tensor | None = None):
-    """Cost-class model (Appendix C) over angle points: hist [B, m + 1] (int64,
-    each row summing to 2^n), gammas/betas [A] single angle pairs. Returns
-    out [B, A, p, 3] (P, <H_P>, Max-SAT weight D after every round) and, with
-    best=True, best [B, p] (the angle point of smallest <H_P> per round)."""
+    """Cost-class model (Appendix C) over angle points: hist [B, stride] (int64,
+    each row summing to 2^n; stride m + 1, or less when the classes past it
+    are empty), gammas/betas [A] single angle pairs. Returns out [B, A, p, 3]
+    (P, <H_P>, Max-SAT weight D after every round; a view of the library's
+    round-major [B, p, 3, A] buffer) and, with best=True, best [B, p] (the
+    angle point of smallest <H_P> per round)."""
     _require_cuda(hist)
     device = hist.device
     hist = hist.reshape(-1, hist.shape[-1]).contiguous()
@@ -224,14 +226,14 @@ def reduced_sweep(hist: torch.Tensor, n: int, gammas, betas, p: int, best: bool 
     g = _angles(gammas, device).reshape(-1)
     b = _angles(betas, device).reshape(-1)
     A = g.numel()
-    out = torch.empty((B, A, p, 3), dtype=torch.float64, device=device)
+    out = torch.empty((B, p, 3, A), dtype=torch.float64, device=device)  # round-major
     bst = torch.empty((B, p), dtype=torch.int32, device=device) if best else None
-    need = C.gqaoa_reduced_sweep_workspace_size(A)
+    need = C.gqaoa_reduced_sweep_workspace_size(stride, B, A, p)
     if ws is None or ws.numel() < need:
         ws = workspace(need, device)
     C.gqaoa_reduced_sweep(_ptr(hist), stride, n, B, _ptr(g), _ptr(b), A, p, _ptr(out), _ptr(bst),
                           _ptr(ws), ws.numel(), _stream())
-    return out, bst
+    return out.permute(0, 3, 1, 2), bst
 
 
 def fairness(shots: torch.Tensor, runs: int, cost: torch.Tensor, n: int, target: int,

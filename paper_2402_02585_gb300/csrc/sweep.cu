@@ -28,8 +28,8 @@
 
 namespace gq {
 
-int phase_tables(const double *gammas, const double *betas, int64_t count, float2 *phase,
-                 double2 *alpha, cudaStream_t st);
+int phase_tables(const double *gammas, const double *betas, int64_t count, int entries,
+                 float2 *phase, double2 *alpha, cudaStream_t st);
 int sm_count();
 
 constexpr int kSweepMaxRounds = 16;
@@ -699,7 +699,7 @@ extern "C" int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const d
   double2 *alpha = nullptr;
   float4 *scratch = nullptr;
   sweep_ws_layout(n, angles, resident, static_cast<char *>(ws), &phase, &alpha, &scratch);
-  rc = phase_tables(gammas, betas, angles, phase, alpha, st);
+  rc = phase_tables(gammas, betas, angles, 256, phase, alpha, st);
   if (rc) return rc;
   args.cost = cost;
   args.phase = phase;

@@ -320,7 +320,11 @@ class Protocol:
         self.launches = 0
         self._small = (1 << n) < 4096  # one CTA per state: phase tables + one or two kernels
         h = hist.cpu().numpy()
-        self.min_class = int(np.nonzero(h)[0][0])  # 0 when satisfiable
+        nz = np.nonzero(h)[0]
+        self.min_class = int(nz[0])  # 0 when satisfiable
+        # the grid search's histogram ends at the last non-empty class: the
+        # cost-class kernel's work grows with the row length
+        self.grid_hist = hist[:int(nz[-1]) + 1].reshape(1, -1).contiguous()
 
     def _evolve_workspace(self, p: int) -> torch.Tensor:
         if p not in self._ws:
@@ -455,8 +459,8 @@ class Protocol:
         self.launches = 0
         G, B = grid if grid is not None else grid_for(self.n, seed)
         with _GATE.work():
-            out, best = core.reduced_sweep(self.hist[None], self.n, G, B, p_max)
-            self.launches += 3  # phase tables, the cost-class evolution, the argmin
+            out, best = core.reduced_sweep(self.grid_hist, self.n, G, B, p_max)
+            self.launches += 4  # phase tables, minima reset, the cost-class evolution, argmin
             bi = best[0].long()
             seed_vals = out[0, bi, torch.arange(p_max, device=out.device)].cpu().numpy()
             bi = bi.cpu().numpy()

@@ -184,8 +184,24 @@ def test_reduced_sweep_rejects_bad_arguments_before_launch():
     with pytest.raises(C.GQAOAError) as e:  # misaligned output
         C.gqaoa_reduced_sweep(fake, 43, 10, 1, fake, fake, 4, 4, fake + 4, None, fake, 1 << 20, None)
     assert e.value.status == C.GQAOA_EINVAL
-    need = C.gqaoa_reduced_sweep_workspace_size(4)
-    assert need == 8192 + 256
+    # phase tables of 64 entries (stride 43 rounded up to 32), alpha, the
+    # minima of 1 x 4 rounds, the per-warp minima (4 lanes per item: 8 items
+    # per warp, one block), two FP32 weight rows of 64 entries and the lowest
+    # class per instance, each region 256-byte aligned
+    need = C.gqaoa_reduced_sweep_workspace_size(43, 1, 4, 4)
+    assert need == 4 * 64 * 8 + 6 * 256
+    # 16 lanes per item: 2 items per warp, 15 blocks of 30 items x 7 rounds
+    assert (C.gqaoa_reduced_sweep_workspace_size(256, 3, 10, 7)
+            == 10 * 256 * 8 + 256 + 256 + 1024 + 2 * 3 * 256 * 4 + 256)
+    for bad in ((0, 1, 4, 4), (257, 1, 4, 4), (43, 0, 4, 4), (43, 1, 0, 4), (43, 1, 4, 0),
+                (43, 1 << 12, 4, 1 << 19)):  # batch * p = 2^31
+        with pytest.raises(C.GQAOAError) as e:
+            C.gqaoa_reduced_sweep_workspace_size(*bad)
+        assert e.value.status == C.GQAOA_ERANGE
+    with pytest.raises(C.GQAOAError) as e:  # batch * p = 2^31, refused before any launch
+        C.gqaoa_reduced_sweep(fake, 43, 10, 1 << 12, fake, fake, 4, 1 << 19, fake, None, fake,
+                              1 << 40, None)
+    assert e.value.status == C.GQAOA_ERANGE
     with pytest.raises(C.GQAOAError) as e:
         C.gqaoa_reduced_sweep(fake, 43, 10, 1, fake, fake, 4, 4, fake, None, fake, need - 1, None)
     assert e.value.status == C.GQAOA_ENOMEM

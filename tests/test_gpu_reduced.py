@@ -40,8 +40,10 @@ def _hist_rows(shapes, seed0):
 
 
 @pytest.mark.parametrize("n,ms,A,p", [
-    (8, [5], 6, 10),             # 6 classes: one lane per item, 6 of a warp's 32 items
-    (9, [12], 5, 10),            # 13 classes: one lane per item
+    (8, [5], 6, 10),             # 6 classes: one lane per item, 8 slots, 6 of a warp's 32 items
+    (9, [10], 40, 12),           # 11 classes: one lane per item, 12 slots, one instance per warp
+    (9, [12], 5, 10),            # 13 classes: one lane per item, 16 slots
+    (8, [20], 37, 12),           # 21 classes: lane pairs, 12 slots each
     (7, [20, 30], 5, 12),        # 31 classes: lane pairs
     (6, [10, 40], 7, 12),        # 11 / 41 classes: groups of 4 lanes, partly filled
     (10, [42, 60, 90], 5, 20),   # density 9: unsatisfiable, D != P
@@ -50,6 +52,7 @@ def _hist_rows(shapes, seed0):
     (24, [101], 3, 8),
     (12, [180], 3, 10),          # 181 classes: groups of 16 lanes, 12 classes each
     (11, [230], 2, 6),           # 231 classes: groups of 16 lanes, 16 classes each
+    (13, [55, 56], 70, 24),      # groups of 4 lanes, warps of one instance and mixed ones
 ])
 def test_reduced_sweep_matches_oracle(n, ms, A, p):
     H = _hist_rows([(n, m) for m in ms], 3000 + n)
@@ -68,10 +71,34 @@ def test_reduced_sweep_matches_oracle(n, ms, A, p):
             assert np.max(np.abs(got[:, 2] - ref[:, 2])) < 1e-6, (b, a)
             assert np.max(np.abs(got[:, 1] - ref[:, 1])) < 1e-6 * ms[b], (b, a)
         assert abs(out[b, 0, -1, 1] - ms[b] / 8) < 1e-6 * ms[b]
+    # every written value is a float widened exactly
+    assert np.array_equal(out.astype(np.float32).astype(np.float64), out)
     bst = best.cpu().numpy()
     for b in range(H.shape[0]):
         for k in range(p):
             assert bst[b, k] == int(np.argmin(out[b, :, k, 1]))
+
+
+def test_reduced_sweep_cut_histogram():
+    # a row cut after its last non-empty class (a shorter stride, so smaller
+    # lane groups) gives the same readouts and argmin within the tolerance
+    n, m, p = 14, 60, 32
+    _, hist = core.build_cost(instances.random_3sat(n, m, 4300), n)
+    h = hist.cpu().numpy()
+    nz = np.nonzero(h)[0]
+    rng = np.random.default_rng(5)
+    G = rng.uniform(0, np.pi, 300)
+    Bt = rng.uniform(0, 2 * np.pi, 300)
+    full, bf = core.reduced_sweep(hist[None], n, G, Bt, p)
+    cut, bc = core.reduced_sweep(hist[:nz[-1] + 1][None], n, G, Bt, p)
+    assert nz[-1] + 1 <= 24 < m + 1  # lane pairs instead of groups of 4
+    assert torch.max(torch.abs(full - cut)).item() < 1e-6 * m
+    ref = np.stack([reduced.readouts_trace(h, [G[a]] * p, [Bt[a]] * p) for a in range(0, 300, 37)])
+    got = cut[0, ::37].cpu().numpy()
+    assert np.max(np.abs(got[..., 0] - ref[..., 0])) < 1e-6
+    assert np.max(np.abs(got[..., 1] - ref[..., 1])) < 1e-6 * m
+    e = cut[0, :, :, 1].cpu().numpy()
+    assert np.array_equal(bc[0].cpu().numpy(), np.argmin(e, axis=0))
 
 
 def test_reduced_sweep_agrees_with_statevector_sweep():
@@ -106,8 +133,13 @@ def test_reduced_sweep_edge_cases():
     out, best = core.reduced_sweep(torch.as_tensor(H, device="cuda"), 9, [0.5] * 4, [1.5] * 4, 6)
     assert torch.equal(out[0, 0], out[0, 3])
     assert int(best.min()) == 0 and int(best.max()) == 0
+    # NaN angles: NaN readouts, and no argmin (-1)
+    H1 = _hist_rows([(9, 30)], 4250)
+    out, best = core.reduced_sweep(torch.as_tensor(H1, device="cuda"), 9, [float("nan")] * 3,
+                                   [0.5] * 3, 4)
+    assert torch.isnan(out[..., 1]).all() and int(best.max()) == -1 and int(best.min()) == -1
     # a workspace one byte short is refused before any launch
-    need = C.gqaoa_reduced_sweep_workspace_size(4)
+    need = C.gqaoa_reduced_sweep_workspace_size(H.shape[1], 1, 4, 6)
     ws = core.workspace(need)
     g = torch.zeros(4, dtype=torch.float64, device="cuda")
     hist = torch.as_tensor(H, device="cuda")
