@@ -88,6 +88,11 @@ WORKLOADS = {
     # Section IV's fair-sampling metrics on a satisfiable instance at the
     # protocol's fewest-rounds angles: one step = sample runs x shots_per_run
     # shots and compute both metrics for every run
+    "grid": dict(kind="grid", n=16, m=67, p=64, seed=0,
+                 desc="cost-class model (Appendix C) of the first satisfiable random 3-SAT "
+                      "instance n=16 m=67 (d~4.2) from seed 0, histogram cut after its last "
+                      "non-empty class: the pi/180 grid (65160 single angle pairs) x p = 64 "
+                      "rounds, P/<H_P>/D after every round and the per-round argmin of <H_P>"),
     "fairness": dict(kind="fairness", n=14, d_lo=3.8, d_hi=4.2, runs=100_000, shots_per_run=2048,
                      alpha=0.05, seed=3,
                      desc="one satisfiable random 3-SAT instance n=14, d in (3.8, 4.2), at the "
@@ -741,6 +746,166 @@ def run_sweep(args, wl):
     return 0
 
 
+def grid_instance(wl):
+    """The grid workload's instance: the first satisfiable seed from
+    wl["seed"] on, its histogram by the oracle's cost table (host, int64)."""
+    from oracle import statevector as sv
+    from paper_2402_02585_gb300 import instances
+    seed = wl["seed"]
+    while True:
+        lits = instances.random_3sat(wl["n"], wl["m"], seed)
+        _, hist = sv.cost_table(lits, wl["n"])
+        if hist[0] > 0:
+            return seed, lits, np.asarray(hist, dtype=np.int64)
+        seed += 1
+
+
+def cpu_grid_baseline(wl, hist, G, B, points: int = 20000):
+    """The oracle's cost-class model (numpy FP64, one core) on a bounded
+    sample of the grid: `points` angle pairs spread over it, all p rounds
+    (20000 points, about 10 s)."""
+    from oracle import reduced
+    idx = np.linspace(0, len(G) - 1, points).astype(np.int64)
+    t0 = time.perf_counter()
+    for a in idx:
+        reduced.readouts_trace(hist, [G[a]] * wl["p"], [B[a]] * wl["p"])
+    t = time.perf_counter() - t0
+    return {"value": points * wl["p"] / t, "unit": "item-rounds/s", "cores": 1, "kind": "oracle",
+            "sample": f"{points} of the {len(G)} grid angle pairs (evenly spaced), p = {wl['p']} "
+                      f"rounds each, oracle.reduced.readouts_trace ({t:.1f} s)"}
+
+
+def run_grid(args, wl):
+    """Workload "grid": gqaoa_reduced_sweep of one instance over the protocol's
+    pi/180 grid, the protocol's grid call. Metric: item-rounds per second
+    (angle pairs x rounds). Each timed call follows an L2 flush (the call's
+    buffers, 117 MB at this size, would otherwise stay in L2); the e2e figure
+    goes through core.reduced_sweep from host inputs (histogram and angles
+    copied in, the per-round argmin copied out)."""
+    import torch
+
+    from paper_2402_02585_gb300 import _capi as C
+    from paper_2402_02585_gb300 import core, instances
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seed, lits, hist = grid_instance(wl)
+    nz = np.nonzero(hist)[0]
+    cut = hist[:nz[-1] + 1]
+    classes = int(nz[-1] - nz[0] + 1)
+    n, p = wl["n"], wl["p"]
+    G, B = instances.protocol_grid()
+    A = len(G)
+    hd = torch.as_tensor(cut, device=dev).reshape(1, -1)
+    Gd = torch.as_tensor(G, dtype=torch.float64, device=dev)
+    Bd = torch.as_tensor(B, dtype=torch.float64, device=dev)
+    out = torch.empty((1, p, 3, A), dtype=torch.float32, device=dev)
+    best = torch.empty((1, p), dtype=torch.int32, device=dev)
+    ws = core.workspace(C.gqaoa_reduced_sweep_workspace_size(hd.shape[1], 1, A, p), dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev).cuda_stream
+
+    def call():
+        C.gqaoa_reduced_sweep(hd.data_ptr(), hd.shape[1], n, 1, Gd.data_ptr(), Bd.data_ptr(), A, p,
+                              out.data_ptr(), best.data_ptr(), ws.data_ptr(), ws.numel(), st)
+
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    for e0, e1 in ev:
+        flush.fill_(1)
+        e0.record()
+        call()
+        e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    el = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3
+    # end to end through the Python API: host histogram and angles in, the
+    # per-round argmin out
+    hh = torch.as_tensor(cut).reshape(1, -1).pin_memory()
+    Gh = torch.as_tensor(G, dtype=torch.float64).pin_memory()
+    Bh = torch.as_tensor(B, dtype=torch.float64).pin_memory()
+    bh = torch.empty((1, p), dtype=torch.int32).pin_memory()
+    for _ in range(args.warmup):
+        core.reduced_sweep(hh.to(dev, non_blocking=True), n, Gh.to(dev, non_blocking=True),
+                           Bh.to(dev, non_blocking=True), p, ws=ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, bd = core.reduced_sweep(hh.to(dev, non_blocking=True), n, Gh.to(dev, non_blocking=True),
+                                   Bh.to(dev, non_blocking=True), p, ws=ws)
+        bh.copy_(bd)
+    torch.cuda.synchronize()
+    e2e = time.perf_counter() - t0
+    units = A * p
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    # 11 FP32 instructions per class and round (complex phase multiply 4, the
+    # S sum 2, mixer add 2, the <H_P> term 3) over the classes from the lowest
+    # to the highest non-empty one, at 4 warp-instructions (128 lanes) per
+    # clock per SM
+    alu_peak = 4 * sms * 2.07e9 / (11 * classes / 32)
+    rate = units * args.steps / el
+    line = {"metric": "cost-class item-rounds/s", "value": rate, "unit": "item-rounds/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64 (class amplitudes), f32 sums and readouts",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": n, "m": wl["m"], "instance_seed": seed,
+                       "angle_pairs": A, "p": p, "classes": classes,
+                       "histogram_stride": int(hd.shape[1]),
+                       "l2": "flushed (256 MiB write) before every timed call"},
+            "roofline": {"bound": "alu", "achieved": rate, "peak": alu_peak,
+                         "unit": "item-rounds/s", "frac": rate / alu_peak, "traffic": None,
+                         "kernel": "the whole call (phase tables, weights, reduced_sweep_kernel, "
+                                   "argmin reduce); the kernel's own share is in the profile",
+                         "peak_derivation": "4 warp-instr/clk/SM x SMs x 2.07 GHz / (11 FP32 "
+                                            f"instructions x {classes} classes / 32 lanes) per "
+                                            "item-round"},
+            "e2e": {"value": units * args.steps / e2e, "unit": "item-rounds/s",
+                    "h2d_bytes_per_step": int(cut.nbytes + 16 * A),
+                    "d2h_bytes_per_step": int(4 * p)},
+            "cpu_baseline": (cpu_grid_baseline(wl, cut, G, B)
+                             if os.environ.get("GQAOA_BENCH_NO_CPU") != "1" else None),
+            "gpu_launches": 4 * args.steps, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_grid_reference(args, wl):
+    """The grid workload's oracle arm: the FP64 cost-class model on a bounded
+    sample of the grid per step, on the host."""
+    from paper_2402_02585_gb300 import instances
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    seed, _, hist = grid_instance(wl)
+    cut = hist[:np.nonzero(hist)[0][-1] + 1]
+    G, B = instances.protocol_grid()
+    per = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_grid_baseline(wl, cut, G, B, points=2000)
+        if i >= args.warmup:
+            per.append(r["value"])
+    value = float(np.mean(per))
+    print(json.dumps({
+        "impl": "reference", "metric": "cost-class item-rounds/s", "value": value,
+        "unit": "item-rounds/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 2000 * wl["p"] / value * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "instance_seed": seed, "p": wl["p"]},
+        "cpu_baseline": {"value": value, "unit": "item-rounds/s", "cores": 1, "kind": "oracle",
+                         "sample": r["sample"]},
+        "e2e": {"value": value, "unit": "item-rounds/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+    return 0
+
+
 def run_protocol(args, wl):
     """Workloads "protocol" and "protocol_maxsat": the paper's angle protocol
     for every instance (target P, or D for unsatisfiable instances). Metric:
@@ -786,7 +951,7 @@ def run_protocol(args, wl):
     h0d = prot0.grid_hist
     Gd = torch.as_tensor(G, dtype=torch.float64, device=dev)
     Bd = torch.as_tensor(B, dtype=torch.float64, device=dev)
-    grid_out = torch.empty((1, len(G), wl["p_max"], 3), dtype=torch.float64, device=dev)
+    grid_out = torch.empty((1, wl["p_max"], 3, len(G)), dtype=torch.float32, device=dev)
     grid_best = torch.empty((1, wl["p_max"]), dtype=torch.int32, device=dev)
     grid_ws = core.workspace(
         C.gqaoa_reduced_sweep_workspace_size(h0d.shape[1], 1, len(G), wl["p_max"]), dev)
@@ -1134,11 +1299,16 @@ def main():
     args = parse()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
-        if wl.get("kind") in ("grad", "sweep", "study"):
+        if wl.get("kind") == "grid":
+            return run_grid_reference(args, wl)
+        if wl.get("kind") is not None:
             print(json.dumps({"impl": "reference", "unavailable": "this workload has no "
-                              "bounded oracle arm; run the default workload"}))
+                              "bounded oracle arm of its own (its GPU line carries the oracle's "
+                              "rate as cpu_baseline); run the default workload"}))
             return 0
         return run_reference(args, wl)
+    if wl.get("kind") == "grid":
+        return run_grid(args, wl)
     if wl.get("kind") == "grad":
         return run_grad(args, wl)
     if wl.get("kind") == "protocol":

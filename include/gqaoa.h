@@ -332,7 +332,7 @@ int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const double *gamm
  *        number of assignments with cost c; each row sums to 2^n.
  *        hist_stride in 1..256 (m + 1 for m clauses).
  * gammas, betas  device double [angles].
- * out    device double [batch][p][3][angles], written.
+ * out    device float [batch][p][3][angles] (4-byte aligned), written.
  * best   optional device int32 [batch][p]: the angle point with the smallest
  *        written <H_P> after round k (the smallest index among equal values;
  *        -1 where every value is NaN). NULL skips it.
@@ -344,8 +344,7 @@ int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const double *gamm
  * lanes per item): a caller that knows its last non-empty class can pass the
  * histogram cut after it (classes past the stride are empty).
  * Precision: complex64 class amplitudes and phases rounded to complex64 (as
- * the statevector path); the class sums are FP32. Every written value is a
- * float widened exactly to double.
+ * the statevector path); the class sums and the readouts are FP32.
  * Errors: GQAOA_ERANGE for n outside 1..GQAOA_MAX_N, hist_stride outside
  * 1..256, batch < 1, angles outside 1..2^24, p outside 1..2^20, batch * angles
  * above 2^40 or batch * p of 2^31 or more; GQAOA_EINVAL for NULL or
@@ -356,7 +355,7 @@ int gqaoa_reduced_sweep_workspace_size(int hist_stride, int batch, int angles, i
                                        size_t *bytes);
 int gqaoa_reduced_sweep(const uint64_t *hist, int hist_stride, int n, int batch,
                         const double *gammas, const double *betas, int angles, int p,
-                        double *out, int32_t *best, void *ws, size_t ws_bytes, void *stream);
+                        float *out, int32_t *best, void *ws, size_t ws_bytes, void *stream);
 
 /*
  * Fair-sampling metrics of Section IV (Table I): how evenly the shots of

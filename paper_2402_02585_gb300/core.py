@@ -216,9 +216,9 @@ def reduced_sweep(hist: torch.Tensor, n: int, gammas, betas, p: int, best: bool 
     """Cost-class model (Appendix C) over angle points: hist [B, stride] (int64,
     each row summing to 2^n; stride m + 1, or less when the classes past it
     are empty), gammas/betas [A] single angle pairs. Returns out [B, A, p, 3]
-    (P, <H_P>, Max-SAT weight D after every round; a view of the library's
-    round-major [B, p, 3, A] buffer) and, with best=True, best [B, p] (the
-    angle point of smallest <H_P> per round)."""
+    (P, <H_P>, Max-SAT weight D after every round, FP32; a view of the
+    library's round-major [B, p, 3, A] buffer) and, with best=True,
+    best [B, p] (the angle point of smallest <H_P> per round)."""
     _require_cuda(hist)
     device = hist.device
     hist = hist.reshape(-1, hist.shape[-1]).contiguous()
@@ -226,7 +226,7 @@ def reduced_sweep(hist: torch.Tensor, n: int, gammas, betas, p: int, best: bool 
     g = _angles(gammas, device).reshape(-1)
     b = _angles(betas, device).reshape(-1)
     A = g.numel()
-    out = torch.empty((B, p, 3, A), dtype=torch.float64, device=device)  # round-major
+    out = torch.empty((B, p, 3, A), dtype=torch.float32, device=device)  # round-major
     bst = torch.empty((B, p), dtype=torch.int32, device=device) if best else None
     need = C.gqaoa_reduced_sweep_workspace_size(stride, B, A, p)
     if ws is None or ws.numel() < need:

@@ -40,7 +40,7 @@ struct ReducedArgs {
   const int32_t *cmin;         // [B]: lowest non-empty class
   const float2 *phase;         // [A][tstride]
   const double2 *alpha;        // [A]
-  double *out;                 // [B][p][3][A]
+  float *out;                  // [B][p][3][A]
   unsigned long long *keys;    // [B][p] minima of warps spanning instances, or null
   unsigned long long *part;    // [p][nblocks] minima of the other warps
   uint64_t nitems;             // B * A
@@ -93,22 +93,6 @@ __device__ __forceinline__ float group_fsum(float v) {
   return v;
 }
 
-// The double of a float from its bit fields (IEEE 754 binary32 -> binary64:
-// the exponent rebiased by 1023 - 127 = 896, the fraction moved up 29 bits),
-// in integer instructions and without branches; the FP64 units of this GPU
-// are slow. Exact for every float: a subnormal is first scaled by 2^64 in
-// FP32 (exact, and normal) and the double's exponent lowered by 64.
-__device__ __forceinline__ double f32_to_f64(float f) {
-  const uint32_t b = __float_as_uint(f);
-  uint32_t mag = b & 0x7fffffffu;
-  const bool sub = mag - 1u < 0x007fffffu;  // 0 < mag < 2^23
-  if (sub) mag = __float_as_uint(__fmul_rn(__uint_as_float(mag), 0x1p64f));
-  uint32_t hi = (mag >> 3) + (sub ? 0x38000000u - (64u << 20) : 0x38000000u);
-  if (mag >= 0x7f800000u) hi = 0x7ff00000u | (mag >> 3);  // inf, NaN (fraction kept)
-  if (mag == 0u) hi = 0u;
-  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(mag << 29));
-}
-
 // Order-preserving image of a float's bits (negative values below positive
 // ones, -0 equal to +0, NaN above everything), so the unsigned minimum is the
 // smallest value.
@@ -142,9 +126,9 @@ __device__ __forceinline__ bool block_instance(uint64_t wb, int ipw, uint64_t ni
 // holds the classes c = c_min + l + kG j, j < kJ, so kG kJ >= hist_stride
 // covers every non-empty class. A round costs per slot a complex multiply and
 // the S sum (6 FP32 instructions), the mixer add and the <H_P> term (5), plus
-// log2(kG) butterfly steps for each of the three group sums. The readouts are
-// stored round-major ([B][p][3][A]), so a warp's stores of one round cover
-// contiguous angle points; the per-round minimum of a warp whose items lie in
+// log2(kG) butterfly steps for each of the three group sums. The readouts
+// (FP32, as computed) are stored round-major ([B][p][3][A]), so a warp's
+// stores of one round cover contiguous angle points; the per-round minimum of a warp whose items lie in
 // one instance goes to its own slot of `part` (no atomics), that of a warp
 // spanning instances to `keys` by atomic minimum.
 template <int kG, int kJ>
@@ -177,7 +161,7 @@ __global__ void __launch_bounds__(kRedThreads, 8) reduced_sweep_kernel(const __g
     const double2 al = a.alpha[ai];
     const float alr = (float)al.x, ali = (float)al.y;
     // round k's readout f of this item at o[(3 k + f) A]
-    double *o = a.out + b * (uint64_t)a.p * 3 * (uint64_t)a.A + (uint64_t)ai;
+    float *o = a.out + b * (uint64_t)a.p * 3 * (uint64_t)a.A + (uint64_t)ai;
     const uint64_t stride_f = (uint64_t)a.A;
     const uint64_t wb = base / kPerWarp;
     uint64_t b_block;
@@ -210,12 +194,11 @@ __global__ void __launch_bounds__(kRedThreads, 8) reduced_sweep_kernel(const __g
       // else class 0 is empty and P = 0
       const float d = w[0] * fmaf(u[0].x, u[0].x, u[0].y * u[0].y);
       if (gl == 0 && valid) {
-        const double dd = f32_to_f64(d);
-        double *ok = o + 3 * (uint64_t)k * stride_f;
-        ok[0] = cs == 0 ? dd : 0.0;
-        ok[stride_f] = f32_to_f64(e);
-        ok[2 * stride_f] = dd;
+        o[0] = cs == 0 ? d : 0.f;
+        o[stride_f] = e;
+        o[2 * stride_f] = d;
       }
+      o += 3 * stride_f;
       if (key) {
         const uint32_t kv = valid ? order_key(e) : 0xffffffffu;
         if (pure) {
@@ -235,15 +218,17 @@ __global__ void __launch_bounds__(kRedThreads, 8) reduced_sweep_kernel(const __g
 
 // best[b][k] = the angle point of the minimum over the warps of instance b
 // (their `part` slots) and the atomics of the warps spanning instances
-// (`keys`); -1 where every value was NaN. One warp per (b, k).
-__global__ void reduced_best_kernel(const unsigned long long *__restrict__ keys,
-                                    const unsigned long long *__restrict__ part, uint64_t nblocks,
-                                    int ipw, uint64_t nitems, int A, int B, int p,
-                                    int32_t *__restrict__ best) {
-  const int lane = threadIdx.x & 31;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-       i < (uint64_t)B * (uint64_t)p; i += nw) {
+// (`keys`); -1 where every value was NaN. One CTA per (b, k), its threads
+// reading that round's row of `part` side by side.
+constexpr int kBestThreads = 256;
+
+__global__ void __launch_bounds__(kBestThreads)
+reduced_best_kernel(const unsigned long long *__restrict__ keys,
+                    const unsigned long long *__restrict__ part, uint64_t nblocks, int ipw,
+                    uint64_t nitems, int A, int B, int p, int32_t *__restrict__ best) {
+  __shared__ unsigned long long s_min[kBestThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint64_t i = blockIdx.x; i < (uint64_t)B * (uint64_t)p; i += gridDim.x) {
     const uint64_t b = i / (uint64_t)p, k = i % (uint64_t)p;
     // the blocks that lie in instance b (block_instance's test): first item
     // at or after b A, last item (cut at nitems) before (b + 1) A
@@ -253,7 +238,8 @@ __global__ void reduced_best_kernel(const unsigned long long *__restrict__ keys,
                             : (b + 1) * (uint64_t)A / (uint64_t)ipw;
     unsigned long long m = ~0ull;
     const unsigned long long *row = part + k * nblocks;
-    for (uint64_t wb = lo + lane; wb < hi; wb += 32) {
+#pragma unroll 4
+    for (uint64_t wb = lo + threadIdx.x; wb < hi; wb += kBestThreads) {
       const unsigned long long v = row[wb];
       m = v < m ? v : m;
     }
@@ -262,11 +248,15 @@ __global__ void reduced_best_kernel(const unsigned long long *__restrict__ keys,
       const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
       m = v < m ? v : m;
     }
-    if (lane == 0) {
+    if (lane == 0) s_min[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 0; w < kBestThreads / 32; ++w) m = s_min[w] < m ? s_min[w] : m;
       const unsigned long long v = keys[i];
       m = v < m ? v : m;
       best[i] = (uint32_t)(m >> 32) == 0xffffffffu ? -1 : (int32_t)(uint32_t)m;
     }
+    __syncthreads();  // s_min is rewritten for the next (b, k)
   }
 }
 
@@ -358,15 +348,16 @@ extern "C" int gqaoa_reduced_sweep_workspace_size(int hist_stride, int batch, in
 
 extern "C" int gqaoa_reduced_sweep(const uint64_t *hist, int hist_stride, int n, int batch,
                                    const double *gammas, const double *betas, int angles, int p,
-                                   double *out, int32_t *best, void *ws, size_t ws_bytes,
+                                   float *out, int32_t *best, void *ws, size_t ws_bytes,
                                    void *stream) {
   gq::NvtxRange nvtx_range("gqaoa_reduced_sweep");
   if (n < 1 || n > GQAOA_MAX_N) return GQAOA_ERANGE;
   int rc = check_shape(hist_stride, batch, angles, p);
   if (rc) return rc;
   if (!hist || !gammas || !betas || !out || !ws) return GQAOA_EINVAL;
-  if (!aligned8(hist) || !aligned8(gammas) || !aligned8(betas) || !aligned8(out) ||
-      !aligned16(ws) || (best && (reinterpret_cast<uintptr_t>(best) & 3u) != 0))
+  if (!aligned8(hist) || !aligned8(gammas) || !aligned8(betas) ||
+      (reinterpret_cast<uintptr_t>(out) & 3u) != 0 || !aligned16(ws) ||
+      (best && (reinterpret_cast<uintptr_t>(best) & 3u) != 0))
     return GQAOA_EINVAL;
   if (ws_bytes < reduced_ws_layout(hist_stride, batch, angles, p, nullptr, nullptr))
     return GQAOA_ENOMEM;
@@ -410,8 +401,8 @@ extern "C" int gqaoa_reduced_sweep(const uint64_t *hist, int hist_stride, int n,
   else if (hist_stride <= 192) rc = launch_reduced<16, 12>(args, st);
   else rc = launch_reduced<16, 16>(args, st);
   if (rc || !best) return rc;
-  const unsigned best_grid = (unsigned)(nkeys < 8ull * 1024 ? (nkeys + 7) / 8 : 1024);
-  reduced_best_kernel<<<best_grid, 256, 0, st>>>(w.keys, w.part, args.nblocks,
+  const unsigned best_grid = (unsigned)(nkeys < 4096ull ? nkeys : 4096ull);
+  reduced_best_kernel<<<best_grid, kBestThreads, 0, st>>>(w.keys, w.part, args.nblocks,
                                                  32 / group_lanes(hist_stride), args.nitems,
                                                  angles, batch, p, best);
   GQ_CHECK_LAUNCH();

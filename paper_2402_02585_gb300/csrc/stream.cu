@@ -230,62 +230,66 @@ __device__ __forceinline__ DFc dfc_mul(const DFc &a, const DFc &b) {
 }
 __device__ __forceinline__ DFc dfc_load(float4 v) { return DFc{{v.x, v.y}, {v.z, v.w}}; }
 
-constexpr int kPhaseWarps = 2;  // warps per CTA; each warp owns 32 tables at a time
+constexpr int kPhaseWarps = 8;  // warps per CTA; the CTA owns 32 tables at a time
 
-// Each warp works alone: lane l takes table t0 + l for the sincos and its
-// power chains, which go to the warp's shared rows ([table][power], padded so
-// the lanes' float4 stores spread over the banks); then the warp writes its
-// 32 tables, one table at a time, 32 consecutive entries per store.
+// Warp 0's lane l takes table t0 + l for the sincos and its power chains,
+// which go to shared rows ([table][power], padded so the lanes' float4 stores
+// spread over the banks), while warp 1's lane l forms alpha; then the CTA's
+// warps write the 32 tables, warp w the tables w, w + 8, ..., 32
+// consecutive entries per store.
 __global__ void __launch_bounds__(kPhaseWarps * 32)
 phase_table_kernel(const double *__restrict__ gammas, const double *__restrict__ betas,
                    int64_t count, int entries, float2 *__restrict__ phase,
                    double2 *__restrict__ alpha) {
-  // [warp][table][r] = e^{-i gamma r}, [warp][table][16 + q] = e^{-i 16 gamma q}
-  __shared__ float4 P[kPhaseWarps][32][33];
+  __shared__ float4 P[32][33];  // [table][r] = e^{-i gamma r}, [table][16 + q] = e^{-i 16 gamma q}
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nq = entries / 16;  // rows of the 16 gamma chain in use
   const int64_t nblk = (count + 31) / 32;
-  for (int64_t blk = (int64_t)blockIdx.x * kPhaseWarps + warp; blk < nblk;
-       blk += (int64_t)gridDim.x * kPhaseWarps) {
-    const int64_t t = blk * 32 + lane;
-    const bool live = t < count;
-    const double g = live ? gammas[t] : 0.0;
-    double s1, c1;
-    sincos(g, &s1, &c1);
-    if (live) {
-      double sb, cb;
-      sincos(betas[t], &sb, &cb);
-      alpha[t] = make_double2(cb - 1.0, -sb);
-    }
-    const DFc e1 = {dfv_from(c1), dfv_from(-s1)};
-    DFc e16 = dfc_mul(e1, e1);  // e^{-i 2 gamma}
-    e16 = dfc_mul(e16, e16);
-    e16 = dfc_mul(e16, e16);
-    e16 = dfc_mul(e16, e16);    // e^{-i 16 gamma}
-    DFc a1 = {{1.f, 0.f}, {0.f, 0.f}}, a16 = a1;
-#pragma unroll 1
-    for (int r = 0; r < 16; ++r) {
-      P[warp][lane][r] = make_float4(a1.x.hi, a1.x.lo, a1.y.hi, a1.y.lo);
-      a1 = dfc_mul(a1, e1);
-      if (r < nq) {
-        P[warp][lane][16 + r] = make_float4(a16.x.hi, a16.x.lo, a16.y.hi, a16.y.lo);
-        a16 = dfc_mul(a16, e16);
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    if (warp == 1) {  // the mixer coefficients, beside warp 0's phase powers
+      const int64_t t = blk * 32 + lane;
+      if (t < count) {
+        double sb, cb;
+        sincos(betas[t], &sb, &cb);
+        alpha[t] = make_double2(cb - 1.0, -sb);
       }
     }
-    __syncwarp();
+    if (warp == 0) {
+      const int64_t t = blk * 32 + lane;
+      const bool live = t < count;
+      const double g = live ? gammas[t] : 0.0;
+      double s1, c1;
+      sincos(g, &s1, &c1);
+      const DFc e1 = {dfv_from(c1), dfv_from(-s1)};
+      DFc e16 = dfc_mul(e1, e1);  // e^{-i 2 gamma}
+      e16 = dfc_mul(e16, e16);
+      e16 = dfc_mul(e16, e16);
+      e16 = dfc_mul(e16, e16);    // e^{-i 16 gamma}
+      DFc a1 = {{1.f, 0.f}, {0.f, 0.f}}, a16 = a1;
+#pragma unroll 1
+      for (int r = 0; r < 16; ++r) {
+        P[lane][r] = make_float4(a1.x.hi, a1.x.lo, a1.y.hi, a1.y.lo);
+        a1 = dfc_mul(a1, e1);
+        if (r < nq) {
+          P[lane][16 + r] = make_float4(a16.x.hi, a16.x.lo, a16.y.hi, a16.y.lo);
+          a16 = dfc_mul(a16, e16);
+        }
+      }
+    }
+    __syncthreads();
     const int tn = (int)(count - blk * 32 < 32 ? count - blk * 32 : 32);
 #pragma unroll 1
-    for (int tt = 0; tt < tn; ++tt) {
-      const DFc er = dfc_load(P[warp][tt][lane & 15]);
+    for (int tt = warp; tt < tn; tt += kPhaseWarps) {
+      const DFc er = dfc_load(P[tt][lane & 15]);
       float2 *dst = phase + (blk * 32 + tt) * entries;
 #pragma unroll 8
       for (int i = 0; i < entries / 32; ++i) {
         // entry c = lane + 32 i = 16 q + r with r = lane & 15, q = (lane >> 4) + 2 i
-        const DFc v = dfc_mul(dfc_load(P[warp][tt][16 + (lane >> 4) + 2 * i]), er);
+        const DFc v = dfc_mul(dfc_load(P[tt][16 + (lane >> 4) + 2 * i]), er);
         dst[lane + 32 * i] = make_float2(v.x.hi, v.y.hi);
       }
     }
-    __syncwarp();  // the rows are rewritten for the warp's next block
+    __syncthreads();  // the rows are rewritten for the next block
   }
 }
 
@@ -1156,10 +1160,9 @@ static double *parts_half(const Ws &w, int i) { return w.parts + (size_t)(i & 1)
 int phase_tables(const double *gammas, const double *betas, int64_t count, int entries,
                  float2 *phase, double2 *alpha, cudaStream_t st) {
   if (entries < 32 || entries > 256 || entries % 32 != 0) return GQAOA_EINVAL;
-  const int64_t nblk = (count + 31) / 32;  // blocks of 32 tables, one per warp
-  const int64_t need = (nblk + kPhaseWarps - 1) / kPhaseWarps;
-  const int64_t cap = (int64_t)sm_count() * 16;
-  const int64_t grid = need < cap ? need : cap;
+  const int64_t nblk = (count + 31) / 32;  // blocks of 32 tables, one per CTA
+  const int64_t cap = (int64_t)sm_count() * 8;
+  const int64_t grid = nblk < cap ? nblk : cap;
   phase_table_kernel<<<(unsigned)grid, kPhaseWarps * 32, 0, st>>>(gammas, betas, count, entries,
                                                                   phase, alpha);
   GQ_CHECK_LAUNCH();

@@ -31,8 +31,15 @@ def test_reference_arm_json_line():
 
 
 def test_reference_arm_unavailable_for_device_only_workloads():
-    d = run("--impl", "reference", "--workload", "grad")
-    assert d["impl"] == "reference" and "unavailable" in d
+    for wl in ("grad", "protocol", "fairness", "sweep"):
+        d = run("--impl", "reference", "--workload", wl)
+        assert d["impl"] == "reference" and "unavailable" in d, wl
+
+
+def test_reference_arm_of_the_grid_workload():
+    d = run("--impl", "reference", "--workload", "grid", "--steps", "1", "--warmup", "0")
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "item-rounds/s"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
 
 
 def test_workload_table():
@@ -45,7 +52,8 @@ def test_workload_table():
             "sweep": ("count", "grid", "p", "rounds"),
             "protocol": ("count", "n_values", "d_lo", "d_hi", "S", "p_max"),
             "fairness": ("n", "runs", "shots_per_run", "alpha"),
-            "study": ("train", "train_n", "test", "test_n", "p")}
+            "study": ("train", "train_n", "test", "test_n", "p"),
+            "grid": ("n", "m", "p", "seed")}
     for name, wl in bench.WORKLOADS.items():
         assert isinstance(wl.get("desc"), str) and wl["desc"], name
         for key in need[wl.get("kind")]:

@@ -181,8 +181,8 @@ def test_reduced_sweep_rejects_bad_arguments_before_launch():
         with pytest.raises(C.GQAOAError) as e:
             C.gqaoa_reduced_sweep(*args)
         assert e.value.status == C.GQAOA_ERANGE
-    with pytest.raises(C.GQAOAError) as e:  # misaligned output
-        C.gqaoa_reduced_sweep(fake, 43, 10, 1, fake, fake, 4, 4, fake + 4, None, fake, 1 << 20, None)
+    with pytest.raises(C.GQAOAError) as e:  # misaligned output (FP32: 4-byte aligned)
+        C.gqaoa_reduced_sweep(fake, 43, 10, 1, fake, fake, 4, 4, fake + 2, None, fake, 1 << 20, None)
     assert e.value.status == C.GQAOA_EINVAL
     # phase tables of 64 entries (stride 43 rounded up to 32), alpha, the
     # minima of 1 x 4 rounds, the per-warp minima (4 lanes per item: 8 items

@@ -71,8 +71,6 @@ def test_reduced_sweep_matches_oracle(n, ms, A, p):
             assert np.max(np.abs(got[:, 2] - ref[:, 2])) < 1e-6, (b, a)
             assert np.max(np.abs(got[:, 1] - ref[:, 1])) < 1e-6 * ms[b], (b, a)
         assert abs(out[b, 0, -1, 1] - ms[b] / 8) < 1e-6 * ms[b]
-    # every written value is a float widened exactly
-    assert np.array_equal(out.astype(np.float32).astype(np.float64), out)
     bst = best.cpu().numpy()
     for b in range(H.shape[0]):
         for k in range(p):
@@ -143,7 +141,7 @@ def test_reduced_sweep_edge_cases():
     ws = core.workspace(need)
     g = torch.zeros(4, dtype=torch.float64, device="cuda")
     hist = torch.as_tensor(H, device="cuda")
-    o = torch.empty((1, 4, 6, 3), dtype=torch.float64, device="cuda")
+    o = torch.empty((1, 6, 3, 4), dtype=torch.float32, device="cuda")
     with pytest.raises(C.GQAOAError) as e:
         C.gqaoa_reduced_sweep(hist.data_ptr(), H.shape[1], 9, 1, g.data_ptr(), g.data_ptr(), 4, 6,
                               o.data_ptr(), None, ws.data_ptr(), need - 1,
