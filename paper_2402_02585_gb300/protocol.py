@@ -28,11 +28,15 @@ statevector decides.
 Evaluations are issued in one of two ways. Depth by depth (window = 1), each
 depth's gqaoa_grad call is captured once into a CUDA graph and replayed for
 every L-BFGS-B evaluation. With a depth window (window = W), W consecutive
-depths are refined side by side: their L-BFGS-B searches run on host
-threads in lockstep and every wave of their gradient requests is one
+depths are refined side by side: their L-BFGS-B searches advance in
+lockstep and every wave of their gradient requests is one
 gqaoa_grad_batched call, the shallower depths padded with identity rounds;
 the shallowest depth of the window that reaches S is the answer, as in the
-depth-by-depth scan.
+depth-by-depth scan. The searches are SciPy's L-BFGS-B routine stepped by
+reverse communication from one thread, with the calls
+scipy.optimize.minimize makes (so the same iterates, checked once per
+process); where that check fails, each search runs minimize on a host
+thread of its own.
 """
 
 from __future__ import annotations
@@ -247,6 +251,115 @@ class _DepthBatch:
                 for i, (k, _, _) in enumerate(rows)]
 
 
+class _Lbfgsb:
+    """One L-BFGS-B search run by reverse communication: point() is the next
+    x to evaluate (None once the search has ended), tell(f, g) gives the
+    value and gradient there. It drives SciPy's L-BFGS-B routine (setulb,
+    one step per call) with the calls scipy.optimize.minimize(method=
+    "L-BFGS-B") makes for the same options and its defaults (10 corrections,
+    20 line-search steps, 15000 evaluations, no bounds): an evaluation at x0
+    before the first call, the last value reused when the routine asks again
+    for the same x, and the iteration and evaluation limits checked at each
+    new iterate. So its iterates, evaluation count and result are minimize's
+    bit for bit (`lbfgsb_matches_scipy` checks this once per process), while
+    many searches can be stepped from one thread."""
+
+    def __init__(self, x0, ftol: float, gtol: float, maxiter: int, maxcor: int = 10,
+                 maxls: int = 20, maxfun: int = 15000):
+        from scipy.linalg.lapack import HAS_ILP64
+        from scipy.optimize import _lbfgsb
+        self._setulb = _lbfgsb.setulb
+        it = np.int64 if HAS_ILP64 else np.int32
+        self.x = np.array(x0, dtype=np.float64).ravel()
+        n, m = self.x.size, maxcor
+        self.m, self.maxls, self.maxiter, self.maxfun = m, maxls, maxiter, maxfun
+        self.factr = ftol / np.finfo(float).eps
+        self.pgtol = gtol
+        self.lo = np.zeros(n)
+        self.hi = np.zeros(n)
+        self.nbd = np.zeros(n, dtype=it)
+        self.wa = np.zeros(2 * m * n + 5 * n + 11 * m * m + 8 * m)
+        self.iwa = np.zeros(3 * n, dtype=it)
+        self.task = np.zeros(2, dtype=it)
+        self.ln_task = np.zeros(2, dtype=it)
+        self.lsave = np.zeros(4, dtype=it)
+        self.isave = np.zeros(44, dtype=it)
+        self.dsave = np.zeros(29)
+        self.f = 0.0
+        self.g = np.zeros(n)
+        self.nit = 0
+        self.nfev = 0
+        self.last = None          # (x, f, g) of the latest evaluation
+        self.want = self.x.copy()  # minimize evaluates at x0 first
+        self.converged = False
+
+    def point(self):
+        return self.want
+
+    def tell(self, f, g):
+        self.nfev += 1
+        self.last = (self.want, float(f), np.array(g, dtype=np.float64).ravel())
+        if self.nfev > 1:
+            self.f, self.g = self.last[1], self.last[2].copy()
+        while True:
+            self._setulb(self.m, self.x, self.lo, self.hi, self.nbd, self.f, self.g, self.factr,
+                         self.pgtol, self.wa, self.iwa, self.task, self.lsave, self.isave,
+                         self.dsave, self.maxls, self.ln_task)
+            task = int(self.task[0])
+            if task == 3:  # f and g wanted at self.x
+                if np.array_equal(self.x, self.last[0]):
+                    self.f, self.g = self.last[1], self.last[2].copy()
+                    continue
+                self.want = self.x.copy()
+                return
+            if task == 1:  # a new iterate
+                self.nit += 1
+                if self.nit >= self.maxiter:
+                    self.task[0], self.task[1] = 5, 504
+                elif self.nfev > self.maxfun:
+                    self.task[0], self.task[1] = 5, 502
+                continue
+            self.converged = task == 4
+            self.want = None
+            return
+
+
+_LBFGSB_OK = None
+
+
+def lbfgsb_matches_scipy() -> bool:
+    """Whether _Lbfgsb reproduces scipy.optimize.minimize(method="L-BFGS-B")
+    bit for bit on this SciPy (a few seeded smooth problems of 2 and 12
+    variables); False as well if SciPy's low-level routine is missing or has
+    another interface. Checked once per process."""
+    global _LBFGSB_OK
+    if _LBFGSB_OK is not None:
+        return _LBFGSB_OK
+    ok = True
+    try:
+        rng = np.random.default_rng(7)
+        for n in (2, 12):
+            A = rng.normal(size=(n, n))
+            H = A @ A.T + np.eye(n)
+            c = rng.normal(size=n)
+
+            def fun(x):
+                r = x - c
+                return float(0.5 * r @ H @ r + 0.3 * np.sin(x).sum()), H @ r + 0.3 * np.cos(x)
+
+            x0 = rng.normal(size=n)
+            ref = scipy.optimize.minimize(fun, x0, jac=True, method="L-BFGS-B",
+                                          options=dict(ftol=1e-6, gtol=1e-10, maxiter=500))
+            s = _Lbfgsb(x0, 1e-6, 1e-10, 500)
+            while s.point() is not None:
+                s.tell(*fun(s.point()))
+            ok = ok and np.array_equal(s.x, ref.x) and s.f == ref.fun and s.nfev == ref.nfev
+    except Exception:  # another SciPy: the threaded lockstep is used instead
+        ok = False
+    _LBFGSB_OK = ok
+    return ok
+
+
 class _Lockstep:
     """Runs several L-BFGS-B searches side by side, one host thread each, and
     gathers every wave of their evaluation requests into one call: a wave is
@@ -376,10 +489,11 @@ class Protocol:
         single angle pair seeds[k]): the searches run side by side and each
         wave of their gradient requests is one batched call (_DepthBatch).
         Each depth's search is the one refine() makes, so the results equal
-        refine()'s up to the rounding of the batched sums. Returns
-        {k: (gammas, betas, <H_P>)}."""
+        refine()'s up to the rounding of the batched sums. The searches are
+        stepped from the calling thread (_Lbfgsb) where that reproduces
+        SciPy's minimize bit for bit, else each runs minimize on a host
+        thread of its own (_Lockstep). Returns {k: (gammas, betas, <H_P>)}."""
         batch = _DepthBatch(self, len(depths), max(depths))
-        steps = _Lockstep(depths)
         results, errors = {}, []
 
         def rows_of(wave):
@@ -398,17 +512,38 @@ class Protocol:
                 res[k] = (e, np.array([dg.sum(), db.sum()]) if single else np.concatenate([dg, db]))
             return res
 
+        def x0_of(k):
+            g0, b0 = seeds[k]
+            return np.array([g0, b0]) if single else np.concatenate([np.full(k, g0), np.full(k, b0)])
+
+        def keep(k, x, fun):
+            if single:
+                results[k] = (np.full(k, x[0]), np.full(k, x[1]), float(fun))
+            else:
+                results[k] = (x[:k].copy(), x[k:].copy(), float(fun))
+
+        if lbfgsb_matches_scipy():
+            # every search stepped from this thread: one batched call per wave
+            searches = {k: _Lbfgsb(x0_of(k), 1e-6, 1e-10, 500) for k in depths}
+            while True:
+                wave = {k: s.point() for k, s in searches.items() if s.point() is not None}
+                if not wave:
+                    break
+                for k, fg in evaluate(wave).items():
+                    searches[k].tell(*fg)
+            for k, s in searches.items():
+                keep(k, s.x, s.f)
+            return results
+
+        # the same searches by scipy.optimize.minimize, one host thread each
+        steps = _Lockstep(depths)
+
         def search(k):
             try:
-                g0, b0 = seeds[k]
-                x0 = np.array([g0, b0]) if single else np.concatenate([np.full(k, g0), np.full(k, b0)])
-                r = scipy.optimize.minimize(lambda x: steps.request(k, x), x0, jac=True,
+                r = scipy.optimize.minimize(lambda x: steps.request(k, x), x0_of(k), jac=True,
                                             method="L-BFGS-B",
                                             options=dict(ftol=1e-6, gtol=1e-10, maxiter=500))
-                if single:
-                    results[k] = (np.full(k, r.x[0]), np.full(k, r.x[1]), float(r.fun))
-                else:
-                    results[k] = (r.x[:k].copy(), r.x[k:].copy(), float(r.fun))
+                keep(k, r.x, r.fun)
             except BaseException as exc:
                 errors.append(exc)
             finally:
