@@ -470,11 +470,18 @@ class Protocol:
                 e, dg, db = self.energy_and_grad(x[:p], x[p:])
                 return e, np.concatenate([dg, db])
             x0 = np.concatenate([g0, b0])
-        r = scipy.optimize.minimize(fun, x0, jac=True, method="L-BFGS-B",
-                                    options=dict(ftol=1e-6, gtol=1e-10, maxiter=500))
+        if lbfgsb_matches_scipy():  # minimize's search, without its per-call wrapping
+            s = _Lbfgsb(x0, 1e-6, 1e-10, 500)
+            while s.point() is not None:
+                s.tell(*fun(s.point()))
+            x, fx, nfev = s.x, s.f, s.nfev
+        else:
+            r = scipy.optimize.minimize(fun, x0, jac=True, method="L-BFGS-B",
+                                        options=dict(ftol=1e-6, gtol=1e-10, maxiter=500))
+            x, fx, nfev = r.x, r.fun, r.nfev
         if single:
-            return np.full(p, r.x[0]), np.full(p, r.x[1]), float(r.fun), int(r.nfev)
-        return r.x[:p].copy(), r.x[p:].copy(), float(r.fun), int(r.nfev)
+            return np.full(p, x[0]), np.full(p, x[1]), float(fx), int(nfev)
+        return x[:p].copy(), x[p:].copy(), float(fx), int(nfev)
 
     def probability(self, gammas, betas, cls: int = 0) -> float:
         """Probability of cost value cls in the evolved state (statevector)."""
