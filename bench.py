@@ -605,8 +605,8 @@ def l2_rmw_peak(device) -> float:
 
 
 # on-chip share of the state on the cluster-resident sweep path: 16 CTAs x
-# 256 on-chip threads x (20 float4 in registers + 48 in shared memory) x 2
-L2_PATH_ONCHIP_AMPS = 16 * 256 * (20 + 48) * 2
+# 256 on-chip threads x (18 float4 in registers + 48 in shared memory) x 2
+L2_PATH_ONCHIP_AMPS = 16 * 256 * (18 + 48) * 2
 
 
 def run_sweep(args, wl):

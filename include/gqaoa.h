@@ -290,8 +290,8 @@ int gqaoa_batched_geometry(int n, int batch, int adjoint, int *ctas_per_instance
  *   16  a thread holds 16 amplitudes in registers (n in 9..18);
  *   32  16 in registers and 16 in shared memory (n in 10..19);
  *   GQAOA_SWEEP_L2  cluster-resident: one 16-CTA cluster per item keeps
- *       557056 amplitudes on chip (163840 in registers, 393216 in shared
- *       memory: 53 % of an n = 20 state) and streams the rest through its
+ *       540672 amplitudes on chip (147456 in registers, 393216 in shared
+ *       memory: 52 % of an n = 20 state) and streams the rest through its
  *       slot of the workspace (16 slots of 2^n * 8 bytes), which stays in L2
  *       while the items in flight fit there (n = 20: 3.75 MiB touched per
  *       item, at most 16 items); n in GQAOA_SWEEP_L2_MIN_N..

@@ -255,7 +255,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
 // side, so the SM's L2 port and its ALUs are busy at the same time:
 //  * on-chip warps (8): thread u holds the float4 j 256 + u of the sixteenth
 //    for j < kL2RegVec in registers and for kL2RegVec <= j < kL2OnChip in
-//    shared memory, for the whole evolution (17408 float4 per CTA, 53 % of an
+//    shared memory, for the whole evolution (16896 float4 per CTA, 52 % of an
 //    n = 20 state);
 //  * streaming warps (8): thread u owns the float4 kL2OnChip 256 + j 256 + u
 //    for the rest of the sixteenth; they live in the cluster's slot of the
@@ -283,11 +283,16 @@ constexpr int kL2Warps = kL2Threads / 32;
 constexpr int kL2RoleThreads = kL2Threads / 2;  // threads per role
 constexpr int kL2Cluster = 16;
 constexpr int kL2Slots = 16;
-constexpr int kL2RegVec = 20;   // float4 per on-chip thread held in registers
+constexpr int kL2RegVec = 18;   // float4 per on-chip thread held in registers
 constexpr int kL2SmemVec = 48;  // float4 per on-chip thread held in shared memory
 constexpr int kL2OnChip = kL2RegVec + kL2SmemVec;
 constexpr int kL2Batch = 2;     // float4 per streaming batch
 constexpr int kL2Ring = kL2RegVec / kL2Batch;  // batches in a streaming thread's ring
+// a batch's two float4 take their four cost bytes from one 32-bit word of the
+// cost ring, and a thread's streamed share (2^(n-13) - kL2OnChip float4 for
+// n = 20..24) must split into whole batches
+static_assert(kL2Batch == 2 && kL2RegVec % kL2Batch == 0 && kL2OnChip % kL2Batch == 0,
+              "cluster-resident sweep: ring layout");
 constexpr size_t kL2DynSmem =
     (size_t)kL2SmemVec * kL2RoleThreads * (sizeof(float4) + sizeof(uint16_t));
 

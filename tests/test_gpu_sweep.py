@@ -6,7 +6,7 @@ small n, the exact cost-class model (pinned against it) at larger n. The
 on-chip cases cover one warp per item (n = 9), whole CTAs (n = 12..14),
 clusters of 2, 4, 8 and 16 CTAs (n = 15..18), a 16-CTA cluster with half the
 state in shared memory (n = 19), and more items than resident CTAs. The
-cluster-resident path (GQAOA_SWEEP_L2) covers n = 20..22 (53 % of an n = 20
+cluster-resident path (GQAOA_SWEEP_L2) covers n = 20..22 (52 % of an n = 20
 state on chip, the rest streamed through the workspace) and more items than
 resident clusters.
 """
