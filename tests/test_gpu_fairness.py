@@ -28,6 +28,9 @@ pytestmark = pytest.mark.gpu
     (8, 30, 11, 500, 64, 0.6),     # 5 solutions
     (10, 40, 2, 2000, 512, 0.3),   # 16 solutions (about 180 shots to see them all)
     (9, 60, 2, 300, 400, 0.5),     # unsatisfiable: the lowest class c* = 1
+    # the kernel with counts in global memory: runs longer than 4095 shots, and n > 15
+    (8, 30, 11, 200, 5000, 0.6),
+    (16, 67, 3, 300, 700, 0.3),
 ])
 def test_fairness_matches_oracle_exactly(n, m, seed, runs, per_run, hot):
     lits = instances.random_3sat(n, m, seed)
