@@ -23,6 +23,7 @@ GQAOA_ENOMEM = -5
 GQAOA_STATE_IN = 1
 GQAOA_OBJ_P0 = 0
 GQAOA_OBJ_ENERGY = 1
+GQAOA_GRAD_STREAMING = 1 << 16  # OR-ed into a gradient objective: the streaming passes
 
 
 def GQAOA_OBJ_CLASS(c: int) -> int:

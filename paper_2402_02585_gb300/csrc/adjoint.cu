@@ -1,0 +1,341 @@
+// Cluster-resident adjoint gradient (Eq. 3 rounds, forward then backward,
+// for states of 2^12..2^16 amplitudes).
+//
+// The streaming adjoint makes one launch per round and direction; for a
+// state of at most 2^16 amplitudes a round is a few microseconds of work on
+// the whole GPU, so the launch boundaries set the time. Here one thread-block
+// cluster owns one instance (row) for the whole call: each thread keeps 16
+// amplitudes in registers, the forward rounds write the checkpoints chi_k
+// (each thread later rereads only its own), and the backward rounds follow
+// in the same launch. A round's sums go warp (double-float butterfly) -> CTA
+// (warp 0 over the warp partials) -> cluster (every CTA's partial pushed into
+// the shared memory of every peer, one cluster barrier, every warp summing
+// the partials in rank order), so every warp of every CTA holds the same
+// totals bit for bit and no further barrier is needed. The arithmetic is the
+// small-state kernels' (double-float sums, FP32 amplitudes); the mixer
+// coefficients are formed in FP32 from the double-float sums, and FP64 is
+// used only by the thread that writes a row's records and gradients.
+//
+// Forward round k: chi_k = T_k[c] psi_{k-1} (checkpointed), S_k = sum chi_k,
+// a_k = alpha_k S_k / N, psi_k = chi_k + a_k. Backward, from
+// lambda = O psi_p: with L = sum lambda and mu = lambda + conj(alpha_k) L / N,
+// dE/dgamma_k = 2 sum_z c(z) Im(conj(mu) chi_k), and lambda <- conj(T_k) mu;
+// dE/dbeta_k = 2 Im(conj(e^{-i beta_k} S_k / N) L). The sum of the updated
+// lambda (the next round's L) is reduced together with the gamma term, so a
+// backward round takes one cluster reduction.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace gq {
+
+int sm_count();
+
+namespace {
+
+constexpr int kAdjPer = 16;  // amplitudes per thread
+constexpr int kAdjVals = 3;  // values per reduction
+
+struct AdjArgs {
+  const uint8_t *cost;    // row b at cost + b * cost_bstride
+  uint64_t cost_bstride;
+  const float2 *phase;    // [B][p][256]
+  const double2 *alpha;   // [B][p]
+  double *record;         // [B][p][4]: S_k (re, im) of the forward
+  float2 *ckpt;           // [p][B][N]
+  double *value;          // [B]
+  double *dgamma;         // [B][p]
+  double *dbeta;          // [B][p]
+  int n;
+  int p;
+  int B;
+  int objective;          // GQAOA_OBJ_P0 (projector on `target`) or GQAOA_OBJ_ENERGY
+  unsigned target;
+};
+
+// Double-float sum over the warp's lanes (every lane ends with the same sum).
+__device__ __forceinline__ void adj_df_warp(float &hi, float &lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    float s, e;
+    two_sum(hi, h2, s, e);
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, l2), e);
+  }
+}
+
+// (hi, lo) += x in double-float arithmetic.
+__device__ __forceinline__ void adj_df_add(float &hi, float &lo, float x) {
+  float s, e;
+  two_sum(hi, x, s, e);
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
+__device__ __forceinline__ void adj_st_dsmem(float2 *p, unsigned rank, float2 v) {
+  uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(remote), "f"(v.x), "f"(v.y)
+               : "memory");
+}
+
+// Cluster-wide double-float sums of kV <= kAdjVals values: v[k] holds this thread's
+// (hi, lo) on entry and the cluster's total on exit, the same in every
+// thread. buf alternates between calls: the partials of one call are read
+// while the next call's are written.
+template <int kThreads, int kCluster, int kV>
+__device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
+                                                float2 (*s_wp)[kThreads / 32][kAdjVals],
+                                                float2 (*s_ps)[kCluster][kAdjVals], int buf,
+                                                unsigned rank) {
+  constexpr int kW = kThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kV; ++k) adj_df_warp(v[k].x, v[k].y);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < kV; ++k) s_wp[buf][warp][k] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < kV; ++k) {
+      float2 d = lane < kW ? s_wp[buf][lane][k] : make_float2(0.f, 0.f);
+      adj_df_warp(d.x, d.y);
+      if (kCluster == 1) {
+        if (lane == 0) s_ps[buf][0][k] = d;
+      } else if (lane < kCluster) {
+        adj_st_dsmem(&s_ps[buf][rank][k], (unsigned)lane, d);
+      }
+    }
+  }
+  if (kCluster > 1)
+    cluster_sync();  // release/acquire: every CTA's partial visible locally
+  else
+    __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kV; ++k) {
+    float2 d = lane < kCluster ? s_ps[buf][lane][k] : make_float2(0.f, 0.f);
+    adj_df_warp(d.x, d.y);
+    v[k] = d;
+  }
+}
+
+// The mixer coefficients as FP32 pairs, into the records' spare slots
+// (record[4 bk + 2], read as a float2), so the rounds convert no FP64.
+__global__ void adj_alpha_kernel(const double2 *__restrict__ alpha, uint64_t count,
+                                 double *__restrict__ record) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const double2 al = alpha[i];
+    *reinterpret_cast<float2 *>(record + 4 * i + 2) = make_float2((float)al.x, (float)al.y);
+  }
+}
+
+// Pull one 2 KB phase table into L1 (16 threads, one 128-byte line each).
+__device__ __forceinline__ void adj_prefetch_table(const float2 *T) {
+  if (threadIdx.x < 16) asm volatile("prefetch.global.L1 [%0];" ::"l"(T + 16 * threadIdx.x));
+}
+
+template <int kThreads, int kCluster>
+__global__ void __launch_bounds__(kThreads, 512 / kThreads)
+adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
+  constexpr int kW = kThreads / 32;
+  __shared__ float2 s_wp[2][kW][kAdjVals];
+  __shared__ float2 s_ps[2][kCluster][kAdjVals];
+  const unsigned rank = kCluster > 1 ? cluster_ctarank() : 0u;
+  const uint64_t cl = blockIdx.x / kCluster, ncl = gridDim.x / kCluster;
+  const uint64_t N = 1ull << a.n;
+  const float inv_n = (float)(1.0 / (double)N);  // a power of two: exact
+  const float amp0 = (float)(1.0 / sqrt((double)N));
+  const bool writer = rank == 0 && threadIdx.x == 0;
+  // slot j of this thread is amplitude z0 + j kThreads
+  const uint64_t z0 = (uint64_t)rank * kAdjPer * kThreads + threadIdx.x;
+  int buf = 0;
+  for (uint64_t b = cl; b < (uint64_t)a.B; b += ncl) {
+    const uint8_t *cost = a.cost + b * a.cost_bstride + z0;
+    unsigned c[kAdjPer];
+    float2 s[kAdjPer];
+#pragma unroll
+    for (int j = 0; j < kAdjPer; ++j) {
+      c[j] = cost[j * kThreads];
+      s[j] = make_float2(amp0, 0.f);
+    }
+    // forward: chi_k into the checkpoints, psi_k = chi_k + a_k
+    for (int k = 0; k < a.p; ++k) {
+      const uint64_t bk = b * (uint64_t)a.p + k;
+      const float2 *T = a.phase + bk * 256;
+      float2 *ck = a.ckpt + ((uint64_t)k * a.B + b) * N + z0;
+      float sr = 0.f, si = 0.f;
+#pragma unroll
+      for (int j = 0; j < kAdjPer; ++j) {
+        s[j] = cmul(T[c[j]], s[j]);
+        ck[j * kThreads] = s[j];
+        sr += s[j].x;
+        si += s[j].y;
+      }
+      adj_prefetch_table(k + 1 < a.p ? T + 256 : a.phase + (b * (uint64_t)a.p + a.p - 1) * 256);
+      float2 v[kAdjVals] = {make_float2(sr, 0.f), make_float2(si, 0.f), make_float2(0.f, 0.f)};
+      adj_cluster_sum<kThreads, kCluster, 2>(v, s_wp, s_ps, buf, rank);
+      buf ^= 1;
+      const float Sr = v[0].x + v[0].y, Si = v[1].x + v[1].y;
+      const float2 al = *reinterpret_cast<const float2 *>(a.record + 4 * bk + 2);
+      const float2 af = make_float2((al.x * Sr - al.y * Si) * inv_n, (al.x * Si + al.y * Sr) * inv_n);
+#pragma unroll
+      for (int j = 0; j < kAdjPer; ++j) s[j] = make_float2(s[j].x + af.x, s[j].y + af.y);
+      if (writer) {
+        a.record[4 * bk] = (double)v[0].x + (double)v[0].y;
+        a.record[4 * bk + 1] = (double)v[1].x + (double)v[1].y;
+      }
+    }
+    // lambda_p = O psi_p, the objective sum_z O |psi_p|^2 (double-float:
+    // each square split exactly by an FMA) and L = sum lambda
+    float2 l[kAdjPer];
+    float vh = 0.f, vl = 0.f, lr = 0.f, li = 0.f;
+#pragma unroll
+    for (int j = 0; j < kAdjPer; ++j) {
+      const float o = a.objective == GQAOA_OBJ_P0 ? (c[j] == a.target ? 1.f : 0.f) : (float)c[j];
+      l[j] = make_float2(o * s[j].x, o * s[j].y);
+      const float px = s[j].x * s[j].x, ex = fmaf(s[j].x, s[j].x, -px);
+      const float py = s[j].y * s[j].y, ey = fmaf(s[j].y, s[j].y, -py);
+      float wh, wl;
+      two_sum(px, py, wh, wl);
+      wl = __fadd_rn(wl, __fadd_rn(ex, ey));
+      const float ph = o * wh, pe = fmaf(o, wh, -ph);  // o is an integer below 256
+      adj_df_add(vh, vl, ph);
+      vl = __fadd_rn(vl, fmaf(o, wl, pe));
+      lr += l[j].x;
+      li += l[j].y;
+    }
+    // the last round's checkpoints are loaded before the reduction, and each
+    // backward round loads the next one's after its own are consumed, so the
+    // loads' latency overlaps the reductions
+    float2 x[kAdjPer];
+    {
+      const float2 *ck = a.ckpt + ((uint64_t)(a.p - 1) * a.B + b) * N + z0;
+#pragma unroll
+      for (int j = 0; j < kAdjPer; ++j) x[j] = ck[j * kThreads];
+    }
+    float2 v[kAdjVals] = {make_float2(vh, vl), make_float2(lr, 0.f), make_float2(li, 0.f)};
+    adj_cluster_sum<kThreads, kCluster, 3>(v, s_wp, s_ps, buf, rank);
+    buf ^= 1;
+    if (writer) a.value[b] = (double)v[0].x + (double)v[0].y;
+    // backward rounds
+    for (int k = a.p - 1; k >= 0; --k) {
+      const uint64_t bk = b * (uint64_t)a.p + k;
+      const float2 Ld = v[1], Li2 = v[2];  // this round's L (double-float)
+      const float Lr = Ld.x + Ld.y, Li = Li2.x + Li2.y;
+      const float2 al = *reinterpret_cast<const float2 *>(a.record + 4 * bk + 2);
+      const float2 bv = make_float2((al.x * Lr + al.y * Li) * inv_n, (al.x * Li - al.y * Lr) * inv_n);
+      const float2 *T = a.phase + bk * 256;
+      float g = 0.f, nlr = 0.f, nli = 0.f;
+#pragma unroll
+      for (int j = 0; j < kAdjPer; ++j) {
+        const float2 mu = make_float2(l[j].x + bv.x, l[j].y + bv.y);
+        g = fmaf((float)c[j], fmaf(mu.x, x[j].y, -mu.y * x[j].x), g);
+        const float2 t = T[c[j]];
+        l[j] = make_float2(fmaf(t.x, mu.x, t.y * mu.y), fmaf(t.x, mu.y, -t.y * mu.x));
+        nlr += l[j].x;
+        nli += l[j].y;
+      }
+      if (k > 0) {
+        const float2 *ck = a.ckpt + ((uint64_t)(k - 1) * a.B + b) * N + z0;
+#pragma unroll
+        for (int j = 0; j < kAdjPer; ++j) x[j] = ck[j * kThreads];
+        adj_prefetch_table(T - 256);
+      }
+      v[0] = make_float2(g, 0.f);
+      v[1] = make_float2(nlr, 0.f);
+      v[2] = make_float2(nli, 0.f);
+      adj_cluster_sum<kThreads, kCluster, 3>(v, s_wp, s_ps, buf, rank);
+      buf ^= 1;
+      if (writer) {
+        const double2 ald = a.alpha[bk];
+        const double Sre = a.record[4 * bk] / (double)N, Sim = a.record[4 * bk + 1] / (double)N;
+        const double er = ald.x + 1.0, ei = ald.y;  // e^{-i beta_k}
+        const double qr = er * Sre - ei * Sim, qi = er * Sim + ei * Sre;
+        const double Lrd = (double)Ld.x + (double)Ld.y, Lid = (double)Li2.x + (double)Li2.y;
+        a.dbeta[bk] = 2.0 * (qi * Lrd - qr * Lid);
+        a.dgamma[bk] = 2.0 * ((double)v[0].x + (double)v[0].y);
+      }
+    }
+  }
+  if (kCluster > 1) cluster_sync();  // no CTA leaves while a peer may still store into it
+}
+
+template <int kThreads, int kCluster>
+int launch_adjoint(const AdjArgs &args, cudaStream_t st) {
+  auto kernel = adjoint_cluster_kernel<kThreads, kCluster>;
+  if (kCluster > 8 &&
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return GQAOA_ECUDA;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCluster, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;  // resident clusters (CTAs for kCluster = 1)
+  if (kCluster == 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&clusters, kernel, kThreads, 0) != cudaSuccess)
+      return GQAOA_ECUDA;
+    clusters *= sm_count();
+  } else if (cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg) != cudaSuccess) {
+    return GQAOA_ECUDA;
+  }
+  if (clusters < 1) return GQAOA_ECUDA;
+  const uint64_t units = (uint64_t)args.B < (uint64_t)clusters ? (uint64_t)args.B : (uint64_t)clusters;
+  cfg.gridDim = dim3((unsigned)(units * kCluster), 1, 1);
+  cfg.stream = st;
+  cfg.numAttrs = kCluster > 1 ? 1 : 0;
+  if (cudaLaunchKernelEx(&cfg, kernel, args) != cudaSuccess) return GQAOA_ECUDA;
+  return GQAOA_OK;
+}
+
+}  // namespace
+
+// Whether the cluster-resident adjoint takes B states of 2^n amplitudes:
+// 12 <= n <= 16, and at most 2^24 amplitudes in all. Each instance's rounds
+// then run back to back on one cluster, which beats the streaming passes
+// (one launch per round) while the instances fit a few waves of clusters;
+// beyond that the streaming passes, bound by HBM bandwidth, are faster
+// (1024 instances of 2^16 amplitudes, p = 32: 13.8 ms against 16.0 ms).
+bool adjoint_cluster_fits(int n, int B) {
+  return n >= 12 && n <= 16 && ((uint64_t)B << n) <= (1ull << 24);
+}
+
+// Objective and adjoint gradient of B rows of 2^n amplitudes (12 <= n <= 16)
+// in one launch (plus the FP32 mixer coefficients' conversion). phase,
+// alpha: the rows' tables ([B][p][256], [B][p]); record [B][p][4] and ckpt
+// [p][B][2^n] are workspace. objective: GQAOA_OBJ_P0 with target, or
+// GQAOA_OBJ_ENERGY.
+int adjoint_cluster(const uint8_t *cost, uint64_t cost_bstride, int n, int B, int p,
+                    const float2 *phase, const double2 *alpha, double *record, float2 *ckpt,
+                    int objective, unsigned target, double *value, double *dgamma,
+                    double *dbeta, cudaStream_t st) {
+  if (!adjoint_cluster_fits(n, B)) return GQAOA_ERANGE;
+  const uint64_t count = (uint64_t)B * (uint64_t)p;
+  const unsigned grid = (unsigned)(count < 256ull * 1024 ? (count + 255) / 256 : 1024);
+  adj_alpha_kernel<<<grid, 256, 0, st>>>(alpha, count, record);
+  GQ_CHECK_LAUNCH();
+  AdjArgs args = {cost, cost_bstride, phase, alpha, record, ckpt, value, dgamma, dbeta,
+                  n, p, B, objective, target};
+  switch (n) {
+    case 12: return launch_adjoint<256, 1>(args, st);
+    case 13: return launch_adjoint<512, 1>(args, st);
+    case 14: return launch_adjoint<512, 2>(args, st);
+    case 15: return launch_adjoint<512, 4>(args, st);
+    default: return launch_adjoint<512, 8>(args, st);
+  }
+}
+
+}  // namespace gq

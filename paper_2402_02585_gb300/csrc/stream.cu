@@ -1255,12 +1255,20 @@ static int evolve_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m,
   return GQAOA_OK;
 }
 
+bool adjoint_cluster_fits(int n, int B);
+int adjoint_cluster(const uint8_t *cost, uint64_t cost_bstride, int n, int B, int p,
+                    const float2 *phase, const double2 *alpha, double *record, float2 *ckpt,
+                    int objective, unsigned target, double *value, double *dgamma,
+                    double *dbeta, cudaStream_t st);
+
 static int grad_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m, int B,
                      const double *gammas, const double *betas, int p, int objective, double *value,
                      double *dgamma, double *dbeta, void *ws, size_t ws_bytes, cudaStream_t st) {
   int rc = check_common(n, m, B, p);
   if (rc) return rc;
   if (!cost || !gammas || !betas || !value || !dgamma || !dbeta || !ws) return GQAOA_EINVAL;
+  const bool streaming = (objective & GQAOA_GRAD_STREAMING) != 0;
+  objective &= ~GQAOA_GRAD_STREAMING;
   // GQAOA_OBJ_CLASS(c): the projector objective on cost class c (P0 is class 0)
   unsigned target = 0u;
   if (objective >= GQAOA_OBJ_CLASS(0) && objective <= GQAOA_OBJ_CLASS(255)) {
@@ -1290,6 +1298,9 @@ static int grad_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m, i
     GQ_CHECK_LAUNCH();
     return GQAOA_OK;
   }
+  if (!streaming && adjoint_cluster_fits(n, B))  // every round of a row on one cluster
+    return adjoint_cluster(cost, cost_bstride, n, B, p, w.phase, w.alpha, w.record, w.ckpt,
+                           objective, target, value, dgamma, dbeta, st);
   // forward: chi_k -> ckpt[k]; round 0 synthesises |+> (src unused)
   rc = run_forward(g, w, cost, cost_bstride, p, w.lambda, false, nullptr, w.ckpt, st);
   if (rc) return rc;

@@ -2,14 +2,16 @@
 benchmark's shape: n = 16, m = 67, p = 32 independent angle pairs drawn
 uniformly in [0, pi).
 
-At this size an instance spans 16 tiles of 4096 amplitudes, so several CTAs
-share it and each round's mixer sum is combined from several reduction
-records per instance (asserted through gqaoa_batched_geometry); the
-smaller-n gradient tests run one CTA per instance. Every instance's value
-and gradient is compared with the oracle's cost-class adjoint (exact
-dynamics, FP64) within the gradient tolerance of the other parity tests
-(1e-6 on P, 2e-5 on each angle's derivative), and some rows with FP64
-central differences (h = 1e-4) within 5e-5.
+At this size the default path holds each instance on one 8-CTA cluster for
+all its rounds (the cluster-resident adjoint); with GQAOA_GRAD_STREAMING the
+streaming passes run instead, where an instance spans 16 tiles of 4096
+amplitudes, so several CTAs share it and each round's mixer sum is combined
+from several reduction records per instance (asserted through
+gqaoa_batched_geometry). Every instance's value and gradient is compared
+with the oracle's cost-class adjoint (exact dynamics, FP64) within the
+gradient tolerance of the other parity tests (1e-6 on P, 2e-5 on each
+angle's derivative), and some rows with FP64 central differences
+(h = 1e-4) within 5e-5.
 """
 
 import numpy as np
@@ -44,19 +46,24 @@ def _angles(B, seed0):
     return G, Bt
 
 
-def test_batched_gradient_several_ctas_per_instance():
+@pytest.mark.parametrize("streaming", [False, True])
+def test_batched_gradient_several_ctas_per_instance(streaming):
     n, m, p, B = N_VARS, M_CLAUSES, P_ROUNDS, 64
-    for adjoint in (0, 1):
-        cpi, rec = C.gqaoa_batched_geometry(n, B, adjoint)
-        print(f"n={n} B={B} adjoint={adjoint}: {cpi} CTAs, {rec} records per instance")
-        assert cpi >= 2 and rec >= 2
     cost, hists = _instances(B, 500)
     G, Bt = _angles(B, 700)
-    opt = AngleOptimizer(cost, n, m, p)
-    opt.reset(G, Bt)
-    v = opt.evaluate().cpu().numpy()
-    dg = opt.grad[0].cpu().numpy()
-    db = opt.grad[1].cpu().numpy()
+    if streaming:
+        for adjoint in (0, 1):
+            cpi, rec = C.gqaoa_batched_geometry(n, B, adjoint)
+            print(f"n={n} B={B} adjoint={adjoint}: {cpi} CTAs, {rec} records per instance")
+            assert cpi >= 2 and rec >= 2
+        v, dg, db = (t.cpu().numpy() for t in core.grad_batched(
+            cost, n, m, G, Bt, C.GQAOA_OBJ_P0 | C.GQAOA_GRAD_STREAMING))
+    else:
+        opt = AngleOptimizer(cost, n, m, p)
+        opt.reset(G, Bt)
+        v = opt.evaluate().cpu().numpy()
+        dg = opt.grad[0].cpu().numpy()
+        db = opt.grad[1].cpu().numpy()
     for i in range(B):
         L, rdg, rdb = reduced.grad(hists[i], G[i], Bt[i], reduced.OBJ_P0)
         assert abs(v[i] - L) < V_TOL, (i, v[i], L)
