@@ -554,11 +554,42 @@ def run_grad(args, wl):
     clk = clocks.stop()
     el = start.elapsed_time(stop) / 1e3
     units = B * p * N * args.steps
-    # algorithmic bytes per step: forward 9 B (round 1) + 17 B (rounds 2..p)
-    # per amplitude, lambda init 17 B, backward 25 B per amplitude-round
-    alg = B * N * (9 + 17 * (p - 1) + 17 + 25 * p)
+    cluster = 12 <= n <= 16  # the library's cluster-resident adjoint (gqaoa.h)
+    if cluster:
+        # algorithmic bytes per step: the cost table read once (1 B per
+        # amplitude) and every checkpoint written forward and read backward
+        # (8 + 8 B per amplitude-round); the state and lambda stay on chip
+        alg = B * N * (1 + 16 * p)
+        kernel = ("adjoint_cluster_kernel (one cluster per instance for all rounds, 16 B per "
+                  "amplitude-round of checkpoints; bound by its per-round cluster reductions, "
+                  "not by HBM; streaming_grad below: the streaming passes, 42 B per "
+                  "amplitude-round, timed on the same angles)")
+    else:
+        # forward 9 B (round 1) + 17 B (rounds 2..p) per amplitude, lambda
+        # init 17 B, backward 25 B per amplitude-round
+        alg = B * N * (9 + 17 * (p - 1) + 17 + 25 * p)
+        kernel = "forward rounds + backward rounds (mean over the step)"
     achieved = alg * args.steps / el / 1e9
     peak, kind = hbm_peak()
+    streaming = None
+    if cluster:
+        # the same gradient call by the streaming passes, for context
+        code = C.GQAOA_OBJ_P0 | C.GQAOA_GRAD_STREAMING
+        th = opt.theta
+        for _ in range(2):
+            core.grad_batched(costs, n, m, th[0], th[1], code, ws=opt.ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            core.grad_batched(costs, n, m, th[0], th[1], code, ws=opt.ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        s_alg = B * N * (9 + 17 * (p - 1) + 17 + 25 * p)
+        streaming = {"ms_per_call": ms, "hbm_gbs": s_alg / (ms / 1e3) / 1e9,
+                     "frac": s_alg / (ms / 1e3) / 1e9 / peak,
+                     "note": "gradient call only (no Adam step), GQAOA_GRAD_STREAMING"}
     v = opt.evaluate().cpu().numpy()
     line = {"metric": METRIC, "value": units / el, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
@@ -569,10 +600,11 @@ def run_grad(args, wl):
                                             f"{(p * B * N * 8) >> 20} MiB checkpoints)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": kind,
-                         "kernel": "forward rounds + backward rounds (mean over the step)"},
+                         "kernel": kernel},
             "adam_steps_per_s": args.steps / el, "mean_P_after": float(v.mean()),
+            "streaming_grad": streaming,
             "cpu_baseline": cpu_grad_baseline(wl),
-            "gpu_launches": (p + 1 + p + 1 + 1 + 1) * args.steps, "clocks": clk}
+            "gpu_launches": (core.grad_launches(n, p) + 1) * args.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 

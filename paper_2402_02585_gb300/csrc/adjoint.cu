@@ -7,14 +7,13 @@
 // cluster owns one instance (row) for the whole call: each thread keeps 16
 // amplitudes in registers, the forward rounds write the checkpoints chi_k
 // (each thread later rereads only its own), and the backward rounds follow
-// in the same launch. A round's sums go warp (double-float butterfly) -> CTA
-// (warp 0 over the warp partials) -> cluster (every CTA's partial pushed into
+// in the same launch. A round's sums go warp (FP32 butterfly) -> CTA (warp 0
+// over the warp partials, double-float) -> cluster (every CTA's partial pushed into
 // the shared memory of every peer, one cluster barrier, every warp summing
 // the partials in rank order), so every warp of every CTA holds the same
-// totals bit for bit and no further barrier is needed. The arithmetic is the
-// small-state kernels' (double-float sums, FP32 amplitudes); the mixer
-// coefficients are formed in FP32 from the double-float sums, and FP64 is
-// used only by the thread that writes a row's records and gradients.
+// totals bit for bit and no further barrier is needed. FP32 amplitudes; the mixer
+// coefficients are formed in FP32 from the double-float sums, and the rounds
+// use no FP64: a closing kernel forms the gradients from the sums they left.
 //
 // Forward round k: chi_k = T_k[c] psi_{k-1} (checkpointed), S_k = sum chi_k,
 // a_k = alpha_k S_k / N, psi_k = chi_k + a_k. Backward, from
@@ -43,7 +42,7 @@ struct AdjArgs {
   uint64_t cost_bstride;
   const float2 *phase;    // [B][p][256]
   const double2 *alpha;   // [B][p]
-  double *record;         // [B][p][4]: S_k (re, im) of the forward
+  double *record;         // [B][p][4]: S_k as double-float pairs, float alpha_k, G_k
   float2 *ckpt;           // [p][B][N]
   double *value;          // [B]
   double *dgamma;         // [B][p]
@@ -54,19 +53,6 @@ struct AdjArgs {
   int objective;          // GQAOA_OBJ_P0 (projector on `target`) or GQAOA_OBJ_ENERGY
   unsigned target;
 };
-
-// Double-float sum over the warp's lanes (every lane ends with the same sum).
-__device__ __forceinline__ void adj_df_warp(float &hi, float &lo) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-    float s, e;
-    two_sum(hi, h2, s, e);
-    hi = s;
-    lo = __fadd_rn(__fadd_rn(lo, l2), e);
-  }
-}
 
 // (hi, lo) += x in double-float arithmetic.
 __device__ __forceinline__ void adj_df_add(float &hi, float &lo, float x) {
@@ -84,11 +70,31 @@ __device__ __forceinline__ void adj_st_dsmem(float2 *p, unsigned rank, float2 v)
                : "memory");
 }
 
-// Cluster-wide double-float sums of kV <= kAdjVals values: v[k] holds this thread's
-// (hi, lo) on entry and the cluster's total on exit, the same in every
-// thread. buf alternates between calls: the partials of one call are read
-// while the next call's are written.
-template <int kThreads, int kCluster, int kV>
+// Double-float sum over each aligned group of kG lanes (kG a power of two up
+// to 32): every lane ends with its group's sum, the same bits in every group
+// that holds the same values (TwoSum's error term does not depend on the
+// order of its operands).
+template <int kG>
+__device__ __forceinline__ void adj_df_group(float &hi, float &lo) {
+#pragma unroll
+  for (int o = kG / 2; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    float s, e;
+    two_sum(hi, h2, s, e);
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, l2), e);
+  }
+}
+
+// Cluster-wide sums of kV <= kAdjVals values: v[k] holds this thread's
+// partial on entry (an FP32 value in .x, or a double-float pair with
+// kWarpDF); on exit v[k] is the cluster's total as a double-float pair, the
+// same in every thread. The warp's lanes are summed in FP32 (a butterfly;
+// double-float with kWarpDF), the warps and then the CTAs in double-float.
+// buf alternates between calls: the partials of one call are read while the
+// next call's are written.
+template <int kThreads, int kCluster, int kV, bool kWarpDF = false>
 __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
                                                 float2 (*s_wp)[kThreads / 32][kAdjVals],
                                                 float2 (*s_ps)[kCluster][kAdjVals], int buf,
@@ -96,7 +102,16 @@ __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
   constexpr int kW = kThreads / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < kV; ++k) adj_df_warp(v[k].x, v[k].y);
+  for (int k = 0; k < kV; ++k) {
+    if (kWarpDF) {
+      adj_df_group<32>(v[k].x, v[k].y);
+    } else {
+      float x = v[k].x;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      v[k] = make_float2(x, 0.f);
+    }
+  }
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < kV; ++k) s_wp[buf][warp][k] = v[k];
@@ -105,8 +120,9 @@ __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
   if (warp == 0) {
 #pragma unroll
     for (int k = 0; k < kV; ++k) {
-      float2 d = lane < kW ? s_wp[buf][lane][k] : make_float2(0.f, 0.f);
-      adj_df_warp(d.x, d.y);
+      // every group of kW lanes holds the kW warp partials
+      float2 d = s_wp[buf][lane & (kW - 1)][k];
+      adj_df_group<kW>(d.x, d.y);
       if (kCluster == 1) {
         if (lane == 0) s_ps[buf][0][k] = d;
       } else if (lane < kCluster) {
@@ -120,8 +136,8 @@ __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
     __syncthreads();
 #pragma unroll
   for (int k = 0; k < kV; ++k) {
-    float2 d = lane < kCluster ? s_ps[buf][lane][k] : make_float2(0.f, 0.f);
-    adj_df_warp(d.x, d.y);
+    float2 d = s_ps[buf][lane & (kCluster - 1)][k];
+    adj_df_group<kCluster>(d.x, d.y);
     v[k] = d;
   }
 }
@@ -137,17 +153,16 @@ __global__ void adj_alpha_kernel(const double2 *__restrict__ alpha, uint64_t cou
   }
 }
 
-// Pull one 2 KB phase table into L1 (16 threads, one 128-byte line each).
-__device__ __forceinline__ void adj_prefetch_table(const float2 *T) {
-  if (threadIdx.x < 16) asm volatile("prefetch.global.L1 [%0];" ::"l"(T + 16 * threadIdx.x));
-}
-
 template <int kThreads, int kCluster>
 __global__ void __launch_bounds__(kThreads, 512 / kThreads)
 adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
   constexpr int kW = kThreads / 32;
   __shared__ float2 s_wp[2][kW][kAdjVals];
   __shared__ float2 s_ps[2][kCluster][kAdjVals];
+  // phase tables, double-buffered: a round reads s_T[k & 1] while its table
+  // for two rounds on is in flight in a register (tn) of threads 0..255
+  __shared__ float2 s_T[2][256];
+  const bool tabler = threadIdx.x < 256;
   const unsigned rank = kCluster > 1 ? cluster_ctarank() : 0u;
   const uint64_t cl = blockIdx.x / kCluster, ncl = gridDim.x / kCluster;
   const uint64_t N = 1ull << a.n;
@@ -166,10 +181,17 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       c[j] = cost[j * kThreads];
       s[j] = make_float2(amp0, 0.f);
     }
+    const float2 *tab = a.phase + b * (uint64_t)a.p * 256 + threadIdx.x;  // + 256 k: round k
+    float2 tn = make_float2(0.f, 0.f);
+    if (tabler) {
+      s_T[0][threadIdx.x] = tab[0];
+      if (a.p > 1) tn = tab[256];
+    }
+    __syncthreads();
     // forward: chi_k into the checkpoints, psi_k = chi_k + a_k
     for (int k = 0; k < a.p; ++k) {
       const uint64_t bk = b * (uint64_t)a.p + k;
-      const float2 *T = a.phase + bk * 256;
+      const float2 *T = s_T[k & 1];
       float2 *ck = a.ckpt + ((uint64_t)k * a.B + b) * N + z0;
       float sr = 0.f, si = 0.f;
 #pragma unroll
@@ -179,7 +201,12 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
         sr += s[j].x;
         si += s[j].y;
       }
-      adj_prefetch_table(k + 1 < a.p ? T + 256 : a.phase + (b * (uint64_t)a.p + a.p - 1) * 256);
+      // round k + 1's table (its buffer was last read in round k - 1, before
+      // that round's barriers; this round's barrier publishes it)
+      if (tabler) {
+        if (k + 1 < a.p) s_T[(k + 1) & 1][threadIdx.x] = tn;
+        if (k + 2 < a.p) tn = tab[(uint64_t)(k + 2) * 256];
+      }
       float2 v[kAdjVals] = {make_float2(sr, 0.f), make_float2(si, 0.f), make_float2(0.f, 0.f)};
       adj_cluster_sum<kThreads, kCluster, 2>(v, s_wp, s_ps, buf, rank);
       buf ^= 1;
@@ -188,10 +215,8 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       const float2 af = make_float2((al.x * Sr - al.y * Si) * inv_n, (al.x * Si + al.y * Sr) * inv_n);
 #pragma unroll
       for (int j = 0; j < kAdjPer; ++j) s[j] = make_float2(s[j].x + af.x, s[j].y + af.y);
-      if (writer) {
-        a.record[4 * bk] = (double)v[0].x + (double)v[0].y;
-        a.record[4 * bk + 1] = (double)v[1].x + (double)v[1].y;
-      }
+      if (writer)  // S_k as double-float pairs (adj_finalize_kernel reads them)
+        *reinterpret_cast<float4 *>(a.record + 4 * bk) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
     }
     // lambda_p = O psi_p, the objective sum_z O |psi_p|^2 (double-float:
     // each square split exactly by an FMA) and L = sum lambda
@@ -221,8 +246,11 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
 #pragma unroll
       for (int j = 0; j < kAdjPer; ++j) x[j] = ck[j * kThreads];
     }
+    // the backward rounds read the tables in reverse: s_T[(p - 1) & 1] still
+    // holds round p - 1's; round p - 2's is in flight
+    if (tabler && a.p > 1) tn = tab[(uint64_t)(a.p - 2) * 256];
     float2 v[kAdjVals] = {make_float2(vh, vl), make_float2(lr, 0.f), make_float2(li, 0.f)};
-    adj_cluster_sum<kThreads, kCluster, 3>(v, s_wp, s_ps, buf, rank);
+    adj_cluster_sum<kThreads, kCluster, 3, true>(v, s_wp, s_ps, buf, rank);
     buf ^= 1;
     if (writer) a.value[b] = (double)v[0].x + (double)v[0].y;
     // backward rounds
@@ -232,7 +260,7 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       const float Lr = Ld.x + Ld.y, Li = Li2.x + Li2.y;
       const float2 al = *reinterpret_cast<const float2 *>(a.record + 4 * bk + 2);
       const float2 bv = make_float2((al.x * Lr + al.y * Li) * inv_n, (al.x * Li - al.y * Lr) * inv_n);
-      const float2 *T = a.phase + bk * 256;
+      const float2 *T = s_T[k & 1];
       float g = 0.f, nlr = 0.f, nli = 0.f;
 #pragma unroll
       for (int j = 0; j < kAdjPer; ++j) {
@@ -247,25 +275,48 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
         const float2 *ck = a.ckpt + ((uint64_t)(k - 1) * a.B + b) * N + z0;
 #pragma unroll
         for (int j = 0; j < kAdjPer; ++j) x[j] = ck[j * kThreads];
-        adj_prefetch_table(T - 256);
+      }
+      // round k - 1's table (its buffer was last read in round k + 1, or in
+      // forward round p - 2 for k = p - 1)
+      if (tabler) {
+        if (k >= 1) s_T[(k - 1) & 1][threadIdx.x] = tn;
+        if (k >= 2) tn = tab[(uint64_t)(k - 2) * 256];
       }
       v[0] = make_float2(g, 0.f);
       v[1] = make_float2(nlr, 0.f);
       v[2] = make_float2(nli, 0.f);
       adj_cluster_sum<kThreads, kCluster, 3>(v, s_wp, s_ps, buf, rank);
       buf ^= 1;
-      if (writer) {
-        const double2 ald = a.alpha[bk];
-        const double Sre = a.record[4 * bk] / (double)N, Sim = a.record[4 * bk + 1] / (double)N;
-        const double er = ald.x + 1.0, ei = ald.y;  // e^{-i beta_k}
-        const double qr = er * Sre - ei * Sim, qi = er * Sim + ei * Sre;
-        const double Lrd = (double)Ld.x + (double)Ld.y, Lid = (double)Li2.x + (double)Li2.y;
-        a.dbeta[bk] = 2.0 * (qi * Lrd - qr * Lid);
-        a.dgamma[bk] = 2.0 * ((double)v[0].x + (double)v[0].y);
+      if (writer) {  // the round's sums, finished in FP64 by adj_finalize_kernel
+        *reinterpret_cast<float2 *>(a.record + 4 * bk + 3) = v[0];  // G_k
+        *reinterpret_cast<float2 *>(a.dbeta + bk) = Ld;             // L_k (re)
+        *reinterpret_cast<float2 *>(a.dgamma + bk) = Li2;           // L_k (im)
       }
     }
   }
   if (kCluster > 1) cluster_sync();  // no CTA leaves while a peer may still store into it
+}
+
+// The gradients in FP64 from the double-float sums the rounds left (one
+// thread per instance and round, off the rounds' critical path):
+// dE/dbeta_k = 2 Im(conj(e^{-i beta_k} S_k / N) L_k), dE/dgamma_k = 2 G_k.
+__global__ void adj_finalize_kernel(const double2 *__restrict__ alpha, const double *record,
+                                    uint64_t count, int n, double *dgamma, double *dbeta) {
+  const double inv_n = ldexp(1.0, -n);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const float4 S = *reinterpret_cast<const float4 *>(record + 4 * i);
+    const float2 G = *reinterpret_cast<const float2 *>(record + 4 * i + 3);
+    const float2 Lr = *reinterpret_cast<const float2 *>(dbeta + i);
+    const float2 Li = *reinterpret_cast<const float2 *>(dgamma + i);
+    const double Sre = ((double)S.x + (double)S.y) * inv_n, Sim = ((double)S.z + (double)S.w) * inv_n;
+    const double2 al = alpha[i];
+    const double er = al.x + 1.0, ei = al.y;  // e^{-i beta_k}
+    const double qr = er * Sre - ei * Sim, qi = er * Sim + ei * Sre;
+    const double Lrd = (double)Lr.x + (double)Lr.y, Lid = (double)Li.x + (double)Li.y;
+    dbeta[i] = 2.0 * (qi * Lrd - qr * Lid);
+    dgamma[i] = 2.0 * ((double)G.x + (double)G.y);
+  }
 }
 
 template <int kThreads, int kCluster>
@@ -303,15 +354,11 @@ int launch_adjoint(const AdjArgs &args, cudaStream_t st) {
 
 }  // namespace
 
-// Whether the cluster-resident adjoint takes B states of 2^n amplitudes:
-// 12 <= n <= 16, and at most 2^24 amplitudes in all. Each instance's rounds
-// then run back to back on one cluster, which beats the streaming passes
-// (one launch per round) while the instances fit a few waves of clusters;
-// beyond that the streaming passes, bound by HBM bandwidth, are faster
-// (1024 instances of 2^16 amplitudes, p = 32: 13.8 ms against 16.0 ms).
-bool adjoint_cluster_fits(int n, int B) {
-  return n >= 12 && n <= 16 && ((uint64_t)B << n) <= (1ull << 24);
-}
+// Whether the cluster-resident adjoint takes B states of 2^n amplitudes
+// (12 <= n <= 16, any batch: each instance's rounds run back to back on one
+// cluster and move only the checkpoints through memory, which beats the
+// streaming passes at every batch size measured).
+bool adjoint_cluster_fits(int n, int B) { return n >= 12 && n <= 16 && B >= 1; }
 
 // Objective and adjoint gradient of B rows of 2^n amplitudes (12 <= n <= 16)
 // in one launch (plus the FP32 mixer coefficients' conversion). phase,
@@ -329,13 +376,18 @@ int adjoint_cluster(const uint8_t *cost, uint64_t cost_bstride, int n, int B, in
   GQ_CHECK_LAUNCH();
   AdjArgs args = {cost, cost_bstride, phase, alpha, record, ckpt, value, dgamma, dbeta,
                   n, p, B, objective, target};
+  int rc;
   switch (n) {
-    case 12: return launch_adjoint<256, 1>(args, st);
-    case 13: return launch_adjoint<512, 1>(args, st);
-    case 14: return launch_adjoint<512, 2>(args, st);
-    case 15: return launch_adjoint<512, 4>(args, st);
-    default: return launch_adjoint<512, 8>(args, st);
+    case 12: rc = launch_adjoint<256, 1>(args, st); break;
+    case 13: rc = launch_adjoint<512, 1>(args, st); break;
+    case 14: rc = launch_adjoint<512, 2>(args, st); break;
+    case 15: rc = launch_adjoint<512, 4>(args, st); break;
+    default: rc = launch_adjoint<512, 8>(args, st); break;
   }
+  if (rc) return rc;
+  adj_finalize_kernel<<<grid, 256, 0, st>>>(alpha, record, count, n, dgamma, dbeta);
+  GQ_CHECK_LAUNCH();
+  return GQAOA_OK;
 }
 
 }  // namespace gq

@@ -56,9 +56,7 @@ class AngleOptimizer:
                              core.objective_code(self.objective), self.value.data_ptr(),
                              self.grad[0].data_ptr(), self.grad[1].data_ptr(), self.ws.data_ptr(),
                              self.ws.numel(), s)
-        # phase tables + one-CTA forward + adjoint below a tile, else phase
-        # tables, p forward rounds, lambda init, p adjoint rounds, finalize
-        self.launches += 3 if (1 << self.n) < 4096 else 2 * self.p + 3
+        self.launches += core.grad_launches(self.n, self.p)
         self.amp_evaluations += self.B << self.n
         return self.value
 

@@ -130,8 +130,8 @@ class _EnergyGrad:
     """<H_P> and its adjoint gradient at a fixed depth p with resident
     buffers: the angles go to the device in one copy from pinned host memory
     and the value and both gradients come back in one. An L-BFGS-B search
-    makes hundreds of these small calls and each is 2p + 3 kernel launches
-    on the streaming path, so after one direct call the library call is
+    makes hundreds of these small calls (each several kernel launches; 2p + 3
+    on the streaming path above 2^16 amplitudes), so after one direct call the library call is
     captured once into a CUDA graph and every further evaluation is one copy
     up, one graph launch and one copy down (the same kernels in the same
     order, so the same results)."""
@@ -246,7 +246,7 @@ class _DepthBatch:
         v = self.a_out[:B]
         gr = self.a_out[B:nb].reshape(2, B, P)
         prot.evaluations += B
-        prot.launches += 3 if prot._small else 2 * P + 3
+        prot.launches += core.grad_launches(prot.n, P)
         return [(float(v[i]), gr[0, i, P - k:].copy(), gr[1, i, P - k:].copy())
                 for i, (k, _, _) in enumerate(rows)]
 
@@ -451,7 +451,7 @@ class Protocol:
             with _GATE.work():
                 call = self._grad_calls[p] = _EnergyGrad(self, p)
         self.evaluations += 1
-        self.launches += 3 if self._small else 2 * p + 3
+        self.launches += core.grad_launches(self.n, p)
         return call(gammas, betas)
 
     def refine(self, gammas0, betas0, single: bool):
