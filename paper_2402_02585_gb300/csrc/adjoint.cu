@@ -94,11 +94,18 @@ __device__ __forceinline__ void adj_df_group(float &hi, float &lo) {
 // double-float with kWarpDF), the warps and then the CTAs in double-float.
 // buf alternates between calls: the partials of one call are read while the
 // next call's are written.
-template <int kThreads, int kCluster, int kV, bool kWarpDF = false>
+// between() runs after this thread's arrival at the cluster barrier and
+// before its wait: the barrier's release then covers only what came before
+// (the partials), and global stores placed in between() do not hold it up.
+struct AdjNothing {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+template <int kThreads, int kCluster, int kV, bool kWarpDF = false, typename Between = AdjNothing>
 __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
                                                 float2 (*s_wp)[kThreads / 32][kAdjVals],
                                                 float2 (*s_ps)[kCluster][kAdjVals], int buf,
-                                                unsigned rank) {
+                                                unsigned rank, Between between = Between()) {
   constexpr int kW = kThreads / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -130,10 +137,15 @@ __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
       }
     }
   }
-  if (kCluster > 1)
-    cluster_sync();  // release/acquire: every CTA's partial visible locally
-  else
+  if (kCluster > 1) {
+    // release/acquire: every CTA's partial visible locally
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    between();
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  } else {
     __syncthreads();
+    between();
+  }
 #pragma unroll
   for (int k = 0; k < kV; ++k) {
     float2 d = s_ps[buf][lane & (kCluster - 1)][k];
@@ -197,7 +209,6 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
 #pragma unroll
       for (int j = 0; j < kAdjPer; ++j) {
         s[j] = cmul(T[c[j]], s[j]);
-        ck[j * kThreads] = s[j];
         sr += s[j].x;
         si += s[j].y;
       }
@@ -208,7 +219,11 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
         if (k + 2 < a.p) tn = tab[(uint64_t)(k + 2) * 256];
       }
       float2 v[kAdjVals] = {make_float2(sr, 0.f), make_float2(si, 0.f), make_float2(0.f, 0.f)};
-      adj_cluster_sum<kThreads, kCluster, 2>(v, s_wp, s_ps, buf, rank);
+      // the checkpoints chi_k, stored while the cluster barrier completes
+      adj_cluster_sum<kThreads, kCluster, 2>(v, s_wp, s_ps, buf, rank, [&]() {
+#pragma unroll
+        for (int j = 0; j < kAdjPer; ++j) ck[j * kThreads] = s[j];
+      });
       buf ^= 1;
       const float Sr = v[0].x + v[0].y, Si = v[1].x + v[1].y;
       const float2 al = *reinterpret_cast<const float2 *>(a.record + 4 * bk + 2);
@@ -271,11 +286,6 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
         nlr += l[j].x;
         nli += l[j].y;
       }
-      if (k > 0) {
-        const float2 *ck = a.ckpt + ((uint64_t)(k - 1) * a.B + b) * N + z0;
-#pragma unroll
-        for (int j = 0; j < kAdjPer; ++j) x[j] = ck[j * kThreads];
-      }
       // round k - 1's table (its buffer was last read in round k + 1, or in
       // forward round p - 2 for k = p - 1)
       if (tabler) {
@@ -285,7 +295,14 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       v[0] = make_float2(g, 0.f);
       v[1] = make_float2(nlr, 0.f);
       v[2] = make_float2(nli, 0.f);
-      adj_cluster_sum<kThreads, kCluster, 3>(v, s_wp, s_ps, buf, rank);
+      // round k - 1's checkpoints, loaded while the cluster barrier completes
+      adj_cluster_sum<kThreads, kCluster, 3>(v, s_wp, s_ps, buf, rank, [&]() {
+        if (k > 0) {
+          const float2 *ck = a.ckpt + ((uint64_t)(k - 1) * a.B + b) * N + z0;
+#pragma unroll
+          for (int j = 0; j < kAdjPer; ++j) x[j] = ck[j * kThreads];
+        }
+      });
       buf ^= 1;
       if (writer) {  // the round's sums, finished in FP64 by adj_finalize_kernel
         *reinterpret_cast<float2 *>(a.record + 4 * bk + 3) = v[0];  // G_k
