@@ -554,7 +554,7 @@ def run_grad(args, wl):
     clk = clocks.stop()
     el = start.elapsed_time(stop) / 1e3
     units = B * p * N * args.steps
-    cluster = 12 <= n <= 16  # the library's cluster-resident adjoint (gqaoa.h)
+    cluster = 10 <= n <= 16  # the library's cluster-resident adjoint (gqaoa.h)
     if cluster:
         # algorithmic bytes per step: the cost table read once (1 B per
         # amplitude) and every checkpoint written forward and read backward

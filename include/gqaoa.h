@@ -71,9 +71,10 @@ extern "C" {
  * GQAOA_OBJ_CLASS(0) is GQAOA_OBJ_P0 */
 #define GQAOA_OBJ_CLASS(c) (256 + ((int)(c) & 0xFF))
 /* OR-ed into the objective of gqaoa_grad / gqaoa_grad_batched: take the
- * streaming passes (one launch per round and direction) also where the
- * cluster-resident adjoint would run (12 <= n <= 16); the two agree to the
- * rounding of their sums. */
+ * streaming passes (one launch per round and direction; for n <= 11 the
+ * one-CTA forward and adjoint kernels) also where the cluster-resident
+ * adjoint would run (10 <= n <= 16); they agree to the rounding of their
+ * sums. */
 #define GQAOA_GRAD_STREAMING (1 << 16)
 
 /* Human-readable name of a status code (static storage, never NULL). */
@@ -229,11 +230,12 @@ int gqaoa_grad_workspace_size(int n, int p, size_t *bytes);
  * cost device uint8 [2^n]; gammas, betas device double [p];
  * value  device double [1] written: L;
  * dgamma, dbeta device double [p] written.
- * Paths: one CTA per instance for n <= 11; for 12 <= n <= 16 one
- * thread-block cluster per instance holds the state on chip for all rounds,
- * forward and backward, in one launch (1 to 8 CTAs of 256-512 threads, 16
- * amplitudes per thread; the checkpoints still go to the workspace); for
- * n >= 17, or with GQAOA_GRAD_STREAMING, streaming passes over HBM.
+ * Paths: for 10 <= n <= 16 one CTA (64-512 threads) or thread-block cluster
+ * (2-8 CTAs of 512 threads) per instance holds the state on chip for all
+ * rounds, forward and backward, in one launch (16 amplitudes per thread; the
+ * checkpoints still go to the workspace); otherwise, or with
+ * GQAOA_GRAD_STREAMING, one CTA per instance for n <= 11 (forward and
+ * adjoint kernels) and streaming passes over HBM above.
  */
 int gqaoa_grad(const uint8_t *cost, int n, int m, const double *gammas, const double *betas,
                int p, int objective, double *value, double *dgamma, double *dbeta, void *ws,

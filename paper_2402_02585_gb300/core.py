@@ -193,15 +193,15 @@ def grad(cost: torch.Tensor, n: int, m: int, gammas, betas, objective: str = "p0
 
 def grad_launches(n: int, p: int, streaming: bool = False) -> int:
     """Kernels one gqaoa_grad(_batched) call launches, following the
-    library's choice of path: phase tables plus a one-CTA forward and adjoint
-    below 4096 amplitudes; phase tables, the mixer coefficients' conversion,
-    the cluster-resident adjoint and its closing kernel for 12 <= n <= 16;
-    else phase tables, p forward rounds, lambda init, p adjoint rounds and
-    the finalize (also with GQAOA_GRAD_STREAMING)."""
+    library's choice of path: phase tables, the mixer coefficients'
+    conversion, the cluster-resident adjoint and its closing kernel for
+    10 <= n <= 16; otherwise (or with GQAOA_GRAD_STREAMING) phase tables plus
+    a one-CTA forward and adjoint below 4096 amplitudes, else phase tables,
+    p forward rounds, lambda init, p adjoint rounds and the finalize."""
+    if 10 <= n <= 16 and not streaming:
+        return 4
     if (1 << n) < 4096:
         return 3
-    if 12 <= n <= 16 and not streaming:
-        return 4
     return 2 * p + 3
 
 

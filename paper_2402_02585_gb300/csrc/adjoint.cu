@@ -1,5 +1,5 @@
 // Cluster-resident adjoint gradient (Eq. 3 rounds, forward then backward,
-// for states of 2^12..2^16 amplitudes).
+// for states of 2^10..2^16 amplitudes).
 //
 // The streaming adjoint makes one launch per round and direction; for a
 // state of at most 2^16 amplitudes a round is a few microseconds of work on
@@ -172,7 +172,9 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
   __shared__ float2 s_wp[2][kW][kAdjVals];
   __shared__ float2 s_ps[2][kCluster][kAdjVals];
   // phase tables, double-buffered: a round reads s_T[k & 1] while its table
-  // for two rounds on is in flight in a register (tn) of threads 0..255
+  // for two rounds on is in flight in registers (tn) of threads 0..255, each
+  // holding kTab entries (t, t + kThreads, ...)
+  constexpr int kTab = kThreads >= 256 ? 1 : 256 / kThreads;
   __shared__ float2 s_T[2][256];
   const bool tabler = threadIdx.x < 256;
   const unsigned rank = kCluster > 1 ? cluster_ctarank() : 0u;
@@ -194,10 +196,13 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       s[j] = make_float2(amp0, 0.f);
     }
     const float2 *tab = a.phase + b * (uint64_t)a.p * 256 + threadIdx.x;  // + 256 k: round k
-    float2 tn = make_float2(0.f, 0.f);
+    float2 tn[kTab];
     if (tabler) {
-      s_T[0][threadIdx.x] = tab[0];
-      if (a.p > 1) tn = tab[256];
+#pragma unroll
+      for (int i = 0; i < kTab; ++i) {
+        s_T[0][threadIdx.x + i * kThreads] = tab[i * kThreads];
+        tn[i] = a.p > 1 ? tab[256 + i * kThreads] : make_float2(0.f, 0.f);
+      }
     }
     __syncthreads();
     // forward: chi_k into the checkpoints, psi_k = chi_k + a_k
@@ -215,8 +220,11 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       // round k + 1's table (its buffer was last read in round k - 1, before
       // that round's barriers; this round's barrier publishes it)
       if (tabler) {
-        if (k + 1 < a.p) s_T[(k + 1) & 1][threadIdx.x] = tn;
-        if (k + 2 < a.p) tn = tab[(uint64_t)(k + 2) * 256];
+#pragma unroll
+        for (int i = 0; i < kTab; ++i) {
+          if (k + 1 < a.p) s_T[(k + 1) & 1][threadIdx.x + i * kThreads] = tn[i];
+          if (k + 2 < a.p) tn[i] = tab[(uint64_t)(k + 2) * 256 + i * kThreads];
+        }
       }
       float2 v[kAdjVals] = {make_float2(sr, 0.f), make_float2(si, 0.f), make_float2(0.f, 0.f)};
       // the checkpoints chi_k, stored while the cluster barrier completes
@@ -263,7 +271,10 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
     }
     // the backward rounds read the tables in reverse: s_T[(p - 1) & 1] still
     // holds round p - 1's; round p - 2's is in flight
-    if (tabler && a.p > 1) tn = tab[(uint64_t)(a.p - 2) * 256];
+    if (tabler && a.p > 1) {
+#pragma unroll
+      for (int i = 0; i < kTab; ++i) tn[i] = tab[(uint64_t)(a.p - 2) * 256 + i * kThreads];
+    }
     float2 v[kAdjVals] = {make_float2(vh, vl), make_float2(lr, 0.f), make_float2(li, 0.f)};
     adj_cluster_sum<kThreads, kCluster, 3, true>(v, s_wp, s_ps, buf, rank);
     buf ^= 1;
@@ -289,8 +300,11 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       // round k - 1's table (its buffer was last read in round k + 1, or in
       // forward round p - 2 for k = p - 1)
       if (tabler) {
-        if (k >= 1) s_T[(k - 1) & 1][threadIdx.x] = tn;
-        if (k >= 2) tn = tab[(uint64_t)(k - 2) * 256];
+#pragma unroll
+        for (int i = 0; i < kTab; ++i) {
+          if (k >= 1) s_T[(k - 1) & 1][threadIdx.x + i * kThreads] = tn[i];
+          if (k >= 2) tn[i] = tab[(uint64_t)(k - 2) * 256 + i * kThreads];
+        }
       }
       v[0] = make_float2(g, 0.f);
       v[1] = make_float2(nlr, 0.f);
@@ -372,12 +386,12 @@ int launch_adjoint(const AdjArgs &args, cudaStream_t st) {
 }  // namespace
 
 // Whether the cluster-resident adjoint takes B states of 2^n amplitudes
-// (12 <= n <= 16, any batch: each instance's rounds run back to back on one
+// (10 <= n <= 16, any batch: each instance's rounds run back to back on one
 // cluster and move only the checkpoints through memory, which beats the
 // streaming passes at every batch size measured).
-bool adjoint_cluster_fits(int n, int B) { return n >= 12 && n <= 16 && B >= 1; }
+bool adjoint_cluster_fits(int n, int B) { return n >= 10 && n <= 16 && B >= 1; }
 
-// Objective and adjoint gradient of B rows of 2^n amplitudes (12 <= n <= 16)
+// Objective and adjoint gradient of B rows of 2^n amplitudes (10 <= n <= 16)
 // in one launch (plus the FP32 mixer coefficients' conversion). phase,
 // alpha: the rows' tables ([B][p][256], [B][p]); record [B][p][4] and ckpt
 // [p][B][2^n] are workspace. objective: GQAOA_OBJ_P0 with target, or
@@ -395,6 +409,8 @@ int adjoint_cluster(const uint8_t *cost, uint64_t cost_bstride, int n, int B, in
                   n, p, B, objective, target};
   int rc;
   switch (n) {
+    case 10: rc = launch_adjoint<64, 1>(args, st); break;
+    case 11: rc = launch_adjoint<128, 1>(args, st); break;
     case 12: rc = launch_adjoint<256, 1>(args, st); break;
     case 13: rc = launch_adjoint<512, 1>(args, st); break;
     case 14: rc = launch_adjoint<512, 2>(args, st); break;

@@ -1289,6 +1289,9 @@ static int grad_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m, i
   ws_layout(g, p, true, static_cast<char *>(ws), &w, maxp);
   rc = launch_phase_tables(gammas, betas, (int64_t)B * p, w, st);
   if (rc) return rc;
+  if (!streaming && adjoint_cluster_fits(n, B))  // every round of a row on one cluster
+    return adjoint_cluster(cost, cost_bstride, n, B, p, w.phase, w.alpha, w.record, w.ckpt,
+                           objective, target, value, dgamma, dbeta, st);
   if (g.small) {
     SmallArgs sa = {cost, cost_bstride, n, p, w.phase, w.alpha, w.lambda, false, nullptr,
                     nullptr, w.record, w.ckpt, B, target};
@@ -1298,9 +1301,6 @@ static int grad_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m, i
     GQ_CHECK_LAUNCH();
     return GQAOA_OK;
   }
-  if (!streaming && adjoint_cluster_fits(n, B))  // every round of a row on one cluster
-    return adjoint_cluster(cost, cost_bstride, n, B, p, w.phase, w.alpha, w.record, w.ckpt,
-                           objective, target, value, dgamma, dbeta, st);
   // forward: chi_k -> ckpt[k]; round 0 synthesises |+> (src unused)
   rc = run_forward(g, w, cost, cost_bstride, p, w.lambda, false, nullptr, w.ckpt, st);
   if (rc) return rc;

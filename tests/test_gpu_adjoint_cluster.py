@@ -1,10 +1,11 @@
-"""The cluster-resident adjoint (gqaoa_grad_batched for 12 <= n <= 16: one
-thread-block cluster holds an instance for all its forward and backward
-rounds) against the oracle's cost-class adjoint and against the streaming
-passes of the same call (GQAOA_GRAD_STREAMING).
+"""The cluster-resident adjoint (gqaoa_grad_batched for 10 <= n <= 16: one
+CTA or thread-block cluster holds an instance for all its forward and
+backward rounds) against the oracle's cost-class adjoint and against the
+other path of the same call (GQAOA_GRAD_STREAMING: the one-CTA kernels for
+n <= 11, the streaming passes above).
 
-Every cluster shape is covered: n = 12 (one 256-thread CTA), 13 (one
-512-thread CTA), 14, 15 and 16 (clusters of 2, 4 and 8 CTAs), with more
+Every shape is covered: n = 10, 11, 12 (one CTA of 64, 128, 256 threads), 13
+(one 512-thread CTA), 14, 15 and 16 (clusters of 2, 4 and 8 CTAs), with more
 instances than resident clusters at n = 16 (clusters loop over instances),
 the three objectives (P(C=0), <H_P>, and the probability of the lowest cost
 class of an unsatisfiable instance), a cost table shared by every row, and
@@ -44,7 +45,8 @@ def _check(v, dg, db, hists, G, Bt, obj, scale):
         assert np.max(np.abs(db[i] - rdb)) < G_TOL * scale, i
 
 
-@pytest.mark.parametrize("n,B,p", [(12, 3, 12), (13, 3, 10), (14, 2, 9), (15, 2, 8), (16, 40, 6)])
+@pytest.mark.parametrize("n,B,p", [(10, 5, 14), (11, 3, 12), (12, 3, 12), (13, 3, 10), (14, 2, 9),
+                                   (15, 2, 8), (16, 40, 6)])
 @pytest.mark.parametrize("objective", ["p0", "energy"])
 def test_cluster_adjoint_matches_oracle_and_streaming(n, B, p, objective):
     m = int(round(4.2 * n))
