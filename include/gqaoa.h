@@ -236,6 +236,10 @@ int gqaoa_grad_workspace_size(int n, int p, size_t *bytes);
  * checkpoints still go to the workspace); otherwise, or with
  * GQAOA_GRAD_STREAMING, one CTA per instance for n <= 11 (forward and
  * adjoint kernels) and streaming passes over HBM above.
+ * The clusters exchange each round's partial sums through mbarrier waits
+ * bounded at 2 s; the call is asynchronous, so a wait that gives up (which
+ * no correct launch does) is reported in the results: every value and
+ * derivative of the call is then NaN.
  */
 int gqaoa_grad(const uint8_t *cost, int n, int m, const double *gammas, const double *betas,
                int p, int objective, double *value, double *dgamma, double *dbeta, void *ws,

@@ -52,6 +52,7 @@ struct AdjArgs {
   int B;
   int objective;          // GQAOA_OBJ_P0 (projector on `target`) or GQAOA_OBJ_ENERGY
   unsigned target;
+  unsigned *status;       // nonzero once a bounded wait gave up (outputs then NaN)
 };
 
 // (hi, lo) += x in double-float arithmetic.
@@ -62,12 +63,86 @@ __device__ __forceinline__ void adj_df_add(float &hi, float &lo, float x) {
   lo = __fadd_rn(lo, e);
 }
 
-__device__ __forceinline__ void adj_st_dsmem(float2 *p, unsigned rank, float2 v) {
-  uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+__device__ __forceinline__ uint32_t adj_smem(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint32_t adj_mapa(uint32_t local, unsigned rank) {
   uint32_t remote;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
-  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(remote), "f"(v.x), "f"(v.y)
-               : "memory");
+  return remote;
+}
+
+__device__ __forceinline__ uint64_t adj_globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// The exchange of one cluster reduction: every CTA's partials (three
+// double-float pairs, 24 bytes) land in a receive slot of every CTA of the
+// cluster through st.async, whose writes complete bytes of the transaction
+// count of the receiver's mbarrier; a receiver has all partials once the
+// phase it armed for kCluster x 24 bytes completes. No cluster barrier and
+// no fence: the mbarrier's completion orders the data.
+constexpr uint32_t kAdjSlotBytes = 24;
+constexpr uint64_t kAdjWaitNs = 2000000000ull;  // a bounded wait gives up after 2 s
+
+struct AdjSync {
+  unsigned t;  // calls so far: this call uses buffer t & 1, in its use (t >> 1)
+  bool ok;     // false once a wait of this thread has given up
+};
+
+__device__ __forceinline__ void adj_mb_init(uint32_t mb) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+}
+
+// One arrival, expecting `bytes` of complete_tx in the current phase.
+__device__ __forceinline__ void adj_mb_arm(uint32_t mb, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mb),
+      "r"(bytes)
+      : "memory");
+}
+
+// Store d[0..2] at the receive slot `slot` (a local shared address) of CTA
+// `peer` and complete 24 bytes on that CTA's mbarrier at local address mb.
+__device__ __forceinline__ void adj_send(uint32_t slot, uint32_t mb, unsigned peer,
+                                         const float2 (&d)[kAdjVals]) {
+  const uint32_t rs = adj_mapa(slot, peer), rm = adj_mapa(mb, peer);
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+      ::"r"(rs), "f"(d[0].x), "f"(d[0].y), "f"(d[1].x), "f"(d[1].y), "r"(rm) : "memory");
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
+               ::"r"(rs + 16), "f"(d[2].x), "f"(d[2].y), "r"(rm) : "memory");
+}
+
+// Wait for the phase of parity `parity` of the mbarrier at mb to complete,
+// with acquire semantics at cluster scope (the peers' st.async data is then
+// visible). Bounded: gives up after kAdjWaitNs of polling, or soon after any
+// other thread of the launch has given up (*status nonzero); returns false
+// when it gave up.
+__device__ __forceinline__ bool adj_mb_wait(uint32_t mb, unsigned parity,
+                                            const volatile unsigned *status) {
+  uint32_t t0 = 0;  // low word of the timer: differences below 4.29 s are exact
+  for (unsigned i = 1;; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((i & 255u) == 0) {
+      if (*status) return false;
+      const uint32_t t = (uint32_t)adj_globaltimer();
+      if (i == 256) t0 = t;
+      else if (t - t0 > (uint32_t)kAdjWaitNs) return false;
+    }
+  }
 }
 
 // Double-float sum over each aligned group of kG lanes (kG a power of two up
@@ -92,11 +167,11 @@ __device__ __forceinline__ void adj_df_group(float &hi, float &lo) {
 // kWarpDF); on exit v[k] is the cluster's total as a double-float pair, the
 // same in every thread. The warp's lanes are summed in FP32 (a butterfly;
 // double-float with kWarpDF), the warps and then the CTAs in double-float.
-// buf alternates between calls: the partials of one call are read while the
-// next call's are written.
-// between() runs after this thread's arrival at the cluster barrier and
-// before its wait: the barrier's release then covers only what came before
-// (the partials), and global stores placed in between() do not hold it up.
+// The buffers alternate between calls (sy.t counts them): the partials of
+// one call are read while the next call's are written. Slots are 32 bytes (v[0], v[1] at 0, v[2] at 16).
+// between() runs while the partials are in flight (after this CTA's sends,
+// before its wait), so global loads and stores placed there overlap the
+// exchange.
 struct AdjNothing {
   __device__ __forceinline__ void operator()() const {}
 };
@@ -104,9 +179,11 @@ struct AdjNothing {
 template <int kThreads, int kCluster, int kV, bool kWarpDF = false, typename Between = AdjNothing>
 __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
                                                 float2 (*s_wp)[kThreads / 32][kAdjVals],
-                                                float2 (*s_ps)[kCluster][kAdjVals], int buf,
-                                                unsigned rank, Between between = Between()) {
+                                                float2 (*s_ps)[kCluster][4], uint64_t *s_mb,
+                                                unsigned rank, AdjSync &sy, unsigned *status,
+                                                Between between = Between()) {
   constexpr int kW = kThreads / 32;
+  const int buf = sy.t & 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < kV; ++k) {
@@ -125,23 +202,38 @@ __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
   }
   __syncthreads();
   if (warp == 0) {
+    // every group of kW lanes holds the kW warp partials
+    float2 d[kAdjVals];
 #pragma unroll
-    for (int k = 0; k < kV; ++k) {
-      // every group of kW lanes holds the kW warp partials
-      float2 d = s_wp[buf][lane & (kW - 1)][k];
-      adj_df_group<kW>(d.x, d.y);
-      if (kCluster == 1) {
-        if (lane == 0) s_ps[buf][0][k] = d;
-      } else if (lane < kCluster) {
-        adj_st_dsmem(&s_ps[buf][rank][k], (unsigned)lane, d);
+    for (int k = 0; k < kAdjVals; ++k) {
+      d[k] = make_float2(0.f, 0.f);
+      if (k < kV) {
+        d[k] = s_wp[buf][lane & (kW - 1)][k];
+        adj_df_group<kW>(d[k].x, d[k].y);
       }
+    }
+    if (kCluster == 1) {
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < kV; ++k) s_ps[buf][0][k] = d[k];
+      }
+    } else if (lane < kCluster && sy.ok) {
+      adj_send(adj_smem(&s_ps[buf][rank][0]), adj_smem(&s_mb[buf]), (unsigned)lane, d);
     }
   }
   if (kCluster > 1) {
-    // release/acquire: every CTA's partial visible locally
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
     between();
-    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    if (sy.ok) {
+      if (!adj_mb_wait(adj_smem(&s_mb[buf]), (sy.t >> 1) & 1u, status)) {
+        sy.ok = false;
+        atomicExch(status, 1u);
+      }
+    }
+    // warp-uniform from here on, so warp 0's arming and sends stay in step
+    sy.ok = __all_sync(0xffffffffu, sy.ok);
+    // arm this mbarrier for its next use (two calls on; a peer can send
+    // into it only after this CTA's partials of the call in between)
+    if (threadIdx.x == 0 && sy.ok) adj_mb_arm(adj_smem(&s_mb[buf]), kCluster * kAdjSlotBytes);
   } else {
     __syncthreads();
     between();
@@ -152,12 +244,15 @@ __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
     adj_df_group<kCluster>(d.x, d.y);
     v[k] = d;
   }
+  ++sy.t;
 }
 
 // The mixer coefficients as FP32 pairs, into the records' spare slots
-// (record[4 bk + 2], read as a float2), so the rounds convert no FP64.
+// (record[4 bk + 2], read as a float2), so the rounds convert no FP64; and
+// the launch's status word cleared.
 __global__ void adj_alpha_kernel(const double2 *__restrict__ alpha, uint64_t count,
-                                 double *__restrict__ record) {
+                                 double *__restrict__ record, unsigned *status) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0u;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const double2 al = alpha[i];
@@ -170,7 +265,8 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads)
 adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
   constexpr int kW = kThreads / 32;
   __shared__ float2 s_wp[2][kW][kAdjVals];
-  __shared__ float2 s_ps[2][kCluster][kAdjVals];
+  __shared__ __align__(16) float2 s_ps[2][kCluster][4];  // receive slots
+  __shared__ __align__(8) uint64_t s_mb[2];              // their mbarriers
   // phase tables, double-buffered: a round reads s_T[k & 1] while its table
   // for two rounds on is in flight in registers (tn) of threads 0..255, each
   // holding kTab entries (t, t + kThreads, ...)
@@ -183,9 +279,19 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
   const float inv_n = (float)(1.0 / (double)N);  // a power of two: exact
   const float amp0 = (float)(1.0 / sqrt((double)N));
   const bool writer = rank == 0 && threadIdx.x == 0;
+  AdjSync sy = {0u, true};
+  if (kCluster > 1) {
+    if (threadIdx.x == 0) {
+      adj_mb_init(adj_smem(&s_mb[0]));
+      adj_mb_init(adj_smem(&s_mb[1]));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      adj_mb_arm(adj_smem(&s_mb[0]), kCluster * kAdjSlotBytes);
+      adj_mb_arm(adj_smem(&s_mb[1]), kCluster * kAdjSlotBytes);
+    }
+    cluster_sync();  // every CTA's mbarriers initialised before any partial is sent
+  }
   // slot j of this thread is amplitude z0 + j kThreads
   const uint64_t z0 = (uint64_t)rank * kAdjPer * kThreads + threadIdx.x;
-  int buf = 0;
   for (uint64_t b = cl; b < (uint64_t)a.B; b += ncl) {
     const uint8_t *cost = a.cost + b * a.cost_bstride + z0;
     unsigned c[kAdjPer];
@@ -227,12 +333,11 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
         }
       }
       float2 v[kAdjVals] = {make_float2(sr, 0.f), make_float2(si, 0.f), make_float2(0.f, 0.f)};
-      // the checkpoints chi_k, stored while the cluster barrier completes
-      adj_cluster_sum<kThreads, kCluster, 2>(v, s_wp, s_ps, buf, rank, [&]() {
+      // the checkpoints chi_k, stored while the partials are exchanged
+      adj_cluster_sum<kThreads, kCluster, 2>(v, s_wp, s_ps, s_mb, rank, sy, a.status, [&]() {
 #pragma unroll
         for (int j = 0; j < kAdjPer; ++j) ck[j * kThreads] = s[j];
       });
-      buf ^= 1;
       const float Sr = v[0].x + v[0].y, Si = v[1].x + v[1].y;
       const float2 al = *reinterpret_cast<const float2 *>(a.record + 4 * bk + 2);
       const float2 af = make_float2((al.x * Sr - al.y * Si) * inv_n, (al.x * Si + al.y * Sr) * inv_n);
@@ -276,8 +381,7 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       for (int i = 0; i < kTab; ++i) tn[i] = tab[(uint64_t)(a.p - 2) * 256 + i * kThreads];
     }
     float2 v[kAdjVals] = {make_float2(vh, vl), make_float2(lr, 0.f), make_float2(li, 0.f)};
-    adj_cluster_sum<kThreads, kCluster, 3, true>(v, s_wp, s_ps, buf, rank);
-    buf ^= 1;
+    adj_cluster_sum<kThreads, kCluster, 3, true>(v, s_wp, s_ps, s_mb, rank, sy, a.status);
     if (writer) a.value[b] = (double)v[0].x + (double)v[0].y;
     // backward rounds
     for (int k = a.p - 1; k >= 0; --k) {
@@ -309,15 +413,14 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       v[0] = make_float2(g, 0.f);
       v[1] = make_float2(nlr, 0.f);
       v[2] = make_float2(nli, 0.f);
-      // round k - 1's checkpoints, loaded while the cluster barrier completes
-      adj_cluster_sum<kThreads, kCluster, 3>(v, s_wp, s_ps, buf, rank, [&]() {
+      // round k - 1's checkpoints, loaded while the partials are exchanged
+      adj_cluster_sum<kThreads, kCluster, 3>(v, s_wp, s_ps, s_mb, rank, sy, a.status, [&]() {
         if (k > 0) {
           const float2 *ck = a.ckpt + ((uint64_t)(k - 1) * a.B + b) * N + z0;
 #pragma unroll
           for (int j = 0; j < kAdjPer; ++j) x[j] = ck[j * kThreads];
         }
       });
-      buf ^= 1;
       if (writer) {  // the round's sums, finished in FP64 by adj_finalize_kernel
         *reinterpret_cast<float2 *>(a.record + 4 * bk + 3) = v[0];  // G_k
         *reinterpret_cast<float2 *>(a.dbeta + bk) = Ld;             // L_k (re)
@@ -331,9 +434,20 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
 // The gradients in FP64 from the double-float sums the rounds left (one
 // thread per instance and round, off the rounds' critical path):
 // dE/dbeta_k = 2 Im(conj(e^{-i beta_k} S_k / N) L_k), dE/dgamma_k = 2 G_k.
+// If a bounded wait of the rounds gave up, every value and derivative of the
+// call is NaN instead.
 __global__ void adj_finalize_kernel(const double2 *__restrict__ alpha, const double *record,
-                                    uint64_t count, int n, double *dgamma, double *dbeta) {
+                                    uint64_t count, int n, int B, const unsigned *status,
+                                    double *value, double *dgamma, double *dbeta) {
   const double inv_n = ldexp(1.0, -n);
+  if (*status) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+      dgamma[i] = dbeta[i] = __longlong_as_double(0x7ff8000000000000ll);
+      if (i < (uint64_t)B) value[i] = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    return;
+  }
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const float4 S = *reinterpret_cast<const float4 *>(record + 4 * i);
@@ -394,19 +508,19 @@ bool adjoint_cluster_fits(int n, int B) { return n >= 10 && n <= 16 && B >= 1; }
 // Objective and adjoint gradient of B rows of 2^n amplitudes (10 <= n <= 16)
 // in one launch (plus the FP32 mixer coefficients' conversion). phase,
 // alpha: the rows' tables ([B][p][256], [B][p]); record [B][p][4] and ckpt
-// [p][B][2^n] are workspace. objective: GQAOA_OBJ_P0 with target, or
-// GQAOA_OBJ_ENERGY.
+// [p][B][2^n] and the status word are workspace. objective: GQAOA_OBJ_P0
+// with target, or GQAOA_OBJ_ENERGY.
 int adjoint_cluster(const uint8_t *cost, uint64_t cost_bstride, int n, int B, int p,
                     const float2 *phase, const double2 *alpha, double *record, float2 *ckpt,
                     int objective, unsigned target, double *value, double *dgamma,
-                    double *dbeta, cudaStream_t st) {
+                    double *dbeta, unsigned *status, cudaStream_t st) {
   if (!adjoint_cluster_fits(n, B)) return GQAOA_ERANGE;
   const uint64_t count = (uint64_t)B * (uint64_t)p;
   const unsigned grid = (unsigned)(count < 256ull * 1024 ? (count + 255) / 256 : 1024);
-  adj_alpha_kernel<<<grid, 256, 0, st>>>(alpha, count, record);
+  adj_alpha_kernel<<<grid, 256, 0, st>>>(alpha, count, record, status);
   GQ_CHECK_LAUNCH();
   AdjArgs args = {cost, cost_bstride, phase, alpha, record, ckpt, value, dgamma, dbeta,
-                  n, p, B, objective, target};
+                  n, p, B, objective, target, status};
   int rc;
   switch (n) {
     case 10: rc = launch_adjoint<64, 1>(args, st); break;
@@ -418,7 +532,8 @@ int adjoint_cluster(const uint8_t *cost, uint64_t cost_bstride, int n, int B, in
     default: rc = launch_adjoint<512, 8>(args, st); break;
   }
   if (rc) return rc;
-  adj_finalize_kernel<<<grid, 256, 0, st>>>(alpha, record, count, n, dgamma, dbeta);
+  adj_finalize_kernel<<<grid, 256, 0, st>>>(alpha, record, count, n, B, status, value, dgamma,
+                                           dbeta);
   GQ_CHECK_LAUNCH();
   return GQAOA_OK;
 }

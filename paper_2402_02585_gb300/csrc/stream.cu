@@ -1259,7 +1259,7 @@ bool adjoint_cluster_fits(int n, int B);
 int adjoint_cluster(const uint8_t *cost, uint64_t cost_bstride, int n, int B, int p,
                     const float2 *phase, const double2 *alpha, double *record, float2 *ckpt,
                     int objective, unsigned target, double *value, double *dgamma,
-                    double *dbeta, cudaStream_t st);
+                    double *dbeta, unsigned *status, cudaStream_t st);
 
 static int grad_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m, int B,
                      const double *gammas, const double *betas, int p, int objective, double *value,
@@ -1291,7 +1291,8 @@ static int grad_impl(const uint8_t *cost, uint64_t cost_bstride, int n, int m, i
   if (rc) return rc;
   if (!streaming && adjoint_cluster_fits(n, B))  // every round of a row on one cluster
     return adjoint_cluster(cost, cost_bstride, n, B, p, w.phase, w.alpha, w.record, w.ckpt,
-                           objective, target, value, dgamma, dbeta, st);
+                           objective, target, value, dgamma, dbeta,
+                           reinterpret_cast<unsigned *>(w.parts), st);  // parts: unused here
   if (g.small) {
     SmallArgs sa = {cost, cost_bstride, n, p, w.phase, w.alpha, w.lambda, false, nullptr,
                     nullptr, w.record, w.ckpt, B, target};
