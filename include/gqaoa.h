@@ -230,10 +230,11 @@ int gqaoa_grad_workspace_size(int n, int p, size_t *bytes);
  * cost device uint8 [2^n]; gammas, betas device double [p];
  * value  device double [1] written: L;
  * dgamma, dbeta device double [p] written.
- * Paths: for 10 <= n <= 16 one CTA (64-512 threads) or thread-block cluster
- * (2-8 CTAs of 512 threads) per instance holds the state on chip for all
- * rounds, forward and backward, in one launch (16 amplitudes per thread; the
- * checkpoints still go to the workspace); otherwise, or with
+ * Paths: for 10 <= n <= 16 one CTA (64 or 128 threads, n = 10, 11) or one
+ * thread-block cluster of 2^n / 4096 CTAs of 256 threads (n = 12..16, two
+ * CTAs per SM) per instance holds the state on chip for all rounds, forward
+ * and backward, in one launch (16 amplitudes per thread; the checkpoints
+ * still go to the workspace); otherwise, or with
  * GQAOA_GRAD_STREAMING, one CTA per instance for n <= 11 (forward and
  * adjoint kernels) and streaming passes over HBM above.
  * The clusters exchange each round's partial sums through mbarrier waits

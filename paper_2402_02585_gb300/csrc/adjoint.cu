@@ -7,13 +7,14 @@
 // cluster owns one instance (row) for the whole call: each thread keeps 16
 // amplitudes in registers, the forward rounds write the checkpoints chi_k
 // (each thread later rereads only its own), and the backward rounds follow
-// in the same launch. A round's sums go warp (FP32 butterfly) -> CTA (warp 0
-// over the warp partials, double-float) -> cluster (every CTA's partial pushed into
-// the shared memory of every peer, one cluster barrier, every warp summing
-// the partials in rank order), so every warp of every CTA holds the same
-// totals bit for bit and no further barrier is needed. FP32 amplitudes; the mixer
-// coefficients are formed in FP32 from the double-float sums, and the rounds
-// use no FP64: a closing kernel forms the gradients from the sums they left.
+// in the same launch. A round's sums are FP32 butterflies over the warp's
+// lanes, then (warp 0) over the CTA's warps, then over the cluster's CTAs
+// (every CTA's partial stored into the shared memory of every peer, every
+// warp summing them), so every warp of every CTA holds the same totals bit
+// for bit and no further barrier is needed; the objective's value is summed
+// the same way in double-float. FP32 amplitudes and mixer coefficients: the
+// rounds use no FP64, a closing kernel forms the gradients from the sums
+// they left.
 //
 // Forward round k: chi_k = T_k[c] psi_{k-1} (checkpointed), S_k = sum chi_k,
 // a_k = alpha_k S_k / N, psi_k = chi_k + a_k. Backward, from
@@ -42,7 +43,7 @@ struct AdjArgs {
   uint64_t cost_bstride;
   const float2 *phase;    // [B][p][256]
   const double2 *alpha;   // [B][p]
-  double *record;         // [B][p][4]: S_k as double-float pairs, float alpha_k, G_k
+  double *record;         // [B][p][4]: S_k (re, im as float pairs), float alpha_k, G_k
   float2 *ckpt;           // [p][B][N]
   double *value;          // [B]
   double *dgamma;         // [B][p]
@@ -162,21 +163,36 @@ __device__ __forceinline__ void adj_df_group(float &hi, float &lo) {
   }
 }
 
+// Sum over each aligned group of kG lanes (a power of two up to 32): FP32 in
+// v.x, or (kDF) the double-float pair (v.x, v.y).
+template <int kG, bool kDF>
+__device__ __forceinline__ void adj_group(float2 &v) {
+  if (kDF) {
+    adj_df_group<kG>(v.x, v.y);
+  } else {
+    float x = v.x;
+#pragma unroll
+    for (int o = kG / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    v = make_float2(x, 0.f);
+  }
+}
+
 // Cluster-wide sums of kV <= kAdjVals values: v[k] holds this thread's
-// partial on entry (an FP32 value in .x, or a double-float pair with
-// kWarpDF); on exit v[k] is the cluster's total as a double-float pair, the
-// same in every thread. The warp's lanes are summed in FP32 (a butterfly;
-// double-float with kWarpDF), the warps and then the CTAs in double-float.
+// partial on entry (an FP32 value in .x, or a double-float pair with kDF);
+// on exit v[k] is the cluster's total (FP32 in .x and 0 in .y, or a
+// double-float pair with kDF), the same bits in every thread: each stage
+// (the warp's lanes, the CTA's warps, the cluster's CTAs) is a butterfly,
+// whose partner lanes add the same two operands.
 // The buffers alternate between calls (sy.t counts them): the partials of
-// one call are read while the next call's are written. Slots are 32 bytes (v[0], v[1] at 0, v[2] at 16).
-// between() runs while the partials are in flight (after this CTA's sends,
-// before its wait), so global loads and stores placed there overlap the
-// exchange.
+// one call are read while the next call's are written. Slots are 32 bytes
+// (v[0], v[1] at 0, v[2] at 16). between() runs while the partials are in
+// flight (after this CTA's sends, before its wait), so global loads and
+// stores placed there overlap the exchange.
 struct AdjNothing {
   __device__ __forceinline__ void operator()() const {}
 };
 
-template <int kThreads, int kCluster, int kV, bool kWarpDF = false, typename Between = AdjNothing>
+template <int kThreads, int kCluster, int kV, bool kDF = false, typename Between = AdjNothing>
 __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
                                                 float2 (*s_wp)[kThreads / 32][kAdjVals],
                                                 float2 (*s_ps)[kCluster][4], uint64_t *s_mb,
@@ -186,16 +202,7 @@ __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
   const int buf = sy.t & 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < kV; ++k) {
-    if (kWarpDF) {
-      adj_df_group<32>(v[k].x, v[k].y);
-    } else {
-      float x = v[k].x;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      v[k] = make_float2(x, 0.f);
-    }
-  }
+  for (int k = 0; k < kV; ++k) adj_group<32, kDF>(v[k]);
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < kV; ++k) s_wp[buf][warp][k] = v[k];
@@ -209,7 +216,7 @@ __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
       d[k] = make_float2(0.f, 0.f);
       if (k < kV) {
         d[k] = s_wp[buf][lane & (kW - 1)][k];
-        adj_df_group<kW>(d[k].x, d[k].y);
+        adj_group<kW, kDF>(d[k]);
       }
     }
     if (kCluster == 1) {
@@ -241,7 +248,7 @@ __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
 #pragma unroll
   for (int k = 0; k < kV; ++k) {
     float2 d = s_ps[buf][lane & (kCluster - 1)][k];
-    adj_df_group<kCluster>(d.x, d.y);
+    adj_group<kCluster, kDF>(d);
     v[k] = d;
   }
   ++sy.t;
@@ -343,7 +350,7 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       const float2 af = make_float2((al.x * Sr - al.y * Si) * inv_n, (al.x * Si + al.y * Sr) * inv_n);
 #pragma unroll
       for (int j = 0; j < kAdjPer; ++j) s[j] = make_float2(s[j].x + af.x, s[j].y + af.y);
-      if (writer)  // S_k as double-float pairs (adj_finalize_kernel reads them)
+      if (writer)  // S_k as float pairs (sum, 0), read by adj_finalize_kernel
         *reinterpret_cast<float4 *>(a.record + 4 * bk) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
     }
     // lambda_p = O psi_p, the objective sum_z O |psi_p|^2 (double-float:
@@ -386,7 +393,7 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
     // backward rounds
     for (int k = a.p - 1; k >= 0; --k) {
       const uint64_t bk = b * (uint64_t)a.p + k;
-      const float2 Ld = v[1], Li2 = v[2];  // this round's L (double-float)
+      const float2 Ld = v[1], Li2 = v[2];  // this round's L (as float pairs)
       const float Lr = Ld.x + Ld.y, Li = Li2.x + Li2.y;
       const float2 al = *reinterpret_cast<const float2 *>(a.record + 4 * bk + 2);
       const float2 bv = make_float2((al.x * Lr + al.y * Li) * inv_n, (al.x * Li - al.y * Lr) * inv_n);
@@ -431,7 +438,7 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
   if (kCluster > 1) cluster_sync();  // no CTA leaves while a peer may still store into it
 }
 
-// The gradients in FP64 from the double-float sums the rounds left (one
+// The gradients in FP64 from the sums the rounds left (float pairs; one
 // thread per instance and round, off the rounds' critical path):
 // dE/dbeta_k = 2 Im(conj(e^{-i beta_k} S_k / N) L_k), dE/dgamma_k = 2 G_k.
 // If a bounded wait of the rounds gave up, every value and derivative of the
@@ -488,7 +495,7 @@ int launch_adjoint(const AdjArgs &args, cudaStream_t st) {
   } else if (cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg) != cudaSuccess) {
     return GQAOA_ECUDA;
   }
-  if (clusters < 1) return GQAOA_ECUDA;
+  if (clusters < 1) return GQAOA_ERANGE;  // this shape cannot be placed
   const uint64_t units = (uint64_t)args.B < (uint64_t)clusters ? (uint64_t)args.B : (uint64_t)clusters;
   cfg.gridDim = dim3((unsigned)(units * kCluster), 1, 1);
   cfg.stream = st;
@@ -521,15 +528,24 @@ int adjoint_cluster(const uint8_t *cost, uint64_t cost_bstride, int n, int B, in
   GQ_CHECK_LAUNCH();
   AdjArgs args = {cost, cost_bstride, phase, alpha, record, ckpt, value, dgamma, dbeta,
                   n, p, B, objective, target, status};
+  // CTAs of 256 threads (two per SM, so each SM interleaves two rows'
+  // rounds), 16 amplitudes a thread: a cluster of 2^n / 4096 CTAs.
   int rc;
   switch (n) {
     case 10: rc = launch_adjoint<64, 1>(args, st); break;
     case 11: rc = launch_adjoint<128, 1>(args, st); break;
-    case 12: rc = launch_adjoint<256, 1>(args, st); break;
-    case 13: rc = launch_adjoint<512, 1>(args, st); break;
-    case 14: rc = launch_adjoint<512, 2>(args, st); break;
-    case 15: rc = launch_adjoint<512, 4>(args, st); break;
-    default: rc = launch_adjoint<512, 8>(args, st); break;
+    case 12: rc = launch_adjoint<128, 2>(args, st); break;
+    case 13: rc = launch_adjoint<256, 2>(args, st); break;
+    case 14: rc = launch_adjoint<256, 4>(args, st); break;
+    case 15: rc = launch_adjoint<256, 8>(args, st); break;
+    default:
+      // a non-portable cluster size; 8 CTAs of 512 threads where 16 cannot be placed
+      rc = launch_adjoint<256, 16>(args, st);
+      if (rc == GQAOA_ECUDA || rc == GQAOA_ERANGE) {
+        (void)cudaGetLastError();
+        rc = launch_adjoint<512, 8>(args, st);
+      }
+      break;
   }
   if (rc) return rc;
   adj_finalize_kernel<<<grid, 256, 0, st>>>(alpha, record, count, n, B, status, value, dgamma,
