@@ -318,6 +318,10 @@ int gqaoa_batched_geometry(int n, int batch, int adjoint, int *ctas_per_instance
  * Precision: complex64 state; the mixer sum is FP32 within a warp
  * (GQAOA_SWEEP_L2: double-float within a thread, then FP32 across the warp)
  * and double-float above that; P is formed in FP64.
+ * The CTAs of a cluster exchange each round's partial sums through mbarrier
+ * waits bounded at 2 s; the call is asynchronous, so a wait that gives up
+ * (which no correct launch does) shows in the results: the P values that
+ * depend on a missing partial are NaN.
  */
 #define GQAOA_SWEEP_MIN_N 9
 #define GQAOA_SWEEP_MAX_N 19

@@ -64,86 +64,22 @@ __device__ __forceinline__ void adj_df_add(float &hi, float &lo, float x) {
   lo = __fadd_rn(lo, e);
 }
 
-__device__ __forceinline__ uint32_t adj_smem(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint32_t adj_mapa(uint32_t local, unsigned rank) {
-  uint32_t remote;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
-  return remote;
-}
-
-__device__ __forceinline__ uint64_t adj_globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// The exchange of one cluster reduction: every CTA's partials (three
-// double-float pairs, 24 bytes) land in a receive slot of every CTA of the
-// cluster through st.async, whose writes complete bytes of the transaction
-// count of the receiver's mbarrier; a receiver has all partials once the
-// phase it armed for kCluster x 24 bytes completes. No cluster barrier and
-// no fence: the mbarrier's completion orders the data.
+// The exchange of one cluster reduction (st.async into every CTA's receive
+// slot, mbarrier-counted): a CTA's partials are three float pairs, 24 bytes.
 constexpr uint32_t kAdjSlotBytes = 24;
-constexpr uint64_t kAdjWaitNs = 2000000000ull;  // a bounded wait gives up after 2 s
 
 struct AdjSync {
   unsigned t;  // calls so far: this call uses buffer t & 1, in its use (t >> 1)
   bool ok;     // false once a wait of this thread has given up
 };
 
-__device__ __forceinline__ void adj_mb_init(uint32_t mb) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
-}
-
-// One arrival, expecting `bytes` of complete_tx in the current phase.
-__device__ __forceinline__ void adj_mb_arm(uint32_t mb, uint32_t bytes) {
-  asm volatile(
-      "{\n\t.reg .b64 st;\n\t"
-      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mb),
-      "r"(bytes)
-      : "memory");
-}
-
 // Store d[0..2] at the receive slot `slot` (a local shared address) of CTA
 // `peer` and complete 24 bytes on that CTA's mbarrier at local address mb.
 __device__ __forceinline__ void adj_send(uint32_t slot, uint32_t mb, unsigned peer,
                                          const float2 (&d)[kAdjVals]) {
-  const uint32_t rs = adj_mapa(slot, peer), rm = adj_mapa(mb, peer);
-  asm volatile(
-      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
-      ::"r"(rs), "f"(d[0].x), "f"(d[0].y), "f"(d[1].x), "f"(d[1].y), "r"(rm) : "memory");
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
-               ::"r"(rs + 16), "f"(d[2].x), "f"(d[2].y), "r"(rm) : "memory");
-}
-
-// Wait for the phase of parity `parity` of the mbarrier at mb to complete,
-// with acquire semantics at cluster scope (the peers' st.async data is then
-// visible). Bounded: gives up after kAdjWaitNs of polling, or soon after any
-// other thread of the launch has given up (*status nonzero); returns false
-// when it gave up.
-__device__ __forceinline__ bool adj_mb_wait(uint32_t mb, unsigned parity,
-                                            const volatile unsigned *status) {
-  uint32_t t0 = 0;  // low word of the timer: differences below 4.29 s are exact
-  for (unsigned i = 1;; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(mb), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((i & 255u) == 0) {
-      if (*status) return false;
-      const uint32_t t = (uint32_t)adj_globaltimer();
-      if (i == 256) t0 = t;
-      else if (t - t0 > (uint32_t)kAdjWaitNs) return false;
-    }
-  }
+  const uint32_t rs = mapa_shared(slot, peer), rm = mapa_shared(mb, peer);
+  st_async_v4(rs, make_float4(d[0].x, d[0].y, d[1].x, d[1].y), rm);
+  st_async_v2(rs + 16, d[2], rm);
 }
 
 // Double-float sum over each aligned group of kG lanes (kG a power of two up
@@ -225,13 +161,13 @@ __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
         for (int k = 0; k < kV; ++k) s_ps[buf][0][k] = d[k];
       }
     } else if (lane < kCluster && sy.ok) {
-      adj_send(adj_smem(&s_ps[buf][rank][0]), adj_smem(&s_mb[buf]), (unsigned)lane, d);
+      adj_send(smem_addr(&s_ps[buf][rank][0]), smem_addr(&s_mb[buf]), (unsigned)lane, d);
     }
   }
   if (kCluster > 1) {
     between();
     if (sy.ok) {
-      if (!adj_mb_wait(adj_smem(&s_mb[buf]), (sy.t >> 1) & 1u, status)) {
+      if (!mbar_wait(smem_addr(&s_mb[buf]), (sy.t >> 1) & 1u, status)) {
         sy.ok = false;
         atomicExch(status, 1u);
       }
@@ -240,7 +176,7 @@ __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
     sy.ok = __all_sync(0xffffffffu, sy.ok);
     // arm this mbarrier for its next use (two calls on; a peer can send
     // into it only after this CTA's partials of the call in between)
-    if (threadIdx.x == 0 && sy.ok) adj_mb_arm(adj_smem(&s_mb[buf]), kCluster * kAdjSlotBytes);
+    if (threadIdx.x == 0 && sy.ok) mbar_arm(smem_addr(&s_mb[buf]), kCluster * kAdjSlotBytes);
   } else {
     __syncthreads();
     between();
@@ -289,11 +225,11 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
   AdjSync sy = {0u, true};
   if (kCluster > 1) {
     if (threadIdx.x == 0) {
-      adj_mb_init(adj_smem(&s_mb[0]));
-      adj_mb_init(adj_smem(&s_mb[1]));
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-      adj_mb_arm(adj_smem(&s_mb[0]), kCluster * kAdjSlotBytes);
-      adj_mb_arm(adj_smem(&s_mb[1]), kCluster * kAdjSlotBytes);
+      mbar_init(smem_addr(&s_mb[0]));
+      mbar_init(smem_addr(&s_mb[1]));
+      mbar_init_fence();
+      mbar_arm(smem_addr(&s_mb[0]), kCluster * kAdjSlotBytes);
+      mbar_arm(smem_addr(&s_mb[1]), kCluster * kAdjSlotBytes);
     }
     cluster_sync();  // every CTA's mbarriers initialised before any partial is sent
   }
@@ -309,6 +245,11 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       s[j] = make_float2(amp0, 0.f);
     }
     const float2 *tab = a.phase + b * (uint64_t)a.p * 256 + threadIdx.x;  // + 256 k: round k
+    // the rounds' FP32 mixer coefficients, each loaded one round before its
+    // use (after an exchange's acquire a load could not be hoisted, and its
+    // latency would sit on every round's critical path)
+    const float2 *alf = reinterpret_cast<const float2 *>(a.record + 4 * b * (uint64_t)a.p + 2);
+    float2 aln = alf[0];  // round k at alf[4 k] (a record is four doubles)
     float2 tn[kTab];
     if (tabler) {
 #pragma unroll
@@ -346,7 +287,8 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
         for (int j = 0; j < kAdjPer; ++j) ck[j * kThreads] = s[j];
       });
       const float Sr = v[0].x + v[0].y, Si = v[1].x + v[1].y;
-      const float2 al = *reinterpret_cast<const float2 *>(a.record + 4 * bk + 2);
+      const float2 al = aln;
+      if (k + 1 < a.p) aln = alf[4 * (k + 1)];  // else kept: backward round p - 1 uses it
       const float2 af = make_float2((al.x * Sr - al.y * Si) * inv_n, (al.x * Si + al.y * Sr) * inv_n);
 #pragma unroll
       for (int j = 0; j < kAdjPer; ++j) s[j] = make_float2(s[j].x + af.x, s[j].y + af.y);
@@ -395,7 +337,8 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       const uint64_t bk = b * (uint64_t)a.p + k;
       const float2 Ld = v[1], Li2 = v[2];  // this round's L (as float pairs)
       const float Lr = Ld.x + Ld.y, Li = Li2.x + Li2.y;
-      const float2 al = *reinterpret_cast<const float2 *>(a.record + 4 * bk + 2);
+      const float2 al = aln;
+      if (k > 0) aln = alf[4 * (k - 1)];
       const float2 bv = make_float2((al.x * Lr + al.y * Li) * inv_n, (al.x * Li - al.y * Lr) * inv_n);
       const float2 *T = s_T[k & 1];
       float g = 0.f, nlr = 0.f, nli = 0.f;
@@ -528,18 +471,26 @@ int adjoint_cluster(const uint8_t *cost, uint64_t cost_bstride, int n, int B, in
   GQ_CHECK_LAUNCH();
   AdjArgs args = {cost, cost_bstride, phase, alpha, record, ckpt, value, dgamma, dbeta,
                   n, p, B, objective, target, status};
-  // CTAs of 256 threads (two per SM, so each SM interleaves two rows'
-  // rounds), 16 amplitudes a thread: a cluster of 2^n / 4096 CTAs.
+  // 16 amplitudes a thread; several CTAs per SM, so each SM interleaves
+  // several rows' rounds: 64- or 128-thread CTAs alone at n = 10, 11, then
+  // clusters of 128-thread CTAs (n = 12..15: 2, 4, 8, 16 CTAs) and 16 CTAs
+  // of 256 threads at n = 16. 16 is a non-portable cluster size: where it
+  // cannot be placed, the shape with half as many CTAs of twice the threads.
   int rc;
   switch (n) {
     case 10: rc = launch_adjoint<64, 1>(args, st); break;
     case 11: rc = launch_adjoint<128, 1>(args, st); break;
     case 12: rc = launch_adjoint<128, 2>(args, st); break;
-    case 13: rc = launch_adjoint<256, 2>(args, st); break;
-    case 14: rc = launch_adjoint<256, 4>(args, st); break;
-    case 15: rc = launch_adjoint<256, 8>(args, st); break;
+    case 13: rc = launch_adjoint<128, 4>(args, st); break;
+    case 14: rc = launch_adjoint<128, 8>(args, st); break;
+    case 15:
+      rc = launch_adjoint<128, 16>(args, st);
+      if (rc == GQAOA_ECUDA || rc == GQAOA_ERANGE) {
+        (void)cudaGetLastError();
+        rc = launch_adjoint<256, 8>(args, st);
+      }
+      break;
     default:
-      // a non-portable cluster size; 8 CTAs of 512 threads where 16 cannot be placed
       rc = launch_adjoint<256, 16>(args, st);
       if (rc == GQAOA_ECUDA || rc == GQAOA_ERANGE) {
         (void)cudaGetLastError();

@@ -145,4 +145,93 @@ __device__ __forceinline__ void cluster_reduce_store(const double *vals, int nva
   cluster_sync();  // keep every CTA's shared memory alive until rank 0 is done
 }
 
+// ---------------------------------------------------------------------------
+// cluster exchange through st.async and transaction-counted mbarriers
+// ---------------------------------------------------------------------------
+// A CTA stores its partials into a receive slot of every CTA of the cluster
+// with st.async, each store completing its bytes on the receiver's mbarrier;
+// a receiver that armed the phase for (CTAs x slot bytes) holds every
+// partial once that phase completes. No cluster barrier and no fence: the
+// phase completion, observed with acquire semantics at cluster scope,
+// orders the data. Waits are bounded (kMbarWaitNs); a wait that gives up
+// returns false, after which the caller stops exchanging and marks what it
+// writes invalid.
+constexpr uint32_t kMbarWaitNs = 2000000000u;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// The shared::cluster address of CTA `rank`'s copy of local shared address `local`.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t local, unsigned rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+  return remote;
+}
+
+__device__ __forceinline__ uint32_t globaltimer_lo() {
+  uint32_t t;
+  asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(t));
+  return t;
+}
+
+// An mbarrier with arrival count 1 (the arming thread).
+__device__ __forceinline__ void mbar_init(uint32_t mb) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+}
+
+// Makes the initialised mbarriers visible to the cluster's st.async; a
+// cluster barrier must follow before any peer stores into them.
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// The one arrival of the current phase, expecting `bytes` of complete_tx.
+__device__ __forceinline__ void mbar_arm(uint32_t mb, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mb),
+      "r"(bytes)
+      : "memory");
+}
+
+// 16 (8) bytes to the shared::cluster address `remote` (16- (8-) byte
+// aligned), completing as many bytes on the mbarrier at shared::cluster
+// address `rmb` of the same CTA.
+__device__ __forceinline__ void st_async_v4(uint32_t remote, float4 v, uint32_t rmb) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+      ::"r"(remote), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rmb) : "memory");
+}
+__device__ __forceinline__ void st_async_v2(uint32_t remote, float2 v, uint32_t rmb) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
+               ::"r"(remote), "f"(v.x), "f"(v.y), "r"(rmb) : "memory");
+}
+
+// Wait for the phase of parity `parity` of the mbarrier at mb to complete
+// (acquire at cluster scope: the peers' st.async data is then visible).
+// Bounded: gives up after kMbarWaitNs of polling, or soon after any other
+// thread of the launch has given up (*status nonzero); false when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, unsigned parity,
+                                          const volatile unsigned *status) {
+  uint32_t t0 = 0;  // differences of the timer's low word are exact below 4.29 s
+  for (unsigned i = 1;; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((i & 255u) == 0) {
+      if (*status) return false;
+      const uint32_t t = globaltimer_lo();
+      if (i == 256) t0 = t;
+      else if (t - t0 > kMbarWaitNs) return false;
+    }
+  }
+}
+
 }  // namespace gq

@@ -14,8 +14,10 @@
 // complex multiply-add and a partial sum.
 // The mixer needs S = sum_z chi(z) every round: FP32 over a thread's 16
 // values and the warp's butterfly, then double-float (two FP32 words) across
-// warps and, for clusters, across CTAs through distributed shared memory
-// (ld.shared::cluster after a cluster barrier). Warp 0 of every CTA forms the
+// warps and, for clusters, across CTAs: warp 0 stores its CTA's partial into
+// a receive slot of every CTA of the cluster with st.async, each store
+// completing its bytes on the receiver's mbarrier, and waits on its own
+// mbarrier (no cluster barrier in the rounds). Warp 0 of every CTA forms the
 // same a = alpha S / N from the same partials, so the CTAs of a cluster agree
 // bit for bit without a broadcast. Persistent grid: each CTA/cluster loops
 // over items instance-major, so consecutive items reuse the instance's cost
@@ -34,6 +36,7 @@ int sm_count();
 
 constexpr int kSweepMaxRounds = 16;
 constexpr int kSlots = 6;  // S.re, S.im, A0, B0.re, B0.im, count of C = 0
+constexpr uint32_t kSweepSlotBytes = kSlots * 8;  // a CTA partial: six double-float pairs
 
 struct SweepArgs {
   const uint8_t *cost;   // [B][N]
@@ -41,6 +44,7 @@ struct SweepArgs {
   const double2 *alpha;  // [A]
   double *out;           // [B][A][R]
   float4 *scratch;       // cluster-resident path: [kL2Slots][N / 2]
+  unsigned *status;      // nonzero once a bounded wait gave up (its outputs are then NaN)
   uint64_t nitems;       // B * A
   int n;
   int A;
@@ -65,14 +69,6 @@ __device__ __forceinline__ float warp_fsum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-__device__ __forceinline__ float2 ld_dsmem_f32x2(const float *p, unsigned rank) {
-  uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(p));
-  uint32_t remote;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
-  float x, y;
-  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(remote) : "memory");
-  return make_float2(x, y);
 }
 
 // One round over a thread's 16 amplitudes: chi = T[c] (s + a), then the
@@ -136,7 +132,8 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
   uint32_t *s_cost = reinterpret_cast<uint32_t *>(s_dyn + 16 * kThreads * sizeof(float2));  // [4][kThreads]
   __shared__ float2 s_T[256];
   __shared__ float s_wp[2][kW][kSlots];        // warp partials (FP32)
-  __shared__ float s_cp[2][kSlots][2];         // CTA partials (double-float), read cluster-wide
+  __shared__ __align__(16) float2 s_ps[kCluster > 1 ? 2 : 1][kCluster][kSlots];  // receive slots
+  __shared__ __align__(8) uint64_t s_mb[2];    // their mbarriers (warp 0 exchanges)
   __shared__ float2 s_a;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned rank = kCluster > 1 ? cluster_ctarank() : 0u;
@@ -145,6 +142,18 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
   const float inv_n = (float)(1.0 / (double)N);
   const float amp0 = (float)(1.0 / sqrt((double)N));
   int buf = 0;
+  unsigned xt = 0;  // warp 0: cluster exchanges so far (buffer xt & 1, its use xt >> 1)
+  bool ok = true;   // warp 0: false once its wait gave up
+  if (kCluster > 1) {
+    if (threadIdx.x == 0) {
+      mbar_init(smem_addr(&s_mb[0]));
+      mbar_init(smem_addr(&s_mb[1]));
+      mbar_init_fence();
+      mbar_arm(smem_addr(&s_mb[0]), kSweepSlotBytes * kCluster);
+      mbar_arm(smem_addr(&s_mb[1]), kSweepSlotBytes * kCluster);
+    }
+    cluster_sync();  // every CTA's mbarriers initialised before any partial is sent
+  }
 
   for (uint64_t item = cluster_id; item < a.nitems; item += nclusters) {
     const uint64_t b = item / (uint64_t)a.A;
@@ -204,20 +213,29 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
           lo[k] = 0.f;
           if (k < nv) df_warp(hi[k], lo[k]);
         }
-        if (kCluster > 1 && lane == 0) {
-#pragma unroll
-          for (int k = 0; k < kSlots; ++k)
-            if (k < nv) { s_cp[buf][k][0] = hi[k]; s_cp[buf][k][1] = lo[k]; }
-        }
-      }
-      if (kCluster > 1) {
-        cluster_sync();  // every CTA's partial visible cluster-wide
-        if (warp == 0) {
-          // double-float sum over the cluster's CTAs, in rank order
+        if (kCluster > 1) {
+          // this CTA's partial into a receive slot of every CTA of the
+          // cluster (all six slots, zero past nv), then the cluster's sum
+          const int xb = xt & 1;
+          if (lane < kCluster && ok) {
+            const uint32_t rs = mapa_shared(smem_addr(&s_ps[xb][rank][0]), (unsigned)lane);
+            const uint32_t rm = mapa_shared(smem_addr(&s_mb[xb]), (unsigned)lane);
+            st_async_v4(rs, make_float4(hi[0], lo[0], hi[1], lo[1]), rm);
+            st_async_v4(rs + 16, make_float4(hi[2], lo[2], hi[3], lo[3]), rm);
+            st_async_v4(rs + 32, make_float4(hi[4], lo[4], hi[5], lo[5]), rm);
+          }
+          if (ok && !mbar_wait(smem_addr(&s_mb[xb]), (xt >> 1) & 1u, a.status)) {
+            ok = false;
+            atomicExch(a.status, 1u);
+          }
+          ok = __all_sync(0xffffffffu, ok);
+          // armed for its next use, two rounds on
+          if (lane == 0 && ok) mbar_arm(smem_addr(&s_mb[xb]), kSweepSlotBytes * kCluster);
+          ++xt;
+          // double-float butterfly over the cluster's CTAs
 #pragma unroll
           for (int k = 0; k < kSlots; ++k) {
-            float2 d = make_float2(0.f, 0.f);
-            if (k < nv && lane < kCluster) d = ld_dsmem_f32x2(&s_cp[buf][k][0], (unsigned)lane);
+            const float2 d = (k < nv && lane < kCluster) ? s_ps[xb][lane][k] : make_float2(0.f, 0.f);
             hi[k] = d.x;
             lo[k] = d.y;
             if (k < nv) df_warp(hi[k], lo[k]);
@@ -235,7 +253,8 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
                        Bi = (double)hi[4] + lo[4];
           const double P = A0 + 2.0 * ((double)ar * Br + (double)aim * Bi) +
                            (double)cnt0 * ((double)ar * ar + (double)aim * aim);
-          a.out[(b * (uint64_t)a.A + ai) * a.R + ridx] = P;
+          a.out[(b * (uint64_t)a.A + ai) * a.R + ridx] =
+              ok ? P : __longlong_as_double(0x7ff8000000000000ll);
         }
       }
       __syncthreads();
@@ -272,11 +291,13 @@ sweep_kernel(const __grid_constant__ SweepArgs a) {
 //
 // The mixer sum: FP32 over at most 8 amplitudes, double-float per thread,
 // FP32 across a warp's lanes (butterfly), double-float per CTA (warp 0).
-// Warp 0 then pushes its CTA's partial into the shared memory of every CTA
-// of the cluster (lane r stores to CTA r), one cluster barrier
-// (release/acquire) makes the kL2Cluster partials visible locally, and
-// every warp sums them in rank order, so all warps of all CTAs hold the
-// same a_k bit for bit with no further barrier.
+// Warp 0 then stores its CTA's partial into a receive slot of every CTA of
+// the cluster with st.async (lane r stores to CTA r), each store completing
+// its bytes on the receiver's mbarrier; every thread waits on its own CTA's
+// mbarrier (acquire at cluster scope, no fence: the streaming warps' stores
+// to the L2 slots need not complete first) and every warp sums the
+// kL2Cluster partials with the same butterfly, so all warps of all CTAs
+// hold the same a_k bit for bit with no further barrier.
 // ---------------------------------------------------------------------------
 constexpr int kL2Threads = 512;
 constexpr int kL2Warps = kL2Threads / 32;
@@ -295,14 +316,6 @@ static_assert(kL2Batch == 2 && kL2RegVec % kL2Batch == 0 && kL2OnChip % kL2Batch
               "cluster-resident sweep: ring layout");
 constexpr size_t kL2DynSmem =
     (size_t)kL2SmemVec * kL2RoleThreads * (sizeof(float4) + sizeof(uint16_t));
-
-__device__ __forceinline__ void st_dsmem_f32x2(float2 *p, unsigned rank, float2 v) {
-  uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(p));
-  uint32_t remote;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
-  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(remote), "f"(v.x), "f"(v.y)
-               : "memory");
-}
 
 // chi = T[c] (psi + a) for one float4 (two amplitudes, cost bytes in c2),
 // adding to the FP32 partials v.
@@ -425,7 +438,8 @@ __global__ void __launch_bounds__(kL2Threads, 1) sweep_l2_kernel(const __grid_co
       reinterpret_cast<uint16_t *>(s_dyn + sizeof(float4) * kL2SmemVec * T);  // [kL2SmemVec][T]
   __shared__ float2 s_T[256];
   __shared__ float2 s_wp[2][kL2Warps][kSlots];    // warp partials (double-float)
-  __shared__ float2 s_ps[2][kL2Cluster][kSlots];  // CTA partials, pushed by every CTA
+  __shared__ __align__(16) float2 s_ps[2][kL2Cluster][kSlots];  // receive slots: CTA partials
+  __shared__ __align__(8) uint64_t s_mb[2];                     // their mbarriers
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool streaming = threadIdx.x < T;          // warps 0..7 stream, 8..15 stay on chip
   const int u = streaming ? threadIdx.x : threadIdx.x - T;
@@ -438,7 +452,16 @@ __global__ void __launch_bounds__(kL2Threads, 1) sweep_l2_kernel(const __grid_co
   const float amp0 = (float)(1.0 / sqrt((double)N));
   const uint64_t seg0 = (uint64_t)rank * Q;
   float4 *gp = a.scratch + cluster_id * Nv + seg0 + (uint64_t)kL2OnChip * T + u;
-  int buf = 0;
+  unsigned xt = 0;  // exchanges so far: this round's uses buffer xt & 1, in its use xt >> 1
+  bool ok = true;   // false once a wait of this thread has given up
+  if (threadIdx.x == 0) {
+    mbar_init(smem_addr(&s_mb[0]));
+    mbar_init(smem_addr(&s_mb[1]));
+    mbar_init_fence();
+    mbar_arm(smem_addr(&s_mb[0]), kSweepSlotBytes * kL2Cluster);
+    mbar_arm(smem_addr(&s_mb[1]), kSweepSlotBytes * kL2Cluster);
+  }
+  cluster_sync();  // every CTA's mbarriers initialised before any partial is sent
 
   for (uint64_t item = cluster_id; item < a.nitems; item += nclusters) {
     const uint64_t b = item / (uint64_t)a.A;
@@ -483,6 +506,7 @@ __global__ void __launch_bounds__(kL2Threads, 1) sweep_l2_kernel(const __grid_co
         else
           l2_onchip_round<false, false>(xr, cr, s_state, s_cost, u, s_T, ad, amp0, acc, false);
       }
+      const int buf = xt & 1;
       float hi[kSlots], lo[kSlots];
 #pragma unroll
       for (int k = 0; k < kSlots; ++k) {
@@ -504,13 +528,25 @@ __global__ void __launch_bounds__(kL2Threads, 1) sweep_l2_kernel(const __grid_co
           lo[k] = d.y;
           if (k < nv) df_warp(hi[k], lo[k]);
         }
-        if (lane < kL2Cluster) {
-#pragma unroll
-          for (int k = 0; k < kSlots; ++k)
-            if (k < nv) st_dsmem_f32x2(&s_ps[buf][rank][k], (unsigned)lane, make_float2(hi[k], lo[k]));
+        if (lane < kL2Cluster && ok) {  // all six slots, zero past nv: 48 bytes per peer
+          const uint32_t rs = mapa_shared(smem_addr(&s_ps[buf][rank][0]), (unsigned)lane);
+          const uint32_t rm = mapa_shared(smem_addr(&s_mb[buf]), (unsigned)lane);
+          st_async_v4(rs, make_float4(hi[0], lo[0], hi[1], lo[1]), rm);
+          st_async_v4(rs + 16, make_float4(hi[2], lo[2], hi[3], lo[3]), rm);
+          st_async_v4(rs + 32, make_float4(hi[4], lo[4], hi[5], lo[5]), rm);
         }
       }
-      cluster_sync();  // release/acquire: every CTA's partial visible locally
+      // every CTA's partial in this CTA's receive slots (no cluster barrier:
+      // the streaming warps' stores need not complete first)
+      if (ok && !mbar_wait(smem_addr(&s_mb[buf]), (xt >> 1) & 1u, a.status)) {
+        ok = false;
+        atomicExch(a.status, 1u);
+      }
+      ok = __all_sync(0xffffffffu, ok);
+      // armed for its next use, two rounds on (a peer sends into it only
+      // after this CTA's partial of the round in between)
+      if (threadIdx.x == 0 && ok) mbar_arm(smem_addr(&s_mb[buf]), kSweepSlotBytes * kL2Cluster);
+      ++xt;
       // every warp: the cluster sum in rank order
 #pragma unroll
       for (int k = 0; k < kSlots; ++k) {
@@ -528,11 +564,11 @@ __global__ void __launch_bounds__(kL2Threads, 1) sweep_l2_kernel(const __grid_co
                      Bi = (double)hi[4] + lo[4];
         const double P = A0 + 2.0 * ((double)ar * Br + (double)aim * Bi) +
                          (double)cnt0 * ((double)ar * ar + (double)aim * aim);
-        a.out[(b * (uint64_t)a.A + ai) * a.R + ridx] = P;
+        a.out[(b * (uint64_t)a.A + ai) * a.R + ridx] =
+            ok ? P : __longlong_as_double(0x7ff8000000000000ll);
       }
       ad = make_float2(ar, aim);
       if (ro) ++ridx;
-      buf ^= 1;
     }
     __syncthreads();  // s_T and s_cost are rewritten for the next item
   }
@@ -633,14 +669,18 @@ static int launch_sweep(const SweepArgs &args, cudaStream_t st) {
   return GQAOA_OK;
 }
 
+// [A][256] phase tables | [A] mixer coefficients | the status word (256 B
+// block) | the cluster-resident path's L2 slots.
 static size_t sweep_ws_layout(int n, int A, bool resident, char *base, float2 **phase,
-                              double2 **alpha, float4 **scratch) {
+                              double2 **alpha, unsigned **status, float4 **scratch) {
   const size_t o_alpha = round_up(sizeof(float2) * 256 * (size_t)A, 256);
-  const size_t o_scratch = o_alpha + round_up(sizeof(double2) * (size_t)A, 256);
+  const size_t o_status = o_alpha + round_up(sizeof(double2) * (size_t)A, 256);
+  const size_t o_scratch = o_status + 256;
   const size_t scratch_bytes = resident ? (size_t)kL2Slots * (sizeof(float2) << n) : 0;
   if (base) {
     *phase = reinterpret_cast<float2 *>(base);
     *alpha = reinterpret_cast<double2 *>(base + o_alpha);
+    *status = reinterpret_cast<unsigned *>(base + o_status);
     *scratch = resident ? reinterpret_cast<float4 *>(base + o_scratch) : nullptr;
   }
   return o_scratch + scratch_bytes;
@@ -671,7 +711,8 @@ extern "C" int gqaoa_sweep_workspace_size(int n, int angles, int amps_per_thread
   const int mode = sweep_mode(n, amps_per_thread);
   const int rc = sweep_check_n(n, mode);
   if (rc) return rc;
-  *bytes = sweep_ws_layout(n, angles, mode == GQAOA_SWEEP_L2, nullptr, nullptr, nullptr, nullptr);
+  *bytes = sweep_ws_layout(n, angles, mode == GQAOA_SWEEP_L2, nullptr, nullptr, nullptr, nullptr,
+                           nullptr);
   return GQAOA_OK;
 }
 
@@ -696,21 +737,24 @@ extern "C" int gqaoa_sweep(const uint8_t *cost, int n, int m, int batch, const d
     if (i > 0 && rounds[i] <= rounds[i - 1]) return GQAOA_EINVAL;
   }
   const bool resident = mode == GQAOA_SWEEP_L2;
-  if (ws_bytes < sweep_ws_layout(n, angles, resident, nullptr, nullptr, nullptr, nullptr))
+  if (ws_bytes < sweep_ws_layout(n, angles, resident, nullptr, nullptr, nullptr, nullptr, nullptr))
     return GQAOA_ENOMEM;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SweepArgs args = {};
   float2 *phase = nullptr;
   double2 *alpha = nullptr;
   float4 *scratch = nullptr;
-  sweep_ws_layout(n, angles, resident, static_cast<char *>(ws), &phase, &alpha, &scratch);
+  unsigned *status = nullptr;
+  sweep_ws_layout(n, angles, resident, static_cast<char *>(ws), &phase, &alpha, &status, &scratch);
   rc = phase_tables(gammas, betas, angles, 256, phase, alpha, st);
   if (rc) return rc;
+  GQ_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
   args.cost = cost;
   args.phase = phase;
   args.alpha = alpha;
   args.out = out;
   args.scratch = scratch;
+  args.status = status;
   args.nitems = (uint64_t)batch * (uint64_t)angles;
   args.n = n;
   args.A = angles;
