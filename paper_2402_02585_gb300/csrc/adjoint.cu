@@ -342,10 +342,14 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       const float2 bv = make_float2((al.x * Lr + al.y * Li) * inv_n, (al.x * Li - al.y * Lr) * inv_n);
       const float2 *T = s_T[k & 1];
       float g = 0.f, nlr = 0.f, nli = 0.f;
+      // round k - 1's checkpoint slot j is loaded as soon as round k's is
+      // used, so each load has the rest of the round and its exchange to land
+      const float2 *ckn = a.ckpt + ((uint64_t)(k > 0 ? k - 1 : 0) * a.B + b) * N + z0;
 #pragma unroll
       for (int j = 0; j < kAdjPer; ++j) {
         const float2 mu = make_float2(l[j].x + bv.x, l[j].y + bv.y);
         g = fmaf((float)c[j], fmaf(mu.x, x[j].y, -mu.y * x[j].x), g);
+        if (k > 0) x[j] = ckn[j * kThreads];
         const float2 t = T[c[j]];
         l[j] = make_float2(fmaf(t.x, mu.x, t.y * mu.y), fmaf(t.x, mu.y, -t.y * mu.x));
         nlr += l[j].x;
@@ -363,14 +367,7 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       v[0] = make_float2(g, 0.f);
       v[1] = make_float2(nlr, 0.f);
       v[2] = make_float2(nli, 0.f);
-      // round k - 1's checkpoints, loaded while the partials are exchanged
-      adj_cluster_sum<kThreads, kCluster, 3>(v, s_wp, s_ps, s_mb, rank, sy, a.status, [&]() {
-        if (k > 0) {
-          const float2 *ck = a.ckpt + ((uint64_t)(k - 1) * a.B + b) * N + z0;
-#pragma unroll
-          for (int j = 0; j < kAdjPer; ++j) x[j] = ck[j * kThreads];
-        }
-      });
+      adj_cluster_sum<kThreads, kCluster, 3>(v, s_wp, s_ps, s_mb, rank, sy, a.status);
       if (writer) {  // the round's sums, finished in FP64 by adj_finalize_kernel
         *reinterpret_cast<float2 *>(a.record + 4 * bk + 3) = v[0];  // G_k
         *reinterpret_cast<float2 *>(a.dbeta + bk) = Ld;             // L_k (re)
