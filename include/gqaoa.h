@@ -51,7 +51,8 @@ extern "C" {
 #define GQAOA_EINVAL (-1)   /* null pointer, bad literal, misaligned buffer */
 #define GQAOA_ERANGE (-2)   /* n, m, p or a count outside the supported range */
 #define GQAOA_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
-#define GQAOA_ETIMEOUT (-4) /* a bounded device-side wait gave up */
+#define GQAOA_ETIMEOUT (-4) /* reserved: the asynchronous calls report a bounded
+                               device-side wait that gave up as NaN results */
 #define GQAOA_ENOMEM (-5)   /* the caller's workspace is smaller than required */
 
 #define GQAOA_MAX_N 34   /* 2^34 complex64 amplitudes = 128 GiB */
