@@ -216,10 +216,15 @@ class _DepthBatch:
         self.a_in = self.h_in.numpy()
         self.a_out = self.h_out.numpy()
         self.ws = None
+        self.ws_need = {}  # (rows, rounds) -> workspace bytes
 
-    def __call__(self, rows):
-        """rows: list of (k, gammas [k], betas [k]). Returns a list of
-        (<H_P>, dL/dgamma [k], dL/dbeta [k])."""
+    def __call__(self, rows, single: bool = False):
+        """rows: list of (k, gammas, betas), the angles either k-vectors or,
+        with `single`, two scalars used in all k rounds. Returns one
+        (<H_P>, dL/dgamma, dL/dbeta) per row: with `single` the derivatives
+        summed over the k rounds (floats, the sums of the k-vectors), else
+        views of the k-vectors in the output buffer, valid until the next
+        call."""
         prot = self.prot
         B = len(rows)
         P = max(k for k, _, _ in rows)
@@ -233,7 +238,9 @@ class _DepthBatch:
             st = torch.cuda.current_stream()
             d_in = self.d_in[:2 * B * P]
             d_in.copy_(self.h_in[:2 * B * P], non_blocking=True)
-            need = C.gqaoa_grad_batched_workspace_size(prot.n, B, P)
+            need = self.ws_need.get((B, P))
+            if need is None:
+                need = self.ws_need[(B, P)] = C.gqaoa_grad_batched_workspace_size(prot.n, B, P)
             if self.ws is None or self.ws.numel() < need:
                 self.ws = core.workspace(need, prot.cost.device)
             ang, out = d_in.data_ptr(), self.d_out.data_ptr()
@@ -247,8 +254,10 @@ class _DepthBatch:
         gr = self.a_out[B:nb].reshape(2, B, P)
         prot.evaluations += B
         prot.launches += core.grad_launches(prot.n, P)
-        return [(float(v[i]), gr[0, i, P - k:].copy(), gr[1, i, P - k:].copy())
-                for i, (k, _, _) in enumerate(rows)]
+        if single:
+            return [(float(v[i]), float(gr[0, i, P - k:].sum()), float(gr[1, i, P - k:].sum()))
+                    for i, (k, _, _) in enumerate(rows)]
+        return [(float(v[i]), gr[0, i, P - k:], gr[1, i, P - k:]) for i, (k, _, _) in enumerate(rows)]
 
 
 class _Lbfgsb:
@@ -504,19 +513,15 @@ class Protocol:
         results, errors = {}, []
 
         def rows_of(wave):
-            rows = []
-            for k, x in wave.items():
-                if single:
-                    rows.append((k, np.full(k, x[0]), np.full(k, x[1])))
-                else:
-                    rows.append((k, x[:k], x[k:]))
-            return rows
+            if single:
+                return [(k, x[0], x[1]) for k, x in wave.items()]
+            return [(k, x[:k], x[k:]) for k, x in wave.items()]
 
         def evaluate(wave):
-            out = batch(rows_of(wave))
+            out = batch(rows_of(wave), single)
             res = {}
-            for (k, _), (e, dg, db) in zip(wave.items(), out):
-                res[k] = (e, np.array([dg.sum(), db.sum()]) if single else np.concatenate([dg, db]))
+            for k, (e, dg, db) in zip(wave, out):
+                res[k] = (e, np.array([dg, db]) if single else np.concatenate([dg, db]))
             return res
 
         def x0_of(k):
