@@ -7,14 +7,15 @@
 // cluster owns one instance (row) for the whole call: each thread keeps 16
 // amplitudes in registers, the forward rounds write the checkpoints chi_k
 // (each thread later rereads only its own), and the backward rounds follow
-// in the same launch. A round's sums are FP32 butterflies over the warp's
-// lanes, then (warp 0) over the CTA's warps, then over the cluster's CTAs
-// (every CTA's partial stored into the shared memory of every peer, every
-// warp summing them), so every warp of every CTA holds the same totals bit
-// for bit and no further barrier is needed; the objective's value is summed
-// the same way in double-float. FP32 amplitudes and mixer coefficients: the
-// rounds use no FP64, a closing kernel forms the gradients from the sums
-// they left.
+// in the same launch. A round's sums are butterflies over the warp's lanes
+// (FP32: at most 512 amplitudes a warp), then (warp 0) over the CTA's warps
+// and over the cluster's CTAs in double-float (FP32 pairs, ~48 bits, so the
+// mixer sum keeps FP64 accuracy on the FP32 pipe); every CTA's partial is
+// stored into the shared memory of every peer and every warp sums them, so
+// every warp of every CTA holds the same totals bit for bit and no further
+// barrier is needed. The objective's value is double-float at every stage.
+// FP32 amplitudes and mixer coefficients: the rounds use no FP64, a closing
+// kernel forms the gradients from the double-float sums they left.
 //
 // Forward round k: chi_k = T_k[c] psi_{k-1} (checkpointed), S_k = sum chi_k,
 // a_k = alpha_k S_k / N, psi_k = chi_k + a_k. Backward, from
@@ -43,7 +44,7 @@ struct AdjArgs {
   uint64_t cost_bstride;
   const float2 *phase;    // [B][p][256]
   const double2 *alpha;   // [B][p]
-  double *record;         // [B][p][4]: S_k (re, im as float pairs), float alpha_k, G_k
+  double *record;         // [B][p][4]: S_k (re, im as double-float pairs), float alpha_k, G_k
   float2 *ckpt;           // [p][B][N]
   double *value;          // [B]
   double *dgamma;         // [B][p]
@@ -65,7 +66,7 @@ __device__ __forceinline__ void adj_df_add(float &hi, float &lo, float x) {
 }
 
 // The exchange of one cluster reduction (st.async into every CTA's receive
-// slot, mbarrier-counted): a CTA's partials are three float pairs, 24 bytes.
+// slot, mbarrier-counted): a CTA's partials are three double-float pairs, 24 bytes.
 constexpr uint32_t kAdjSlotBytes = 24;
 
 struct AdjSync {
@@ -115,10 +116,10 @@ __device__ __forceinline__ void adj_group(float2 &v) {
 
 // Cluster-wide sums of kV <= kAdjVals values: v[k] holds this thread's
 // partial on entry (an FP32 value in .x, or a double-float pair with kDF);
-// on exit v[k] is the cluster's total (FP32 in .x and 0 in .y, or a
-// double-float pair with kDF), the same bits in every thread: each stage
-// (the warp's lanes, the CTA's warps, the cluster's CTAs) is a butterfly,
-// whose partner lanes add the same two operands.
+// on exit v[k] is the cluster's total as a double-float pair, the same bits
+// in every thread: each stage is a butterfly, whose partner lanes add the
+// same two operands (the warp's lanes in FP32, or double-float with kDF;
+// the CTA's warps and the cluster's CTAs in double-float).
 // The buffers alternate between calls (sy.t counts them): the partials of
 // one call are read while the next call's are written. Slots are 32 bytes
 // (v[0], v[1] at 0, v[2] at 16). between() runs while the partials are in
@@ -152,7 +153,7 @@ __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
       d[k] = make_float2(0.f, 0.f);
       if (k < kV) {
         d[k] = s_wp[buf][lane & (kW - 1)][k];
-        adj_group<kW, kDF>(d[k]);
+        adj_group<kW, true>(d[k]);
       }
     }
     if (kCluster == 1) {
@@ -184,7 +185,7 @@ __device__ __forceinline__ void adj_cluster_sum(float2 (&v)[kAdjVals],
 #pragma unroll
   for (int k = 0; k < kV; ++k) {
     float2 d = s_ps[buf][lane & (kCluster - 1)][k];
-    adj_group<kCluster, kDF>(d);
+    adj_group<kCluster, true>(d);
     v[k] = d;
   }
   ++sy.t;
@@ -292,7 +293,7 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
       const float2 af = make_float2((al.x * Sr - al.y * Si) * inv_n, (al.x * Si + al.y * Sr) * inv_n);
 #pragma unroll
       for (int j = 0; j < kAdjPer; ++j) s[j] = make_float2(s[j].x + af.x, s[j].y + af.y);
-      if (writer)  // S_k as float pairs (sum, 0), read by adj_finalize_kernel
+      if (writer)  // S_k as double-float pairs, read by adj_finalize_kernel
         *reinterpret_cast<float4 *>(a.record + 4 * bk) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
     }
     // lambda_p = O psi_p, the objective sum_z O |psi_p|^2 (double-float:
@@ -335,7 +336,7 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
     // backward rounds
     for (int k = a.p - 1; k >= 0; --k) {
       const uint64_t bk = b * (uint64_t)a.p + k;
-      const float2 Ld = v[1], Li2 = v[2];  // this round's L (as float pairs)
+      const float2 Ld = v[1], Li2 = v[2];  // this round's L (double-float)
       const float Lr = Ld.x + Ld.y, Li = Li2.x + Li2.y;
       const float2 al = aln;
       if (k > 0) aln = alf[4 * (k - 1)];
@@ -378,7 +379,7 @@ adjoint_cluster_kernel(const __grid_constant__ AdjArgs a) {
   if (kCluster > 1) cluster_sync();  // no CTA leaves while a peer may still store into it
 }
 
-// The gradients in FP64 from the sums the rounds left (float pairs; one
+// The gradients in FP64 from the double-float sums the rounds left (one
 // thread per instance and round, off the rounds' critical path):
 // dE/dbeta_k = 2 Im(conj(e^{-i beta_k} S_k / N) L_k), dE/dgamma_k = 2 G_k.
 // If a bounded wait of the rounds gave up, every value and derivative of the
