@@ -210,6 +210,12 @@ def test_reduced_sweep_rejects_bad_arguments_before_launch():
 def test_sweep_workspace_sizes():
     small = C.gqaoa_sweep_workspace_size(12, 4, 0)
     assert 0 < small < 1 << 16
+    # [A][256] complex64 phase tables | [A] complex128 mixer coefficients |
+    # a 256-byte block for the status word of the clusters' bounded waits,
+    # each part starting on a 256-byte boundary
+    up = lambda b: (b + 255) // 256 * 256
+    for A in (1, 4, 33):
+        assert C.gqaoa_sweep_workspace_size(12, A, 0) == up(8 * 256 * A) + up(16 * A) + 256
     assert C.gqaoa_sweep_workspace_size(19, 4, 32) == small
     resident = C.gqaoa_sweep_workspace_size(20, 4, C.GQAOA_SWEEP_L2)
     assert resident == small + 16 * 8 * (1 << 20)       # 16 slots of 2^20 complex64
