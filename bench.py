@@ -555,19 +555,19 @@ def run_grad(args, wl):
     el = start.elapsed_time(stop) / 1e3
     units = B * p * N * args.steps
     cluster = 10 <= n <= 16  # the library's cluster-resident adjoint (gqaoa.h)
+    # algorithmic bytes per step (core.grad_hbm_bytes): on the cluster path
+    # the cost table read once (1 B per amplitude) and every checkpoint
+    # written forward and read backward (8 + 8 B per amplitude-round), the
+    # state and lambda staying on chip; on the streaming passes the forward
+    # 9 B (round 1) + 17 B (rounds 2..p) per amplitude, lambda init 17 B,
+    # backward 25 B per amplitude-round
+    alg = B * N * core.grad_hbm_bytes(n, p)
     if cluster:
-        # algorithmic bytes per step: the cost table read once (1 B per
-        # amplitude) and every checkpoint written forward and read backward
-        # (8 + 8 B per amplitude-round); the state and lambda stay on chip
-        alg = B * N * (1 + 16 * p)
         kernel = ("adjoint_cluster_kernel (one cluster per instance for all rounds, 16 B per "
                   "amplitude-round of checkpoints; bound by its per-round cluster reductions, "
                   "not by HBM; streaming_grad below: the streaming passes, 42 B per "
                   "amplitude-round, timed on the same angles)")
     else:
-        # forward 9 B (round 1) + 17 B (rounds 2..p) per amplitude, lambda
-        # init 17 B, backward 25 B per amplitude-round
-        alg = B * N * (9 + 17 * (p - 1) + 17 + 25 * p)
         kernel = "forward rounds + backward rounds (mean over the step)"
     achieved = alg * args.steps / el / 1e9
     peak, kind = hbm_peak()
@@ -586,7 +586,7 @@ def run_grad(args, wl):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / 5
-        s_alg = B * N * (9 + 17 * (p - 1) + 17 + 25 * p)
+        s_alg = B * N * core.grad_hbm_bytes(n, p, streaming=True)
         streaming = {"ms_per_call": ms, "hbm_gbs": s_alg / (ms / 1e3) / 1e9,
                      "frac": s_alg / (ms / 1e3) / 1e9 / peak,
                      "note": "gradient call only (no Adam step), GQAOA_GRAD_STREAMING"}
@@ -1189,11 +1189,13 @@ def run_study(args, wl):
     el = time.perf_counter() - t0
     clk = clocks.stop()
     r = results[-1]
-    # the dominant kernels are the batched adjoint passes of the label phase:
-    # per Adam step and instance 9 + 17 (p - 1) + 17 + 25 p bytes per amplitude
-    # (forward rounds with checkpoints, lambda init, backward rounds)
+    # the dominant kernels are the batched adjoint gradients of the label
+    # phase: per Adam step and instance the algorithmic bytes of the path the
+    # library takes for its n (core.grad_hbm_bytes: 1 + 16 p per amplitude
+    # with the state on chip, n <= 16; the streaming passes' 9 + 17 (p - 1)
+    # + 17 + 25 p above)
     p = wl["p"]
-    label_bytes = r["label_amplitudes_x_steps"] * (9 + 17 * (p - 1) + 17 + 25 * p)
+    label_bytes = r["label_hbm_bytes"]
     achieved = label_bytes / r["timings"]["labels_s"] / 1e9
     peak, peak_kind = hbm_peak()
     if rank == 0:
@@ -1218,8 +1220,9 @@ def run_study(args, wl):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                          "kernel": "label phase: batched adjoint gradient + Adam (algorithmic "
-                                   "bytes of the forward and backward passes over the phase's "
-                                   "wall time, host work included)"},
+                                   "bytes of each n's gradient path, cluster-resident for "
+                                   "n <= 16 and streaming above, over the phase's wall time, "
+                                   "host work included)"},
             "cpu_baseline": None,
             "gpu_launches": r["gpu_launches"], "clocks": clk}), flush=True)
     return 0

@@ -205,6 +205,19 @@ def grad_launches(n: int, p: int, streaming: bool = False) -> int:
     return 2 * p + 3
 
 
+def grad_hbm_bytes(n: int, p: int, streaming: bool = False) -> int:
+    """Algorithmic HBM bytes per amplitude of one gqaoa_grad(_batched)
+    evaluation, following the library's choice of path: with the state on
+    chip (the cluster-resident adjoint for 10 <= n <= 16, the one-CTA kernels
+    below 4096 amplitudes) the cost byte once and each round's checkpoint
+    written forward and read backward, 1 + 16 p; on the streaming passes the
+    forward rounds (9 B, then 17 B per round), lambda's initialisation (17 B)
+    and the backward rounds (25 B per round)."""
+    if (10 <= n <= 16 and not streaming) or (1 << n) < 4096:
+        return 1 + 16 * p
+    return 9 + 17 * (p - 1) + 17 + 25 * p
+
+
 def grad_batched(cost: torch.Tensor, n: int, m: int, gammas, betas, objective: str = "p0",
                  shared_cost: bool = False, ws: torch.Tensor | None = None):
     """Batched adjoint: value [B], dgamma [B, p], dbeta [B, p]."""

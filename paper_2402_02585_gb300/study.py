@@ -31,7 +31,7 @@ CKPT_BUDGET_BYTES = 8 << 30
 
 # kernels launched and instances x 2^n x gradient evaluations of the label
 # phase, accumulated by generate_labels / evaluate / features (run() resets them)
-counters = {"launches": 0, "label_amp_evaluations": 0}
+counters = {"launches": 0, "label_amp_evaluations": 0, "label_hbm_bytes": 0}
 
 
 def make_instances(count: int, seed: int, n_values, d_lo: float, d_hi: float,
@@ -93,6 +93,7 @@ def generate_labels(insts, p: int, grid: int = 16, steps: int = 150, lr: float =
         g, b = opt.angles()
         counters["launches"] += 2 + opt.launches  # grid sweep: phase tables + sweep kernel
         counters["label_amp_evaluations"] += opt.amp_evaluations
+        counters["label_hbm_bytes"] += opt.amp_evaluations * core.grad_hbm_bytes(n, p)
         labels[idx] = canonicalize(g.cpu().numpy(), b.cpu().numpy())
     X = features(insts, d_in)
     Y = torch.as_tensor(labels, dtype=torch.float32, device=X.device)
@@ -191,6 +192,7 @@ def run(train_count=20000, train_n=range(10, 19), test_count=2000, test_n=(20,),
     from .proposer import Proposer
     counters["launches"] = 0
     counters["label_amp_evaluations"] = 0
+    counters["label_hbm_bytes"] = 0
     t = {}
     t0 = time.perf_counter()
     train = make_instances(train_count, seed=seed + 1, n_values=train_n, d_lo=d_lo, d_hi=d_hi)
@@ -217,7 +219,8 @@ def run(train_count=20000, train_n=range(10, 19), test_count=2000, test_n=(20,),
     return {"timings": t, "loss_first": losses[0], "loss_last": losses[-1],
             "train_instances": len(train), "test_instances": len(test), "p": p,
             "gpu_launches": counters["launches"] + prop.launches,
-            "label_amplitudes_x_steps": counters["label_amp_evaluations"], **ev}
+            "label_amplitudes_x_steps": counters["label_amp_evaluations"],
+            "label_hbm_bytes": counters["label_hbm_bytes"], **ev}
 
 
 if __name__ == "__main__":

@@ -289,3 +289,16 @@ def test_fairness_workspace_and_bad_arguments_before_launch():
     assert call(shots=0) == C.GQAOA_EINVAL
     assert call(to_all=fake + 4) == C.GQAOA_EINVAL  # misaligned output
     assert call(ws_bytes=need - 1) == C.GQAOA_ENOMEM
+
+
+def test_gradient_path_helpers_agree():
+    # grad_launches and grad_hbm_bytes follow the same choice of path: the
+    # state stays on chip (cluster-resident adjoint, or the one-CTA kernels)
+    # exactly where the streaming passes' 2p + 3 launches are not made
+    from paper_2402_02585_gb300 import core
+    for p in (1, 4, 32):
+        for n in range(6, 29):
+            for streaming in (False, True):
+                on_chip = core.grad_launches(n, p, streaming) != 2 * p + 3
+                assert (core.grad_hbm_bytes(n, p, streaming) == 1 + 16 * p) == on_chip, (n, p, streaming)
+    assert core.grad_hbm_bytes(16, 32) < core.grad_hbm_bytes(16, 32, streaming=True)
