@@ -227,12 +227,7 @@ class _DepthBatch:
         call."""
         prot = self.prot
         B = len(rows)
-        P = max(k for k, _, _ in rows)
-        a = self.a_in[:2 * B * P].reshape(2, B, P)
-        a[:] = 0.0
-        for i, (k, g, b) in enumerate(rows):
-            a[0, i, P - k:] = g
-            a[1, i, P - k:] = b
+        P = pad_depth_rows(self.a_in, rows)
         nb = B + 2 * B * P
         with _GATE.work():
             st = torch.cuda.current_stream()
@@ -250,14 +245,40 @@ class _DepthBatch:
                                  st.cuda_stream)
             self.h_out[:nb].copy_(self.d_out[:nb], non_blocking=True)
             st.synchronize()
-        v = self.a_out[:B]
-        gr = self.a_out[B:nb].reshape(2, B, P)
         prot.evaluations += B
         prot.launches += core.grad_launches(prot.n, P)
-        if single:
-            return [(float(v[i]), float(gr[0, i, P - k:].sum()), float(gr[1, i, P - k:].sum()))
-                    for i, (k, _, _) in enumerate(rows)]
-        return [(float(v[i]), gr[0, i, P - k:], gr[1, i, P - k:]) for i, (k, _, _) in enumerate(rows)]
+        return depth_row_results(self.a_out, rows, P, single)
+
+
+def pad_depth_rows(buf: np.ndarray, rows) -> int:
+    """Write the angles of rows (k, gammas, betas) into buf as the [2][B][P]
+    block [gammas | betas] of a batched call, P the deepest k: row i's k
+    angles (k-vectors, or scalars repeated in all k rounds) in its last k
+    rounds, its first P - k rounds zero (identity rounds: phase factor 1,
+    mixer term 0). Returns P."""
+    B = len(rows)
+    P = max(k for k, _, _ in rows)
+    a = buf[:2 * B * P].reshape(2, B, P)
+    a[:] = 0.0
+    for i, (k, g, b) in enumerate(rows):
+        a[0, i, P - k:] = g
+        a[1, i, P - k:] = b
+    return P
+
+
+def depth_row_results(buf: np.ndarray, rows, P: int, single: bool):
+    """Read a batched call's output [value [B] | dgamma [B][P] | dbeta [B][P]]
+    from buf for rows padded by pad_depth_rows: one (value, dL/dgamma,
+    dL/dbeta) per row over its own last k rounds (the padding rounds'
+    derivatives dropped): with `single` summed over the k rounds (floats),
+    else views of the k-vectors in buf."""
+    B = len(rows)
+    v = buf[:B]
+    gr = buf[B:B + 2 * B * P].reshape(2, B, P)
+    if single:
+        return [(float(v[i]), float(gr[0, i, P - k:].sum()), float(gr[1, i, P - k:].sum()))
+                for i, (k, _, _) in enumerate(rows)]
+    return [(float(v[i]), gr[0, i, P - k:], gr[1, i, P - k:]) for i, (k, _, _) in enumerate(rows)]
 
 
 class _Lbfgsb:
